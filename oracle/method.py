@@ -1,0 +1,331 @@
+"""Multilevel spectral domain decomposition, plain FP64 CPU oracle.
+
+Test infrastructure only: the tests, the smoke check and the CPU-baseline leg
+of the benchmark use it; the CUDA library never does.
+
+Steps, in the paper's order and notation:
+  1. Local Neumann forms abar_{l,i}(u, v) = sum_{tau in T_{h,l,i}} a_tau(u, v)
+     (Eq. locala_cg) and the partition-of-unity weighted form
+     b^1_{l,i}(u, v) = abar_{l,i}(chi u, chi v) (Eq. cg_rhs_blf, first line).
+  2. Local GEVPs abar(w, v) = lambda b(w, v) (Eq. theGEVP), solved exactly:
+     after dropping the common kernel ker A cap ker B (Section 3.3 remark and
+     Section 4.2: on coarse levels only a generating system is available),
+     the spectral transformation b(p, v) = mu (a + b)(p, v), mu = 1/(1+lambda)
+     (proof of the non-defectiveness lemma, Section 3.3) turns the pencil into
+     a standard symmetric problem that the Jacobi method solves completely.
+  3. Coarse space V_{h,l-1} = span{ e chi w : lambda < eta } (Eq.
+     coarse_space_def), at most nev_max per subdomain (Section 5.1.1 offers a
+     fixed count or a threshold; both are applied, the smaller wins).
+  4. Coarse levels built from the generating system of Section 4.2: own
+     children's basis functions plus the restrictions of the neighbouring
+     children's basis functions to Omega_{l,i}; chi_{l,i} keeps the own part.
+  5. Dirichlet subspaces V_{h,l,i} (Eq. dirichlet_space) and the additive
+     preconditioner B = sum_i R_i^T A_i^{-1} R_i over all levels plus the
+     coarsest solve (Section 2.1, Eq. mlsdd), used in CG, stopped when
+     ||b - A x^m|| < tol ||b - A x^0|| (Section 5) with x^0 = 0 and the
+     Euclidean norm.
+
+Readings where the paper is silent (listed with the others in the design
+notes): rank threshold 1e-12 * max eigenvalue of (A + B) for dropping the
+common kernel; eigenvalues with mu <= 1e-13 are treated as +infinity; an
+eigenvector is normalised to b(w, w) = 1 and signed so that its entry of
+largest magnitude is positive; selection uses lambda < eta strictly.
+"""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import fem
+from . import linalg
+from .decomposition import Decomposition
+
+TOL_RANK = 1e-12
+MU_INF = 1e-13
+
+
+def _pool_size():
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def gevp(Abar, B, rank_reveal):
+    """All eigenpairs of Abar w = lambda B w with finite lambda, ascending.
+
+    Returns (lam, W) with W[:, k] b-orthonormal (W^T B W = I) and lam sorted
+    ascending.  If rank_reveal, the common kernel of Abar and B is removed
+    first (eigenvectors of Abar + B with eigenvalue <= TOL_RANK * max).
+    """
+    n = Abar.shape[0]
+    S = Abar + B
+    if rank_reveal:
+        s, U = linalg.jacobi_eigh(S)
+        keep = s > TOL_RANK * max(s.max(), 0.0)
+        U = U[:, keep]
+    else:
+        U = np.eye(n)
+    Ar = U.T @ Abar @ U
+    Br = U.T @ B @ U
+    Lc = linalg.cholesky(0.5 * ((Ar + Br) + (Ar + Br).T))
+    # C = L^{-1} Br L^{-T}
+    T = linalg.forward(Lc, Br)              # L^{-1} Br
+    C = linalg.forward(Lc, T.T)             # L^{-1} (L^{-1} Br)^T = L^{-1} Br L^{-T}
+    mu, V = linalg.jacobi_eigh(C)           # ascending mu
+    order = np.argsort(-mu, kind="stable")  # descending mu == ascending lambda
+    mu, V = mu[order], V[:, order]
+    finite = mu > MU_INF
+    mu, V = mu[finite], V[:, finite]
+    W = U @ linalg.backward(Lc, V)          # w = U L^{-T} v
+    W = W / np.sqrt(mu)[None, :]            # b(w, w) = v^T C v / mu = 1
+    lam = 1.0 / mu - 1.0
+    return lam, W
+
+
+def normalise_sign(W):
+    """Flip each column so that its entry of largest magnitude is positive."""
+    W = W.copy()
+    for k in range(W.shape[1]):
+        i = int(np.argmax(np.abs(W[:, k])))
+        if W[i, k] < 0:
+            W[:, k] = -W[:, k]
+    return W
+
+
+def select_count(lam, nev_max, eta):
+    """m = min(nev_max, #{lambda < eta}) (Eq. coarse_space_def, Section 5.1.1)."""
+    return int(min(nev_max, int(np.sum(lam < eta))))
+
+
+class Level:
+    pass
+
+
+class Hierarchy:
+    """Result of the oracle set-up: all levels, spaces and factors."""
+
+    def __init__(self, mesh, coeff, parts, overlap, levels, group, nev_max, eta,
+                 keep_local=False):
+        self.mesh = mesh
+        self.nev_max = nev_max
+        self.eta = eta
+        self.A = fem.assemble_system(mesh, coeff)
+        self.n = self.A.shape[0]
+        self.dec = Decomposition(mesh, parts, overlap, levels, group)
+        self.L = self.dec.L
+        self.n2u = mesh.node_to_unknown()
+        self._coeff = coeff
+        self.levels = {}
+        self._build_fine(keep_local)
+        for l in range(self.L - 1, 0, -1):
+            self._build_coarse(l, keep_local)
+        P0 = self.levels[1].P_coarse
+        self.A0 = (P0.T @ (self.A @ P0))
+        self.A0 = np.asarray(self.A0.todense() if sp.issparse(self.A0) else self.A0)
+        self.A0 = 0.5 * (self.A0 + self.A0.T)
+        self.n0 = self.A0.shape[0]
+        self.L0 = linalg.cholesky(self.A0) if self.n0 > 0 else None
+
+    # --- fine level -----------------------------------------------------
+    def _build_fine(self, keep_local):
+        mesh, dec = self.mesh, self.dec
+        chis, counts = dec.partition_of_unity()
+        self.pou_counts = counts
+        Ke = fem.element_matrices(mesh, self._coeff)
+        en = mesh.element_nodes()
+
+        def local(i):
+            s = dec.fine[i]
+            nn = s.neumann_nodes()
+            pos = -np.ones(mesh.num_nodes, dtype=np.int64)
+            pos[nn] = np.arange(len(nn))
+            # Neumann matrix: elements of T_{h,L,i} on the non-Dirichlet nodes
+            Abar = np.zeros((len(nn), len(nn)))
+            for e in np.nonzero(s.element_mask)[0]:
+                loc = pos[en[e]]
+                ok = loc >= 0
+                li = loc[ok]
+                Abar[np.ix_(li, li)] += Ke[e][np.ix_(ok, ok)]
+            chi = chis[i]
+            B = chi[:, None] * Abar * chi[None, :]
+            lam, W = gevp(Abar, B, rank_reveal=False)
+            m = select_count(lam, self.nev_max, self.eta)
+            Wm = normalise_sign(W[:, :m])
+            dn = s.dirichlet_nodes()
+            du = self.n2u[dn]
+            Ai = np.asarray(self.A[du][:, du].todense())
+            Li = linalg.cholesky(Ai)
+            return dict(nn=nn, chi=chi, Abar=Abar if keep_local else None,
+                        B=B if keep_local else None, lam=lam, m=m, W=Wm,
+                        dof=du, Ai=Ai if keep_local else None, Li=Li)
+
+        P = self.dec.num_subdomains(self.L)
+        with ThreadPoolExecutor(_pool_size()) as ex:
+            subs = list(ex.map(local, range(P)))
+        lev = Level()
+        lev.subs = subs
+        # fine basis functions phi = e chi w in unknown coordinates
+        rows, cols, vals = [], [], []
+        col = 0
+        lev.col_range = []
+        for i, s in enumerate(subs):
+            u = self.n2u[s["nn"]]
+            for k in range(s["m"]):
+                phi = s["chi"] * s["W"][:, k]
+                nz = phi != 0.0
+                rows.append(u[nz]); cols.append(np.full(nz.sum(), col)); vals.append(phi[nz])
+                col += 1
+            lev.col_range.append((col - s["m"], col))
+        lev.P_coarse = sp.csc_matrix((np.concatenate(vals) if vals else np.zeros(0),
+                                      (np.concatenate(rows) if rows else np.zeros(0, int),
+                                       np.concatenate(cols) if cols else np.zeros(0, int))),
+                                     shape=(self.n, col))
+        lev.P = None          # P_L = identity
+        self.levels[self.L] = lev
+
+    # --- coarse levels ----------------------------------------------------
+    def _build_coarse(self, l, keep_local):
+        """Level l (0 < l < L): GEVPs on generating systems, Section 4.2."""
+        mesh, dec = self.mesh, self.dec
+        child = self.levels[l + 1]
+        Pl = child.P_coarse                     # n x n_l basis of V_{h,l} in fine coords
+        Pl_dense_cols = Pl.tocsc()
+        Al = np.asarray((Pl.T @ (self.A @ Pl)).todense())
+        Al = 0.5 * (Al + Al.T)
+        keep = self.n2u >= 0
+        unk_nodes = np.nonzero(keep)[0]
+
+        def local(i):
+            own = dec.members[l][i]
+            nbr = dec.neighbours(l, i)
+            own_cols = np.concatenate([np.arange(*child.col_range[j]) for j in own]) if own else np.zeros(0, int)
+            nbr_cols = np.concatenate([np.arange(*child.col_range[j]) for j in nbr]) if nbr else np.zeros(0, int)
+            gen = np.concatenate([own_cols, nbr_cols]).astype(np.int64)
+            G = Pl_dense_cols[:, gen]
+            An = fem.assemble_neumann(mesh, self._coeff, dec.element_mask[l][i])
+            An = An[unk_nodes][:, unk_nodes]
+            Abar = np.asarray((G.T @ (An @ G)).todense())
+            Abar = 0.5 * (Abar + Abar.T)
+            x = np.concatenate([np.ones(len(own_cols)), np.zeros(len(nbr_cols))])
+            B = x[:, None] * Abar * x[None, :]
+            lam, W = gevp(Abar, B, rank_reveal=True)
+            m = select_count(lam, self.nev_max, self.eta)
+            Wm = normalise_sign(W[:, :m])
+            Ai = Al[np.ix_(own_cols, own_cols)]
+            Li = linalg.cholesky(Ai) if len(own_cols) else None
+            return dict(own=own, nbr=nbr, own_cols=own_cols, gen=gen,
+                        Abar=Abar if keep_local else None, B=B if keep_local else None,
+                        lam=lam, m=m, W=Wm, Ai=Ai if keep_local else None, Li=Li)
+
+        P = dec.num_subdomains(l)
+        with ThreadPoolExecutor(_pool_size()) as ex:
+            subs = list(ex.map(local, range(P)))
+        lev = Level()
+        lev.subs = subs
+        lev.P = Pl                                # V_{h,l} basis, fine coordinates
+        lev.A_level = Al
+        # next coarse basis: phi = e chi w = sum over own generators only
+        blocks, col = [], 0
+        lev.col_range = []
+        Z = np.zeros((Pl.shape[1], 0))
+        zcols = []
+        for s in subs:
+            nown = len(s["own_cols"])
+            for k in range(s["m"]):
+                z = np.zeros(Pl.shape[1])
+                z[s["own_cols"]] = s["W"][:nown, k]
+                zcols.append(z)
+            lev.col_range.append((col, col + s["m"]))
+            col += s["m"]
+        lev.Z = np.stack(zcols, axis=1) if zcols else np.zeros((Pl.shape[1], 0))
+        lev.P_coarse = sp.csc_matrix(Pl @ sp.csc_matrix(lev.Z))
+        self.levels[l] = lev
+
+    # --- preconditioner and CG --------------------------------------------
+    def apply_preconditioner(self, r):
+        """z = B r, the additive multilevel Schwarz preconditioner."""
+        z = np.zeros_like(r)
+        fine = self.levels[self.L]
+        for s in fine.subs:
+            z[s["dof"]] += linalg.cho_solve(s["Li"], r[s["dof"]])
+        for l in range(self.L - 1, 0, -1):
+            lev = self.levels[l]
+            rl = lev.P.T @ r
+            zl = np.zeros_like(rl)
+            for s in lev.subs:
+                if s["Li"] is not None:
+                    zl[s["own_cols"]] += linalg.cho_solve(s["Li"], rl[s["own_cols"]])
+            z += lev.P @ zl
+        P0 = self.levels[1].P_coarse
+        if self.n0 > 0:
+            z += P0 @ linalg.cho_solve(self.L0, P0.T @ r)
+        return z
+
+    def apply_one_level(self, r):
+        """z = sum_i R_i^T A_i^{-1} R_i r over the fine subdomains only (no coarse space)."""
+        z = np.zeros_like(r)
+        for s in self.levels[self.L].subs:
+            z[s["dof"]] += linalg.cho_solve(s["Li"], r[s["dof"]])
+        return z
+
+    def coarse_dims(self):
+        """n_l for l = L-1 ... 0: dimension of each coarse space."""
+        out = {}
+        for l in range(self.L, 0, -1):
+            out[l - 1] = self.levels[l].P_coarse.shape[1]
+        return out
+
+    def eigenvalues(self, l):
+        return [s["lam"] for s in self.levels[l].subs]
+
+    def counts(self, l):
+        return [s["m"] for s in self.levels[l].subs]
+
+
+def pcg(A, b, precond, tol=1e-8, maxit=1000, x0=None):
+    """Preconditioned CG; stops when ||r_m||_2 < tol * ||r_0||_2.
+
+    Returns (x, iterations, history of ||r||/||r_0||, alphas, betas).
+    """
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A @ x
+    r0 = np.linalg.norm(r)
+    hist = [1.0]
+    alphas, betas = [], []
+    if r0 == 0.0:
+        return x, 0, hist, alphas, betas
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    while it < maxit:
+        q = A @ p
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        alphas.append(alpha)
+        rel = np.linalg.norm(r) / r0
+        hist.append(rel)
+        if rel < tol:
+            break
+        z = precond(r)
+        rz_new = r @ z
+        beta = rz_new / rz
+        betas.append(beta)
+        rz = rz_new
+        p = z + beta * p
+    return x, it, hist, alphas, betas
+
+
+def lanczos_condition(alphas, betas):
+    """Extreme eigenvalues of the CG Lanczos tridiagonal (estimate of kappa(BA))."""
+    k = len(alphas)
+    if k == 0:
+        return 1.0, 1.0
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k and j < len(betas):
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    w, _ = linalg.jacobi_eigh(T)
+    return w[0], w[-1]
