@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Benchmark of the multilevel spectral DD hot path on one GB300.
+
+A step is one pass of the whole hot path on the 2D 512 x 512 Q1 workload
+(GRF background x channels/inclusions, contrast 1e6, 16 x 16 subdomains,
+overlap 2, three levels, nev <= 12, eta = 0.3): hierarchy set-up (fine
+Dirichlet factorisations, shifted-Neumann factorisations, batched subspace
+iterations, coarse Galerkin and generating-system GEVPs, coarsest factor)
+followed by PCG to relative residual 1e-8.  The metric is seconds per step of
+the chosen form (FP32 fine factors and solves, FP64 elsewhere); the plain FP64
+form is timed beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "setup+PCG seconds to rel. residual 1e-8, chosen vs plain FP64 form; % roofline"
+TOL = 1e-8
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64, nominal (used only for "alu"-bound kernels)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["grf512", "channels64"], default="grf512")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-subdomains", type=int, default=4)
+    ap.add_argument("--forms", choices=["both", "chosen"], default="both",
+                    help="chosen: time only the chosen form (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    return ap.parse_args()
+
+
+def workload(name, seed):
+    import synthetic_inputs as si
+    return si.grf512(seed=seed) if name == "grf512" else si.channels64(seed=seed)
+
+
+# ------------------------------------------------------------------ oracle sample
+def oracle_sample(wname, k, threads):
+    """Time the CPU oracle on a bounded sample of the workload.
+
+    The sample is the fine-level local set-up of k subdomains of the workload
+    by the oracle as it stands (local Neumann assembly, partition of unity,
+    B = X Abar X, dense Cholesky of the Dirichlet matrix and of Abar + B, and
+    the spectral transformation C = L^{-1} B L^{-T}), i.e. everything of the
+    oracle's local set-up except the cyclic Jacobi iteration on C, which alone
+    takes ~5 min per 1369-node subdomain on one core.  Returns seconds for the
+    sample and the extrapolation to all fine subdomains on `threads` cores.
+    """
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import decomposition as dd
+    from oracle import fem, linalg
+    w = workload(wname, 0)
+    mesh = fem.Mesh(w.n, w.dirichlet_faces)
+    kap = w.coefficient()
+    t0 = time.perf_counter()
+    dec = dd.Decomposition(mesh, w.parts, w.overlap, 2, w.group)
+    chis, _ = dec.partition_of_unity()
+    A = fem.assemble_system(mesh, kap)
+    n2u = mesh.node_to_unknown()
+    t_global = time.perf_counter() - t0
+    P = len(dec.fine)
+    idx = [int(v) for v in np.linspace(0, P - 1, k)]
+
+    def local(i):
+        s = dec.fine[i]
+        nn = s.neumann_nodes()
+        Ab = fem.assemble_neumann(mesh, kap, s.element_mask)[nn][:, nn].toarray()
+        B = chis[i][:, None] * Ab * chis[i][None, :]
+        du = n2u[s.dirichlet_nodes()]
+        linalg.cholesky(A[du][:, du].toarray())
+        L = linalg.cholesky(Ab + B)
+        T = linalg.forward(L, B)
+        linalg.forward(L, T.T)
+        return 0
+
+    t1 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(local, idx))
+    t_local = time.perf_counter() - t1
+    per_sub_core = t_local * min(threads, k) / k
+    full = t_global + per_sub_core * P / threads
+    return dict(sample_s=t_global + t_local, full_estimate_s=full, subdomains=k, total_subdomains=P,
+                cores=threads)
+
+
+def _cpu_worker(q, wname, k, threads):
+    try:
+        q.put(oracle_sample(wname, k, threads))
+    except Exception as e:  # pragma: no cover - reported in the JSON line
+        q.put({"error": repr(e)})
+
+
+def cpu_baseline_obj(res, wname):
+    if res is None or "error" in res:
+        return {"value": None, "unit": "s", "cores": None, "kind": "oracle",
+                "sample": "failed: %s" % (res or {}).get("error", "not run")}
+    return {
+        "value": round(res["full_estimate_s"], 3), "unit": "s", "cores": res["cores"], "kind": "oracle",
+        "sample": ("%s: oracle fine-level local set-up of %d of %d subdomains (Neumann/Dirichlet assembly, "
+                   "partition of unity, dense Cholesky of A_i and Abar_i+B_i, spectral transform) + global "
+                   "assembly, %.1f s measured, extrapolated to all subdomains on %d cores; excludes the "
+                   "oracle's Jacobi eigen-iteration (~5 min per subdomain per core), coarse levels and PCG, so "
+                   "the oracle's full step is much slower than this value")
+                  % (wname, res["subdomains"], res["total_subdomains"], res["sample_s"], res["cores"]),
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for k, nm in enumerate(names):
+                    if r[3 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import multiprocessing as mp
+    cpu_q = cpu_p = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ctx = mp.get_context("spawn")            # before any CUDA call
+        cpu_q = ctx.Queue()
+        threads = max(1, min(os.cpu_count() or 1, args.cpu_subdomains))
+        cpu_p = ctx.Process(target=_cpu_worker, args=(cpu_q, args.workload, args.cpu_subdomains, threads))
+        cpu_p.start()
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2106_06404_gb300 as pkg
+    from paper_2106_06404_gb300 import msdd
+
+    w = workload(args.workload, rank)
+    kap_np = w.coefficient()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        kappa = torch.tensor(kap_np, device=dev)                   # resident in HBM before timing
+        b = pkg.assemble_rhs(w.n, w.dirichlet_faces)
+
+        def step(precision, profile):
+            H = pkg.Hierarchy(w.n, kappa, w.parts, w.overlap, w.levels, w.group, w.nev_max, w.eta,
+                              dirichlet_faces=w.dirichlet_faces, precision=precision, profile=profile)
+            x, it, rel = H.solve(b, tol=TOL)
+            st = H.stats()
+            H.close()
+            return it, rel, st
+
+        def timed(precision, profile):
+            for _ in range(args.warmup):
+                step(precision, False)
+            times, its, stats = [], [], None
+            barrier()
+            l0 = msdd.kernel_launches()
+            for _ in range(args.steps):
+                flush.fill_(1.0)                                   # evict L2 between steps
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                it, rel, st = step(precision, profile)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+                its.append(it)
+                stats = st
+            launches = msdd.kernel_launches() - l0
+            barrier()
+            return times, its, stats, launches
+
+        with ClockSampler(local_rank) as clk:
+            t_chosen, it_chosen, st_chosen, launches = timed(1, True)
+        if args.forms == "both":
+            t_plain, it_plain, st_plain, _ = timed(0, False)
+        else:
+            t_plain, it_plain, st_plain = None, None, None
+
+        # end to end through host buffers: kappa and b copied in, x copied out
+        kap_pin = torch.tensor(kap_np).pin_memory()
+        b_host = b.cpu().numpy()
+        e2e_times = []
+        for k in range(0 if args.no_e2e else args.warmup + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            kd = kap_pin.to(dev, non_blocking=True)
+            H = pkg.Hierarchy(w.n, kd, w.parts, w.overlap, w.levels, w.group, w.nev_max, w.eta,
+                              dirichlet_faces=w.dirichlet_faces, precision=1)
+            x_host, it, rel = H.solve_host(b_host, tol=TOL)
+            H.close()
+            torch.cuda.synchronize(dev)
+            if k >= args.warmup:
+                e2e_times.append(time.perf_counter() - t0)
+
+    total = sum(t_chosen)
+    if dist is not None:
+        tt = torch.tensor([total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel family of the chosen form (live CUDA events)
+    prof = st_chosen["prof"]
+    fam = max(prof, key=lambda k: prof[k]["ms"])
+    pf = prof[fam]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    intensity = pf["flops"] / max(pf["bytes"], 1.0)
+    fp64_bound = fam.startswith("fine_gevp_update") or fam.startswith("fine_gevp_gram") or \
+        (fam.endswith("_solve") and st_chosen["precision"] == 0)
+    if fp64_bound:
+        achieved = pf["flops"] / (pf["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS_NOMINAL,
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS_NOMINAL, 4)}
+    else:
+        achieved = pf["bytes"] / (pf["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4)}
+    roof.update({"kernel": fam, "launches": pf["launches"], "avg_launch_ms": round(pf["ms"] / pf["launches"], 4),
+                 "algorithmic_bytes_per_launch": pf["bytes"] / pf["launches"],
+                 "algorithmic_flops_per_launch": pf["flops"] / pf["launches"],
+                 "arith_intensity_flop_per_byte": round(intensity, 3),
+                 "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
+                 "traffic": None, "share_of_step": round(pf["ms"] / 1e3 / (total / args.steps) / args.steps, 4)})
+
+    cpu = None
+    if cpu_p is not None:
+        try:
+            cpu = cpu_q.get(timeout=900)
+        except Exception as e:
+            cpu = {"error": repr(e)}
+        cpu_p.join(timeout=10)
+
+    n = st_chosen["n"]
+    e2e_val = statistics.mean(e2e_times) if e2e_times else None
+    line = {
+        "metric": METRIC,
+        "value": round(total / args.steps, 6),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 outer / f32 fine factors",
+        "data": "synthetic (seeded GRF x channels/inclusions, contrast 1e6)",
+        "config": {"workload": w.name, "n_elements": list(w.n), "unknowns": n, "subdomains": list(w.parts),
+                   "overlap": w.overlap, "levels": w.levels, "nev_max": w.nev_max, "eta": w.eta, "tol": TOL,
+                   "form": "chosen (precision=1)", "l2": "flushed between steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": it_chosen[-1],
+        "step_seconds": [round(t, 6) for t in t_chosen],
+        "setup_ms": round(st_chosen["setup_ms"], 3),
+        "solve_ms": round(st_chosen["solve_ms"], 3),
+        "phase_ms": [round(v, 3) for v in st_chosen["phase_ms"][:7]],
+        "level_dim": st_chosen["level_dim"],
+        "eig_iters_max": st_chosen["eig_iters_max"],
+        "plain_fp64": None if t_plain is None else {
+            "value": round(sum(t_plain) / args.steps, 6), "unit": "s", "iterations": it_plain[-1],
+            "setup_ms": round(st_plain["setup_ms"], 3), "solve_ms": round(st_plain["solve_ms"], 3),
+            "step_seconds": [round(t, 6) for t in t_plain]},
+        "speedup_chosen_vs_plain": None if t_plain is None else round(sum(t_plain) / max(total, 1e-12), 3),
+        "kernel_families_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "e2e": {"value": round(e2e_val, 6) if e2e_val else None, "unit": "s",
+                "h2d_bytes_per_step": int(kap_np.nbytes + n * 8), "d2h_bytes_per_step": int(n * 8)},
+        "gpu_launches": int(launches),
+        "cpu_baseline": cpu_baseline_obj(cpu, w.name) if cpu_p is not None else None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on a bounded sample per step (rank 0 only)."""
+    if rank != 0:
+        return
+    threads = max(1, min(os.cpu_count() or 1, args.cpu_subdomains))
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, 1, 1)
+    vals, samples = [], []
+    for _ in range(args.steps):
+        r = oracle_sample(args.workload, args.cpu_subdomains, threads)
+        vals.append(r["full_estimate_s"])
+        samples.append(r)
+    v = statistics.mean(vals)
+    w = workload(args.workload, 0)
+    cb = cpu_baseline_obj(samples[-1], w.name)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * v, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_elements": list(w.n), "subdomains": list(w.parts), "levels": w.levels},
+        "cpu_baseline": dict(cb, value=round(v, 3)),
+        "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * msdd: multilevel spectral domain decomposition on one GB300 GPU (sm_103a).
+ *
+ * C ABI of the library built from paper_2106_06404_gb300/csrc.  It solves the
+ * SPD system A x = b of the Q1 conforming finite element discretisation of
+ *     -div(K grad u) = f in Omega = (0,1)^d,  u = 0 on Gamma_D,  Neumann elsewhere
+ * (Section 3.4, Eq. ScalarBVP and the forms a_h, a_tau, l) with preconditioned
+ * CG (Section 5) and the additive multilevel spectral Schwarz preconditioner
+ *     B = sum_{l=1}^{L} sum_i R_{l,i}^T A_{l,i}^{-1} R_{l,i} + R_0^T A_0^{-1} R_0
+ * (Section 2.1, Eq. subspace_iteration and Eq. mlsdd), whose coarse spaces are
+ * spanned by the partition-of-unity weighted lowest eigenvectors of the local
+ * generalized eigenproblems (Section 2.3, Eq. theGEVP and Eq. coarse_space_def,
+ * right-hand side b^1 of Eq. cg_rhs_blf; coarse-level generating systems of
+ * Section 4.2).
+ *
+ * Conventions (all entry points):
+ *   - Pointers documented as "device" must point to memory of the current CUDA
+ *     device; "host" pointers to ordinary host memory.  The caller owns every
+ *     buffer it passes; the library owns the hierarchy and the band batches.
+ *   - Nothing throws across the ABI.  Every entry point returns an msdd_status;
+ *     on failure msdd_last_error() returns a message for the calling thread and
+ *     outputs are left unspecified unless stated otherwise.
+ *   - Unknowns are the mesh nodes not on a Dirichlet face, numbered
+ *     lexicographically (x fastest) within the box of such nodes.  Element
+ *     (ex, ey, ez) has index ex + nx * (ey + ny * ez).
+ *   - Work is issued on options.stream (a cudaStream_t; NULL = legacy default
+ *     stream).  Calls return after the work has completed.
+ */
+#ifndef MSDD_H
+#define MSDD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum msdd_status {
+    MSDD_OK = 0,
+    MSDD_ERR_INVALID_ARG = -1,        /* a size, pointer or option is out of range          */
+    MSDD_ERR_NOT_SPD = -2,            /* a local factorisation met a non-positive pivot      */
+    MSDD_ERR_NO_CONVERGENCE = -3,     /* CG reached maxit (x holds the last iterate)          */
+    MSDD_ERR_EIG_NO_CONVERGENCE = -4, /* subspace iteration reached eig_maxit (set-up kept)   */
+    MSDD_ERR_OOM = -5,                /* device allocation failed                            */
+    MSDD_ERR_CUDA = -6,               /* any other CUDA runtime error                        */
+    MSDD_ERR_UNSUPPORTED = -7         /* valid request outside what this build implements    */
+} msdd_status;
+
+/* Structured Q1 mesh of n[0] x n[1] (x n[2]) equal elements on the unit box.
+ * dirichlet_faces: bit 2d is the face x_d = 0, bit 2d+1 the face x_d = 1. */
+typedef struct msdd_mesh {
+    int dim;                   /* 2 or 3 */
+    int n[3];                  /* elements per axis (n[2] ignored in 2D) */
+    unsigned dirichlet_faces;  /* at least one bit set (A must be SPD) */
+} msdd_mesh;
+
+/* Coefficient K, constant per element (Section 3.4: K symmetric positive definite). */
+typedef struct msdd_coeff {
+    int kind;            /* 0: scalar, one double per element;
+                            1: tensor, per element (kxx, kyy, kxy) in 2D or
+                               (kxx, kyy, kzz, kyz, kxz, kxy) in 3D */
+    const double* data;  /* device, element-major; read during msdd_setup and
+                            by every solve (must stay valid while the hierarchy lives) */
+} msdd_coeff;
+
+/* Hierarchical box decomposition (Section 2.2).  The fine level splits the
+ * elements into parts[d] blocks per axis (floor(N/P) elements, the first
+ * N mod P blocks one more), each extended by `overlap` >= 1 element layers.
+ * Each coarser level groups group[d] children per axis without overlap.
+ * levels = L + 1 counts the coarsest (single, direct) level. */
+typedef struct msdd_decomp {
+    int parts[3];
+    int overlap;
+    int levels;          /* 2 or 3 in this build */
+    int group[3];        /* children per coarse subdomain per axis (levels == 3) */
+} msdd_decomp;
+
+/* Coarse space selection (Eq. coarse_space_def, Section 5.1.1): on every level
+ * each subdomain contributes its m = min(nev_max, #{lambda < eta}) lowest
+ * eigenvectors. */
+typedef struct msdd_spectral {
+    int nev_max;         /* 1 .. 24 */
+    double eta;          /* > 0 */
+} msdd_spectral;
+
+typedef struct msdd_options {
+    int precision;       /* 0: FP64 everywhere ("plain");
+                            1: FP32 fine-level factors and solves, FP64 elsewhere ("chosen") */
+    int block_p;         /* subspace block size; 0 selects min(nev_max + 8, 32) */
+    int eig_maxit;       /* subspace iterations per level (default 200) */
+    double sigma;        /* shift of K = Abar + sigma B (default 1e-2) */
+    double eig_tol;      /* eigen-residual tolerance (default 1e-6) */
+    double reg_tol;      /* null-pivot threshold for coarse generating systems (default 1e-10) */
+    unsigned long long seed;  /* start vectors of the subspace iteration */
+    void* stream;        /* cudaStream_t */
+    int profile;         /* 1: time kernel families with CUDA events (see msdd_stats.prof) */
+} msdd_options;
+
+/* Per kernel family timing, filled when options.profile = 1.  bytes and flops
+ * are the algorithmic amounts (band storage, not the padded tile layout) that
+ * the launches were given; ms is the sum of CUDA-event durations. */
+typedef struct msdd_kernel_prof {
+    char name[32];
+    int launches;
+    double ms;
+    double bytes;
+    double flops;
+} msdd_kernel_prof;
+
+#define MSDD_MAX_PROF 12
+
+#define MSDD_MAX_LEVELS 8
+
+typedef struct msdd_stats {
+    long long n;                              /* unknowns */
+    int levels;
+    int precision;
+    int subdomains[MSDD_MAX_LEVELS];          /* P_l (index = level, 0 = coarsest) */
+    long long level_dim[MSDD_MAX_LEVELS];     /* dim V_{h,l} */
+    int eig_iters_max[MSDD_MAX_LEVELS];       /* subspace iterations on level l */
+    int eig_iters_min[MSDD_MAX_LEVELS];
+    int eig_unconverged[MSDD_MAX_LEVELS];     /* reached eig_maxit */
+    int eig_at_floor[MSDD_MAX_LEVELS];        /* stopped at their residual noise floor (below
+                                                 sqrt(eig_tol), no progress in 10 iterations) */
+    int null_pivots[MSDD_MAX_LEVELS];         /* regularised pivots (Section 4.2) */
+    int m_min[MSDD_MAX_LEVELS], m_max[MSDD_MAX_LEVELS];
+    double setup_ms;                          /* wall time of msdd_setup */
+    double phase_ms[8];                       /* 0 decomposition, 1 Dirichlet factor, 2 shifted
+                                                 Neumann factor, 3 fine eigensolve, 4 coarse
+                                                 Galerkin, 5 coarse eigensolve, 6 coarse factors */
+    int pcg_iterations;                       /* of the last solve */
+    double pcg_rel_residual;                  /* recursive residual / ||b|| */
+    double solve_ms;
+    size_t device_bytes;                      /* held by the hierarchy */
+    int nprof;
+    msdd_kernel_prof prof[MSDD_MAX_PROF];     /* accumulated over set-up and solves */
+} msdd_stats;
+
+typedef struct msdd_hierarchy msdd_hierarchy;   /* opaque, library-owned */
+
+/* Fill *opt with the defaults listed above.  Never fails for non-NULL opt. */
+msdd_status msdd_default_options(msdd_options* opt);
+
+/* Number of unknowns of the mesh, or -1 if the mesh is invalid. */
+long long msdd_num_unknowns(const msdd_mesh* mesh);
+
+/* Build the hierarchy (Section 2.3 construction, recursive over levels):
+ * local Dirichlet factorisations, local GEVPs by batched subspace iteration,
+ * coarse Galerkin matrices, coarse GEVPs on generating systems and the
+ * coarsest factorisation.  On success *out owns all device memory it needs. */
+msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp,
+                       const msdd_spectral* spectral, const msdd_options* options, msdd_hierarchy** out);
+
+/* Preconditioned CG, x^0 = 0, stopped when ||b - A x^m||_2 < tol ||b||_2
+ * (recursive residual; Section 5).  b, x: device, n doubles.  Returns
+ * MSDD_ERR_NO_CONVERGENCE if maxit iterations did not suffice. */
+msdd_status msdd_solve(msdd_hierarchy* h, const double* b, double tol, int maxit, double* x, int* iterations,
+                       double* rel_residual);
+
+/* Same with host buffers b, x (n doubles each); copies are part of the call. */
+msdd_status msdd_solve_host(msdd_hierarchy* h, const double* b, double tol, int maxit, double* x,
+                            int* iterations, double* rel_residual);
+
+/* z = B r for the multilevel preconditioner (device, n doubles each). */
+msdd_status msdd_apply_preconditioner(msdd_hierarchy* h, const double* r, double* z);
+
+/* y = A x (device, n doubles each). */
+msdd_status msdd_apply_operator(msdd_hierarchy* h, const double* x, double* y);
+
+/* Load vector l(v) = int f v for constant f (device, n doubles). */
+msdd_status msdd_assemble_rhs(const msdd_mesh* mesh, double f, double* b, void* stream);
+
+msdd_status msdd_get_stats(const msdd_hierarchy* h, msdd_stats* out);
+
+/* Ritz values of subdomain `subdomain` on level `level` (1 <= level <= L),
+ * ascending: writes min(cap, block size) values to out (host), the block size
+ * to *count and the number of selected eigenpairs m to *selected. */
+msdd_status msdd_get_eigenvalues(const msdd_hierarchy* h, int level, int subdomain, double* out, int cap,
+                                 int* count, int* selected);
+
+/* Eigen-residuals |Abar x_k - theta_k B x_k| / ((theta_k + sigma) |B x_k|) of
+ * the Ritz pairs of that subdomain (host out, min(cap, block size) values),
+ * and whether its subspace iteration met the tolerance (*converged = 1). */
+msdd_status msdd_get_eigen_residuals(const msdd_hierarchy* h, int level, int subdomain, double* out, int cap,
+                                     int* converged);
+
+/* Fine-level coarse basis function values phi_{i,k} = e chi_i w_{i,k}
+ * (Eq. coarse_space_def) of subdomain i as a dense n x m block (host,
+ * row-major, unknown-major), m = selected count; *m_out receives m. */
+msdd_status msdd_get_fine_basis(const msdd_hierarchy* h, int subdomain, double* out, long long cap, int* m_out);
+
+void msdd_destroy(msdd_hierarchy* h);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (a replayed CUDA graph counts the kernels it holds).  Not thread-safe. */
+long long msdd_kernel_launches(void);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* msdd_last_error(void);
+
+/* ---- batched SPD (semi-definite with reg_tol > 0) band solver ------------
+ * The building block of the local solves (Section 4.3 uses a sparse direct
+ * solver per subdomain): batch matrices, matrix i of order n[i] <= nmax, given
+ * dense row-major at A + i * nmax * nmax (device, only the lower triangle
+ * inside the band |r - c| <= bw is read).  Factorised as L D L^T in tiles.
+ * reg_tol > 0 turns pivots d_k <= reg_tol * A_kk into null pivots (D^{-1}_k = 0)
+ * as in Section 4.2; otherwise a non-positive pivot is reported in status[i]
+ * (host, may be NULL) as row+1 and the call returns MSDD_ERR_NOT_SPD. */
+typedef struct msdd_band_batch msdd_band_batch;
+msdd_status msdd_band_factor(int batch, const int* n, int nmax, int bw, const double* A, int precision,
+                             double reg_tol, void* stream, msdd_band_batch** out, int* status);
+/* Solve A_i X_i = B_i in place for every i; X (device) holds matrix i's
+ * right-hand sides at X + i * nmax * nrhs, row-major n[i] x nrhs, nrhs <= 32.
+ * Uses a library-allocated staging buffer. */
+msdd_status msdd_band_solve(const msdd_band_batch* bb, int nrhs, double* X, void* stream);
+void msdd_band_destroy(msdd_band_batch* bb);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSDD_H */

@@ -1,0 +1,8 @@
+"""GB300-native multilevel spectral domain decomposition (hot path).
+
+The CUDA library (csrc/, built into lib/libmsdd.so by build.py) implements
+the set-up and the preconditioned CG solve behind the C ABI of
+include/msdd.h; msdd.py is the ctypes binding.
+"""
+from . import msdd  # noqa: F401
+from .msdd import Hierarchy, BandBatch, MsddError, assemble_rhs, num_unknowns  # noqa: F401

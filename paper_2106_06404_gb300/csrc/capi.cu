@@ -1,0 +1,369 @@
+// C ABI of the msdd library (declarations and contracts in include/msdd.h).
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "hierarchy.cuh"
+
+struct msdd_hierarchy {
+    msdd::Hierarchy h;
+};
+
+struct msdd_band_batch {
+    msdd::TileBatch tb;
+    int nmax = 0;
+    std::vector<int> n;
+    msdd::DevBuf<long long> d_src, d_dst;
+    msdd::DevBuf<int> d_len;
+};
+
+namespace msdd {
+long long& kernel_launch_counter() {
+    static long long counter = 0;
+    return counter;
+}
+}  // namespace msdd
+
+namespace {
+
+thread_local std::string g_last_error;
+
+msdd_status fail(msdd_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+template <class F>
+msdd_status guarded(F&& f) {
+    try {
+        g_last_error.clear();
+        return f();
+    } catch (const msdd::MsddError& e) {
+        return fail(e.status, e.what());
+    } catch (const msdd::CudaError& e) {
+        std::string m = e.what();
+        if (m.find("out of memory") != std::string::npos) return fail(MSDD_ERR_OOM, m);
+        return fail(MSDD_ERR_CUDA, m);
+    } catch (const std::bad_alloc&) {
+        return fail(MSDD_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(MSDD_ERR_CUDA, e.what());
+    }
+}
+
+bool mesh_ok(const msdd_mesh* m) {
+    if (!m || (m->dim != 2 && m->dim != 3)) return false;
+    for (int d = 0; d < m->dim; ++d)
+        if (m->n[d] < 1 || m->n[d] > (1 << 20)) return false;
+    unsigned mask = m->dim == 2 ? 0xFu : 0x3Fu;
+    if ((m->dirichlet_faces & mask) == 0) return false;
+    if (m->dirichlet_faces & ~mask) return false;
+    for (int d = 0; d < m->dim; ++d)
+        if (((m->dirichlet_faces >> (2 * d)) & 3u) == 3u && m->n[d] < 2) return false;
+    return true;
+}
+
+long long unknowns_of(const msdd_mesh* m) {
+    long long n = 1;
+    for (int d = 0; d < m->dim; ++d) {
+        int lo = (m->dirichlet_faces >> (2 * d)) & 1 ? 1 : 0;
+        int hi = (m->dirichlet_faces >> (2 * d + 1)) & 1 ? m->n[d] - 1 : m->n[d];
+        n *= (hi - lo + 1);
+    }
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* msdd_last_error(void) { return g_last_error.c_str(); }
+
+msdd_status msdd_default_options(msdd_options* opt) {
+    if (!opt) return fail(MSDD_ERR_INVALID_ARG, "options pointer is NULL");
+    opt->precision = 0;
+    opt->block_p = 0;
+    opt->eig_maxit = 200;
+    opt->sigma = 1e-2;
+    opt->eig_tol = 1e-6;
+    opt->reg_tol = 1e-10;
+    opt->seed = 12345;
+    opt->stream = nullptr;
+    opt->profile = 0;
+    return MSDD_OK;
+}
+
+long long msdd_num_unknowns(const msdd_mesh* mesh) {
+    if (!mesh_ok(mesh)) return -1;
+    return unknowns_of(mesh);
+}
+
+msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp,
+                       const msdd_spectral* spectral, const msdd_options* options, msdd_hierarchy** out) {
+    return guarded([&]() -> msdd_status {
+        if (!out) return fail(MSDD_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        if (!mesh_ok(mesh)) return fail(MSDD_ERR_INVALID_ARG, "invalid mesh (dim, sizes or Dirichlet faces)");
+        if (!coeff || !coeff->data || (coeff->kind != 0 && coeff->kind != 1))
+            return fail(MSDD_ERR_INVALID_ARG, "invalid coefficient");
+        if (!decomp || !spectral) return fail(MSDD_ERR_INVALID_ARG, "decomposition or spectral options NULL");
+        if (decomp->levels < 2) return fail(MSDD_ERR_INVALID_ARG, "levels must be >= 2");
+        if (decomp->levels > 3) return fail(MSDD_ERR_UNSUPPORTED, "this build supports 2 or 3 levels");
+        if (decomp->overlap < 1) return fail(MSDD_ERR_INVALID_ARG, "overlap must be >= 1 (partition of unity)");
+        for (int d = 0; d < mesh->dim; ++d) {
+            if (decomp->parts[d] < 1 || decomp->parts[d] > mesh->n[d])
+                return fail(MSDD_ERR_INVALID_ARG, "parts must be in 1..n per axis");
+            if (decomp->levels == 3 && decomp->group[d] < 1)
+                return fail(MSDD_ERR_INVALID_ARG, "group must be >= 1 per axis");
+        }
+        if (spectral->nev_max < 1 || spectral->nev_max > 24 || !(spectral->eta > 0.0))
+            return fail(MSDD_ERR_INVALID_ARG, "nev_max must be in 1..24 and eta > 0");
+        msdd_options opt;
+        msdd_default_options(&opt);
+        if (options) opt = *options;
+        if (opt.precision != 0 && opt.precision != 1) return fail(MSDD_ERR_INVALID_ARG, "precision must be 0 or 1");
+        if (opt.block_p < 0 || opt.block_p > msdd::PMAX) return fail(MSDD_ERR_INVALID_ARG, "block_p out of range");
+        if (opt.block_p > 0 && opt.block_p <= spectral->nev_max)
+            return fail(MSDD_ERR_INVALID_ARG, "block_p must exceed nev_max");
+        if (!(opt.sigma > 0.0) || !(opt.eig_tol > 0.0) || opt.eig_maxit < 1 || opt.reg_tol < 0.0)
+            return fail(MSDD_ERR_INVALID_ARG, "invalid eigensolver options");
+        msdd_hierarchy* H = new msdd_hierarchy();
+        H->h.opt = opt;
+        H->h.spec = *spectral;
+        H->h.dec = *decomp;
+        H->h.st = (cudaStream_t)opt.stream;
+        try {
+            H->h.setup(*mesh, *coeff);
+        } catch (...) {
+            delete H;
+            throw;
+        }
+        *out = H;
+        if (H->h.stats.eig_unconverged[H->h.L] || (H->h.levels == 3 && H->h.stats.eig_unconverged[1])) {
+            g_last_error = "subspace iteration reached eig_maxit on some subdomains (hierarchy kept)";
+            return MSDD_ERR_EIG_NO_CONVERGENCE;
+        }
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_solve(msdd_hierarchy* h, const double* b, double tol, int maxit, double* x, int* iterations,
+                       double* rel_residual) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !b || !x) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        if (!(tol > 0.0) || maxit < 1) return fail(MSDD_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 1");
+        int it = h->h.solve(b, tol, maxit, x, rel_residual);
+        if (iterations) *iterations = it < 0 ? -it : it;
+        if (it < 0) return fail(MSDD_ERR_NO_CONVERGENCE, "CG reached maxit");
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_solve_host(msdd_hierarchy* h, const double* b, double tol, int maxit, double* x, int* iterations,
+                            double* rel_residual) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !b || !x) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        long long n = h->h.nun;
+        msdd::DevBuf<double> db(n), dx(n);
+        cudaStream_t st = h->h.st;
+        MSDD_CUDA(cudaMemcpyAsync(db.p, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        msdd_status s = msdd_solve(h, db.p, tol, maxit, dx.p, iterations, rel_residual);
+        if (s != MSDD_OK && s != MSDD_ERR_NO_CONVERGENCE) return s;
+        MSDD_CUDA(cudaMemcpyAsync(x, dx.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        return s;
+    });
+}
+
+msdd_status msdd_apply_preconditioner(msdd_hierarchy* h, const double* r, double* z) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !r || !z) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        h->h.apply_prec(r, z, nullptr);
+        MSDD_CUDA(cudaStreamSynchronize(h->h.st));
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_apply_operator(msdd_hierarchy* h, const double* x, double* y) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !x || !y) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        msdd::apply_global(h->h.g, x, y, h->h.st);
+        MSDD_CUDA(cudaStreamSynchronize(h->h.st));
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_assemble_rhs(const msdd_mesh* mesh, double f, double* b, void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!mesh_ok(mesh) || !b) return fail(MSDD_ERR_INVALID_ARG, "invalid mesh or NULL b");
+        msdd::Geom g{};
+        g.dim = mesh->dim;
+        for (int d = 0; d < 3; ++d) {
+            g.n[d] = d < mesh->dim ? mesh->n[d] : 1;
+            if (d < mesh->dim) {
+                g.ulo[d] = (mesh->dirichlet_faces >> (2 * d)) & 1 ? 1 : 0;
+                g.uhi[d] = (mesh->dirichlet_faces >> (2 * d + 1)) & 1 ? g.n[d] - 1 : g.n[d];
+            }
+            g.ushape[d] = g.uhi[d] - g.ulo[d] + 1;
+        }
+        msdd::load_vector(g, f, b, (cudaStream_t)stream);
+        MSDD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_get_stats(const msdd_hierarchy* h, msdd_stats* out) {
+    if (!h || !out) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+    *out = h->h.stats;
+    return MSDD_OK;
+}
+
+msdd_status msdd_get_eigenvalues(const msdd_hierarchy* h, int level, int subdomain, double* out, int cap, int* count,
+                                 int* selected) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !out || cap < 0) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        const msdd::GevpBatch* gb = nullptr;
+        if (level == h->h.L) gb = &h->h.fge;
+        else if (h->h.levels == 3 && level == 1) gb = &h->h.mge;
+        else return fail(MSDD_ERR_INVALID_ARG, "level has no eigenproblems");
+        if (subdomain < 0 || subdomain >= gb->P) return fail(MSDD_ERR_INVALID_ARG, "subdomain out of range");
+        int p = gb->p[subdomain];
+        std::vector<double> th(msdd::PMAX);
+        MSDD_CUDA(cudaMemcpy(th.data(), gb->theta.p + (size_t)subdomain * msdd::PMAX, msdd::PMAX * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+        int mval = 0;
+        MSDD_CUDA(cudaMemcpy(&mval, gb->m.p + subdomain, sizeof(int), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < std::min(cap, p); ++k) out[k] = th[k];
+        if (count) *count = p;
+        if (selected) *selected = mval;
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_get_eigen_residuals(const msdd_hierarchy* h, int level, int subdomain, double* out, int cap,
+                                     int* converged) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !out || cap < 0) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        const msdd::GevpBatch* gb = nullptr;
+        if (level == h->h.L) gb = &h->h.fge;
+        else if (h->h.levels == 3 && level == 1) gb = &h->h.mge;
+        else return fail(MSDD_ERR_INVALID_ARG, "level has no eigenproblems");
+        if (subdomain < 0 || subdomain >= gb->P) return fail(MSDD_ERR_INVALID_ARG, "subdomain out of range");
+        std::vector<double> r(msdd::PMAX);
+        MSDD_CUDA(cudaMemcpy(r.data(), gb->res.p + (size_t)subdomain * msdd::PMAX, msdd::PMAX * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+        int dn = 0;
+        MSDD_CUDA(cudaMemcpy(&dn, gb->done.p + subdomain, sizeof(int), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < std::min(cap, gb->p[subdomain]); ++k) out[k] = r[k];
+        if (converged) *converged = (dn == 1 || dn == 3) ? 1 : 0;
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_get_fine_basis(const msdd_hierarchy* h, int subdomain, double* out, long long cap, int* m_out) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !out) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        const msdd::Hierarchy& H = h->h;
+        if (subdomain < 0 || subdomain >= H.Pf) return fail(MSDD_ERR_INVALID_ARG, "subdomain out of range");
+        int m = H.fm[subdomain];
+        if (m_out) *m_out = m;
+        if (cap < H.nun * (long long)m) return fail(MSDD_ERR_INVALID_ARG, "output too small (n * m doubles)");
+        const msdd::ProbBox& b = H.fboxes[subdomain];
+        int nd = msdd::box_size(b.dlo, b.dhi, H.g.dim);
+        std::vector<double> blk((size_t)nd * H.ldphi);
+        MSDD_CUDA(cudaMemcpy(blk.data(), H.Phi.p + H.phioff[subdomain], blk.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+        std::fill(out, out + H.nun * m, 0.0);
+        for (int r = 0; r < nd; ++r) {
+            int x[3];
+            msdd::box_coords(r, b.dlo, b.dhi, H.g.dim, x);
+            long long u = msdd::unknown_index(H.g, x);
+            for (int k = 0; k < m; ++k) out[u * m + k] = blk[(size_t)r * H.ldphi + k];
+        }
+        return MSDD_OK;
+    });
+}
+
+void msdd_destroy(msdd_hierarchy* h) { delete h; }
+
+long long msdd_kernel_launches(void) { return msdd::kernel_launch_counter(); }
+
+msdd_status msdd_band_factor(int batch, const int* n, int nmax, int bw, const double* A, int precision,
+                             double reg_tol, void* stream, msdd_band_batch** out, int* status) {
+    return guarded([&]() -> msdd_status {
+        if (!out) return fail(MSDD_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        if (batch < 1 || !n || !A || nmax < 1 || bw < 0 || (precision != 0 && precision != 1) || reg_tol < 0.0)
+            return fail(MSDD_ERR_INVALID_ARG, "invalid band batch arguments");
+        std::vector<int> nv(n, n + batch);
+        for (int v : nv)
+            if (v < 1 || v > nmax) return fail(MSDD_ERR_INVALID_ARG, "n[i] must be in 1..nmax");
+        cudaStream_t st = (cudaStream_t)stream;
+        msdd_band_batch* bb = new msdd_band_batch();
+        try {
+            bb->nmax = nmax;
+            bb->n = nv;
+            std::vector<int> bws(batch, bw);
+            bb->tb.layout(nv, bws, precision, st);
+            std::vector<long long> so(batch);
+            std::vector<int> ld(batch, nmax);
+            for (int i = 0; i < batch; ++i) so[i] = (long long)i * nmax * nmax;
+            msdd::DevBuf<long long> d_so;
+            d_so.upload(so, st);
+            msdd::DevBuf<int> d_ld;
+            d_ld.upload(ld, st);
+            // only the lower band |r - c| <= bw is copied into the tiles
+            msdd::tile_from_dense(bb->tb, A, d_so.p, d_ld.p, st);
+            msdd::tile_factor(bb->tb, reg_tol, st);
+            std::vector<int> stv = bb->tb.d_status.download(st);
+            bool bad = false;
+            for (int i = 0; i < batch; ++i) {
+                if (status) status[i] = stv[i];
+                bad = bad || stv[i] != 0;
+            }
+            MSDD_CUDA(cudaStreamSynchronize(st));
+            if (bad) {
+                delete bb;
+                return fail(MSDD_ERR_NOT_SPD, "non-positive pivot (see status)");
+            }
+        } catch (...) {
+            delete bb;
+            throw;
+        }
+        *out = bb;
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_band_solve(const msdd_band_batch* bb, int nrhs, double* X, void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!bb || !X || nrhs < 1 || nrhs > msdd::PMAX) return fail(MSDD_ERR_INVALID_ARG, "invalid band solve arguments");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int P = bb->tb.P;
+        msdd::DevBuf<double> stage((size_t)bb->tb.total_rows * nrhs);
+        stage.zero(st);
+        std::vector<long long> so(P), dof(P);
+        std::vector<int> len(P);
+        int maxlen = 0;
+        for (int i = 0; i < P; ++i) {
+            so[i] = (long long)i * bb->nmax * nrhs;
+            dof[i] = bb->tb.roff[i] * nrhs;
+            len[i] = bb->n[i] * nrhs;
+            maxlen = std::max(maxlen, len[i]);
+        }
+        msdd::DevBuf<long long> d_so, d_do;
+        msdd::DevBuf<int> d_len;
+        d_so.upload(so, st);
+        d_do.upload(dof, st);
+        d_len.upload(len, st);
+        msdd::segment_copy(d_so.p, d_do.p, d_len.p, P, maxlen, X, stage.p, 0, nullptr, st);
+        msdd::tile_solve(bb->tb, stage.p, nrhs, nrhs, nullptr, st);
+        msdd::segment_copy(d_do.p, d_so.p, d_len.p, P, maxlen, stage.p, X, 0, nullptr, st);
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        return MSDD_OK;
+    });
+}
+
+void msdd_band_destroy(msdd_band_batch* bb) { delete bb; }
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// Coarse-level assembly, batched small GEMMs and preconditioner vector kernels.
+#include "coarse.cuh"
+
+namespace msdd {
+
+namespace {
+
+__global__ void k_block_sum(const SumItem* __restrict__ items, const long long* __restrict__ contrib,
+                            const double* __restrict__ G, double* __restrict__ dst) {
+    const SumItem it = items[blockIdx.x];
+    const int n = it.rows * it.cols;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        double v = 0.0;
+        for (int c = it.cbeg; c < it.cend; ++c) v += G[contrib[c] + e];
+        dst[it.doff + (long long)(e / it.cols) * it.ld + e % it.cols] = v;
+    }
+}
+
+constexpr int GT = 32;
+
+__global__ void __launch_bounds__(256) k_gemm_batched(const GemmItem* __restrict__ items, int transA, int transB,
+                                                      double alpha, const double* __restrict__ A,
+                                                      const double* __restrict__ B, double beta,
+                                                      double* __restrict__ C, const int* __restrict__ gdone) {
+    __shared__ double sA[GT][GT + 1], sB[GT][GT + 1];
+    if (gdone && *gdone) return;
+    const GemmItem it = items[blockIdx.z];
+    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+    if (row0 >= it.m || col0 >= it.n) return;
+    const int t = threadIdx.x;
+    const int r = t >> 3, cb = t & 7;
+    double acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < it.k; k0 += GT) {
+        for (int e = t; e < GT * GT; e += 256) {
+            int a = e / GT, b = e % GT;       // sA[a = row][b = k], sB[a = k][b = col]
+            int gr = row0 + a, gk = k0 + b;
+            double va = 0.0;
+            if (gr < it.m && gk < it.k)
+                va = transA ? A[it.aoff + (long long)gk * it.lda + gr] : A[it.aoff + (long long)gr * it.lda + gk];
+            sA[a][b] = va;
+            int bk = k0 + a, bc = col0 + b;
+            double vb = 0.0;
+            if (bk < it.k && bc < it.n)
+                vb = transB ? B[it.boff + (long long)bc * it.ldb + bk] : B[it.boff + (long long)bk * it.ldb + bc];
+            sB[a][b] = vb;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < GT; ++k) {
+            double a = sA[r][k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += a * sB[k][cb + 8 * q];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int gr = row0 + r, gc = col0 + cb + 8 * q;
+        if (gr < it.m && gc < it.n) {
+            double* dst = C + it.coff + (long long)gr * it.ldc + gc;
+            *dst = alpha * acc[q] + (beta != 0.0 ? beta * *dst : 0.0);
+        }
+    }
+}
+
+__global__ void k_dense_shift(const double* __restrict__ A, double* __restrict__ Kd, const long long* __restrict__ aoff,
+                              const int* __restrict__ n_, const int* __restrict__ nown_, double sigma) {
+    const int i = blockIdx.y;
+    const int n = n_[i], nown = nown_[i];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        int a = (int)(e / n), b = (int)(e % n);
+        double v = A[aoff[i] + e];
+        if (a < nown && b < nown) v *= 1.0 + sigma;
+        Kd[aoff[i] + e] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fine_gather_restrict(
+    Geom g, const ProbBox* __restrict__ fine, const long long* __restrict__ droff, const int* __restrict__ dK,
+    const double* __restrict__ r, double* __restrict__ rhs, const double* __restrict__ Phi,
+    const long long* __restrict__ phioff, int ldphi, const int* __restrict__ m_, const long long* __restrict__ c1off,
+    double* __restrict__ r1, const int* __restrict__ done) {
+    __shared__ double red[PMAX][8];
+    if (done && *done) return;
+    const int j = blockIdx.x;
+    const ProbBox pb = fine[j];
+    const int n = box_size(pb.dlo, pb.dhi, g.dim);
+    const int rows = dK[j] * NB;
+    const int m = m_[j];
+    const int t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    double acc[PMAX];
+#pragma unroll
+    for (int k = 0; k < PMAX; ++k) acc[k] = 0.0;
+    for (int rr = t; rr < rows; rr += blockDim.x) {
+        double v = 0.0;
+        if (rr < n) {
+            int x[3];
+            box_coords(rr, pb.dlo, pb.dhi, g.dim, x);
+            v = r[unknown_index(g, x)];
+            const double* ph = Phi + phioff[j] + (long long)rr * ldphi;
+#pragma unroll
+            for (int k = 0; k < PMAX; ++k)
+                if (k < m) acc[k] += ph[k] * v;
+        }
+        rhs[droff[j] + rr] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < PMAX; ++k) {
+        if (k >= m) break;
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (t < m) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[t][w];
+        r1[c1off[j] + t] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fine_combine(
+    Geom g, CombineMaps cm, const ProbBox* __restrict__ fine, const long long* __restrict__ droff,
+    const double* __restrict__ y, const double* __restrict__ Phi, const long long* __restrict__ phioff, int ldphi,
+    const int* __restrict__ m_, const long long* __restrict__ c1off, const double* __restrict__ z1,
+    double* __restrict__ z, const double* __restrict__ r, double* __restrict__ partial, long long nun,
+    const int* __restrict__ done) {
+    __shared__ double red[256];
+    if (done && *done) return;
+    double part = 0.0;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
+        int x[3] = {0, 0, 0};
+        long long rem = u;
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int d = 0; d < g.dim; ++d) {
+            x[d] = g.ulo[d] + (int)(rem % g.ushape[d]);
+            rem /= g.ushape[d];
+            lo[d] = cm.first[d][x[d]];
+            hi[d] = cm.last[d][x[d]];
+        }
+        double acc = 0.0;
+        for (int pz = lo[2]; pz <= hi[2]; ++pz)
+            for (int py = lo[1]; py <= hi[1]; ++py)
+                for (int px = lo[0]; px <= hi[0]; ++px) {
+                    int j = px + cm.parts[0] * (py + cm.parts[1] * pz);
+                    const ProbBox pb = fine[j];
+                    int loc = box_index(pb.dlo, pb.dhi, x, g.dim);
+                    double v = y[droff[j] + loc];
+                    const int m = m_[j];
+                    const double* ph = Phi + phioff[j] + (long long)loc * ldphi;
+                    const double* zz = z1 + c1off[j];
+                    for (int k = 0; k < m; ++k) v += ph[k] * zz[k];
+                    acc += v;
+                }
+        z[u] = acc;
+        part += acc * r[u];
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_segment_copy(const long long* __restrict__ so, const long long* __restrict__ dof,
+                               const int* __restrict__ len, const double* __restrict__ in, double* __restrict__ out,
+                               int mode, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int i = blockIdx.y;
+    const int n = len[i];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double v = in[so[i] + k];
+        if (mode) out[dof[i] + k] += v;
+        else out[dof[i] + k] = v;
+    }
+}
+
+__global__ void k_dot_partial(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                              double* __restrict__ partial) {
+    __shared__ double red[256];
+    double part = 0.0;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        part += x[u] * y[u];
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+}  // namespace
+
+void block_sum(const SumItem* d_items, int nitems, const long long* d_contrib, const double* G, double* dst,
+               cudaStream_t s) {
+    if (nitems == 0) return;
+    k_block_sum<<<nitems, 256, 0, s>>>(d_items, d_contrib, G, dst);
+    MSDD_LAUNCH_CHECK();
+}
+
+void gemm_batched(const GemmItem* d_items, int nitems, int transA, int transB, double alpha, const double* A,
+                  const double* B, double beta, double* C, int max_m, int max_n, cudaStream_t s,
+                  const int* gdone) {
+    if (nitems == 0 || max_m == 0 || max_n == 0) return;
+    dim3 grid(ceil_div(max_n, GT), ceil_div(max_m, GT), nitems);
+    k_gemm_batched<<<grid, 256, 0, s>>>(d_items, transA, transB, alpha, A, B, beta, C, gdone);
+    MSDD_LAUNCH_CHECK();
+}
+
+void fine_gather_restrict(const Geom& g, const ProbBox* d_fine, const long long* d_droff, const int* d_K,
+                          const double* r, double* rhs, const double* Phi, const long long* d_phioff, int ldphi,
+                          const int* d_m, const long long* d_c1off, double* r1, int P, const int* done,
+                          cudaStream_t s) {
+    if (P == 0) return;
+    k_fine_gather_restrict<<<P, 256, 0, s>>>(g, d_fine, d_droff, d_K, r, rhs, Phi, d_phioff, ldphi, d_m, d_c1off, r1,
+                                             done);
+    MSDD_LAUNCH_CHECK();
+}
+
+void fine_combine(const Geom& g, const CombineMaps& cm, const ProbBox* d_fine, const long long* d_droff,
+                  const double* y, const double* Phi, const long long* d_phioff, int ldphi, const int* d_m,
+                  const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
+                  int nblocks, const int* done, cudaStream_t s) {
+    long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    k_fine_combine<<<nblocks, 256, 0, s>>>(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off, z1, z, r,
+                                           partial, nun, done);
+    MSDD_LAUNCH_CHECK();
+}
+
+void segment_copy(const long long* d_src_off, const long long* d_dst_off, const int* d_len, int P, int maxlen,
+                  const double* in, double* out, int mode, const int* done, cudaStream_t s) {
+    if (P == 0 || maxlen == 0) return;
+    dim3 grid(std::max(1u, std::min(ceil_div(maxlen, 256), 64u)), P);
+    k_segment_copy<<<grid, 256, 0, s>>>(d_src_off, d_dst_off, d_len, in, out, mode, done);
+    MSDD_LAUNCH_CHECK();
+}
+
+int dot_blocks(long long n) { return (int)std::max(1u, std::min(ceil_div(n, 1024), 152u * 4)); }
+
+void dot_partial(const double* x, const double* y, long long n, double* partial, int nblocks, cudaStream_t s) {
+    k_dot_partial<<<nblocks, 256, 0, s>>>(x, y, n, partial);
+    MSDD_LAUNCH_CHECK();
+}
+
+void dense_shift(const double* Abar, double* Kd, const long long* d_aoff, const int* d_n, const int* d_nown,
+                 double sigma, int P, int nmax, cudaStream_t s) {
+    if (P == 0) return;
+    dim3 grid(std::max(1u, std::min(ceil_div((long long)nmax * nmax, 256), 256u)), P);
+    k_dense_shift<<<grid, 256, 0, s>>>(Abar, Kd, d_aoff, d_n, d_nown, sigma);
+    MSDD_LAUNCH_CHECK();
+}
+
+}  // namespace msdd
+
+namespace msdd {
+namespace {
+__global__ void k_copy_blocks(const CopyItem* __restrict__ items, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+    const CopyItem it = items[blockIdx.x];
+    for (int e = threadIdx.x; e < it.rows * it.cols; e += blockDim.x) {
+        int r = e / it.cols, c = e % it.cols;
+        dst[it.doff + (long long)r * it.ldd + c] = src[it.soff + (long long)r * it.lds + c];
+    }
+}
+}  // namespace
+void copy_blocks(const CopyItem* d_items, int nitems, const double* src, double* dst, cudaStream_t s) {
+    if (nitems == 0) return;
+    k_copy_blocks<<<nitems, 256, 0, s>>>(d_items, src, dst);
+    MSDD_LAUNCH_CHECK();
+}
+}  // namespace msdd

@@ -1,0 +1,919 @@
+// Set-up of the multilevel spectral DD hierarchy and the CG solve.
+//
+// Set-up follows the recursive construction of Section 2.3:
+//   fine level L: local Dirichlet matrices (Eq. dirichlet_space) factorised;
+//     local GEVPs (Eq. theGEVP with abar of Eq. locala_cg and b^1 of Eq.
+//     cg_rhs_blf) by batched subspace iteration; coarse basis
+//     phi = e chi w for the selected eigenpairs (Eq. coarse_space_def).
+//   level L-1: Galerkin matrix from patch Gram blocks (Section 4.1);
+//     with three levels, generating-system Neumann matrices (Section 4.2),
+//     regularised factorisation, dense GEVPs, next coarse basis.
+//   level 0: one direct factorisation.
+#include "hierarchy.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+namespace msdd {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+double ms_since(Clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+void split_axis(int N, int P, std::vector<int>& s, std::vector<int>& e) {
+    s.resize(P);
+    e.resize(P);
+    int base = N / P, rem = N % P, cur = 0;
+    for (int p = 0; p < P; ++p) {
+        s[p] = cur;
+        cur += base + (p < rem ? 1 : 0);
+        e[p] = cur;
+    }
+}
+
+int box_bandwidth(const int lo[3], const int hi[3], int dim) {
+    int w0 = hi[0] - lo[0] + 1;
+    if (dim == 2) return w0 + 1;
+    int w1 = hi[1] - lo[1] + 1;
+    return w0 * w1 + w0 + 1;
+}
+
+int host_box_size(const int lo[3], const int hi[3], int dim) { return box_size(lo, hi, dim); }
+
+template <typename T>
+DevBuf<T> upload_vec(const std::vector<T>& h, cudaStream_t s) {
+    DevBuf<T> d;
+    d.upload(h, s);
+    return d;
+}
+
+void check_status(const TileBatch& tb, cudaStream_t s, const char* what) {
+    std::vector<int> stv = tb.d_status.download(s);
+    for (int i = 0; i < (int)stv.size(); ++i)
+        if (stv[i] != 0)
+            throw MsddError(MSDD_ERR_NOT_SPD, std::string(what) + ": non-positive pivot in problem " +
+                                                  std::to_string(i) + " at row " + std::to_string(stv[i] - 1));
+}
+
+int sum_nreg(const TileBatch& tb, cudaStream_t s) {
+    std::vector<int> v = tb.d_nreg.download(s);
+    int t = 0;
+    for (int x : v) t += x;
+    return t;
+}
+
+// Subspace iteration driver; `apply(X, AX, BX, skip)` applies Abar and B.
+// `tag` names the kernel families for profiling; `apply_bytes`/`apply_flops`
+// are the algorithmic amounts of one operator application per problem.
+template <class Apply>
+void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, cudaStream_t st, Prof& prof, const std::string& tag,
+             double apply_bytes, double apply_flops) {
+    if (g.P == 0) return;
+    eig_init(g, ep.seed, st);
+    int pmax = 0;
+    for (int v : g.p) pmax = std::max(pmax, v);
+    // algorithmic amounts per problem: band solve (two sweeps) and the
+    // block-vector kernels
+    const double fsz = g.K.prec ? 4.0 : 8.0;
+    double solve_b = 0, solve_f = 0, vec_n = 0;
+    for (int i = 0; i < g.P; ++i) {
+        double n = g.K.n[i], b = g.K.b[i], p = g.p[i];
+        solve_b += 2.0 * n * (b + 1) * fsz + 4.0 * n * p * 8.0;
+        solve_f += 4.0 * n * b * p;
+        vec_n += n * p;
+    }
+    const double pavg = (double)pmax;
+    apply(g.X.p, g.AX.p, g.BX.p, (const int*)nullptr);
+    int active = g.P;
+    for (int it = 0; it < ep.maxit; ++it) {
+        bool first = it == 0;
+        const double fr = (double)active / g.P;
+        eig_form_rhs(g, ep.sigma, first, st);
+        prof.begin(tag + "_solve", st);
+        tile_solve(g.K, g.W.p, g.ldx, pmax, g.done.p, st);
+        prof.end(st, solve_b * fr, solve_f * fr);
+        if (g.knorm && !first) {
+            // test the current Ritz pairs before updating them
+            eig_form_y_knorm(g, ep.sigma, st);
+            MSDD_CUDA(cudaMemsetAsync(g.n_active.p, 0, sizeof(int), st));
+            eig_check_knorm(g, ep, it, st);
+        } else {
+            eig_form_y(g, ep.sigma, first, st);
+        }
+        prof.begin(tag + "_apply", st);
+        apply(g.Y.p, g.AY.p, g.BY.p, (const int*)g.done.p);
+        prof.end(st, apply_bytes * active, apply_flops * active);
+        prof.begin(tag + "_gram", st);
+        eig_gram(g, st);
+        prof.end(st, 3.0 * vec_n * 8.0 * fr, 2.0 * vec_n * (pavg + 1) * fr);
+        prof.begin(tag + "_rayleigh_ritz", st);
+        eig_rayleigh_ritz(g, st);
+        prof.end(st, 0.0, 0.0);
+        prof.begin(tag + "_update", st);
+        eig_update(g, st);
+        prof.end(st, 6.0 * vec_n * 8.0 * fr, 6.0 * vec_n * pavg * fr);
+        if (g.knorm) {
+            if (first) continue;
+        } else {
+            MSDD_CUDA(cudaMemsetAsync(g.n_active.p, 0, sizeof(int), st));
+            eig_check(g, ep, it, st);
+        }
+        MSDD_CUDA(cudaMemcpyAsync(&active, g.n_active.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        if (active == 0) break;
+    }
+    if (g.knorm && active > 0) {
+        // eig_maxit reached: the last updated pairs are kept and marked unconverged
+        std::vector<int> dn = g.done.download(st);
+        for (int& v : dn)
+            if (v == 0) v = 2;
+        g.done.upload(dn, st);
+    }
+    prof.collect();
+}
+
+}  // namespace
+
+Hierarchy::~Hierarchy() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (own_stream && st) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+}
+
+size_t Hierarchy::device_bytes() const {
+    size_t b = 0;
+    b += fdir.bytes() + fge.K.bytes() + cdir.bytes() + mdir.bytes() + mge.K.bytes();
+    b += (fge.X.n + fge.AX.n + fge.BX.n + fge.Y.n + fge.AY.n + fge.BY.n + fge.W.n) * 8;
+    b += (mge.X.n + mge.AX.n + mge.BX.n + mge.Y.n + mge.AY.n + mge.BY.n + mge.W.n) * 8;
+    b += (Phi.n + A1.n + Abar_m.n + K_m.n + Zb.n + Tm.n + A0.n + frhs.n + mrhs.n + v1.n + r0buf.n) * 8;
+    b += (x.n + r.n + p.n + q.n + z.n) * 8;
+    return b;
+}
+
+void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
+    auto t_all = Clock::now();
+    if (!st) {
+        // graph capture needs a stream other than the legacy default one; a
+        // blocking stream keeps the legacy stream's ordering for the caller
+        MSDD_CUDA(cudaStreamCreate(&st));
+        own_stream = true;
+    }
+    levels = dec.levels;
+    L = levels - 1;
+    prof.on = opt.profile != 0;
+    g.dim = mesh.dim;
+    for (int d = 0; d < 3; ++d) g.n[d] = d < mesh.dim ? mesh.n[d] : 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < mesh.dim) {
+            g.ulo[d] = (mesh.dirichlet_faces >> (2 * d)) & 1 ? 1 : 0;
+            g.uhi[d] = (mesh.dirichlet_faces >> (2 * d + 1)) & 1 ? g.n[d] - 1 : g.n[d];
+        } else {
+            g.ulo[d] = g.uhi[d] = 0;
+        }
+        g.ushape[d] = g.uhi[d] - g.ulo[d] + 1;
+    }
+    g.coeff_kind = coeff.kind;
+    g.ncomp = coeff.kind == 0 ? 1 : (mesh.dim == 2 ? 3 : 6);
+    g.coeff = coeff.data;
+    nun = (long long)g.ushape[0] * g.ushape[1] * g.ushape[2];
+    upload_reference(g);
+
+    memset(&stats, 0, sizeof(stats));
+    stats.n = nun;
+    stats.levels = levels;
+    stats.precision = opt.precision;
+
+    build_fine();
+    build_coarse();
+
+    // CG buffers
+    x.alloc(nun); r.alloc(nun); p.alloc(nun); q.alloc(nun); z.alloc(nun);
+    nblocks = dot_blocks(nun);
+    partial.alloc(nblocks);
+    sc.alloc(1);
+    MSDD_CUDA(cudaMemsetAsync(sc.p, 0, sizeof(PcgScalars), st));
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    stats.setup_ms = ms_since(t_all);
+    stats.device_bytes = device_bytes();
+    export_prof();
+}
+
+void Hierarchy::export_prof() {
+    stats.nprof = (int)std::min<size_t>(prof.fams.size(), MSDD_MAX_PROF);
+    for (int k = 0; k < stats.nprof; ++k) {
+        const Prof::Fam& f = prof.fams[k];
+        memset(stats.prof[k].name, 0, sizeof(stats.prof[k].name));
+        strncpy(stats.prof[k].name, f.name.c_str(), sizeof(stats.prof[k].name) - 1);
+        stats.prof[k].launches = f.launches;
+        stats.prof[k].ms = f.ms;
+        stats.prof[k].bytes = f.bytes;
+        stats.prof[k].flops = f.flops;
+    }
+}
+
+void Hierarchy::build_fine() {
+    auto t0 = Clock::now();
+    const int dim = g.dim;
+    std::vector<int> s[3], e[3];
+    for (int d = 0; d < 3; ++d) {
+        int P = d < dim ? dec.parts[d] : 1;
+        split_axis(g.n[d], P, s[d], e[d]);
+    }
+    int P0 = dec.parts[0], P1 = dim >= 2 ? dec.parts[1] : 1, P2 = dim == 3 ? dec.parts[2] : 1;
+    Pf = P0 * P1 * P2;
+    fboxes.resize(Pf);
+    for (int pz = 0; pz < P2; ++pz)
+        for (int py = 0; py < P1; ++py)
+            for (int px = 0; px < P0; ++px) {
+                int j = px + P0 * (py + P1 * pz);
+                int pi[3] = {px, py, pz};
+                ProbBox& b = fboxes[j];
+                for (int d = 0; d < 3; ++d) {
+                    if (d >= dim) {
+                        b.elo[d] = 0; b.ehi[d] = 1;
+                        b.nlo[d] = b.nhi[d] = b.dlo[d] = b.dhi[d] = 0;
+                        continue;
+                    }
+                    int lo = std::max(0, s[d][pi[d]] - dec.overlap);
+                    int hi = std::min(g.n[d], e[d][pi[d]] + dec.overlap);
+                    b.elo[d] = lo;
+                    b.ehi[d] = hi;
+                    b.nlo[d] = std::max(lo, g.ulo[d]);
+                    b.nhi[d] = std::min(hi, g.uhi[d]);
+                    int dlo = lo == 0 ? 0 : lo + 1;
+                    int dhi = hi == g.n[d] ? g.n[d] : hi - 1;
+                    b.dlo[d] = std::max(dlo, g.ulo[d]);
+                    b.dhi[d] = std::min(dhi, g.uhi[d]);
+                }
+                if (host_box_size(b.dlo, b.dhi, dim) <= 0 || host_box_size(b.nlo, b.nhi, dim) <= 0)
+                    throw MsddError(MSDD_ERR_INVALID_ARG, "subdomain " + std::to_string(j) + " has no interior unknowns");
+            }
+    d_fboxes = upload_vec(fboxes, st);
+    // combine maps: per axis and node coordinate, the blocks whose Dirichlet range holds it
+    cmaps.parts[0] = P0; cmaps.parts[1] = P1; cmaps.parts[2] = P2;
+    for (int d = 0; d < 3; ++d) {
+        int nn = g.n[d] + 1;
+        std::vector<int> fi(nn, 0), la(nn, -1);
+        if (d < dim) {
+            int Pd = dec.parts[d];
+            for (int x = 0; x < nn; ++x) {
+                fi[x] = -1;
+                la[x] = -2;
+                for (int p = 0; p < Pd; ++p) {
+                    int idx[3] = {0, 0, 0};
+                    idx[d] = p;
+                    int j = idx[0] + P0 * (idx[1] + P1 * idx[2]);
+                    if (x >= fboxes[j].dlo[d] && x <= fboxes[j].dhi[d]) {
+                        if (fi[x] < 0) fi[x] = p;
+                        la[x] = p;
+                    }
+                }
+                if (x >= g.ulo[d] && x <= g.uhi[d] && fi[x] < 0)
+                    throw MsddError(MSDD_ERR_INVALID_ARG, "node not interior to any subdomain: overlap must be >= 1");
+                if (fi[x] < 0) { fi[x] = 0; la[x] = -1; }
+            }
+        } else {
+            fi.assign(nn, 0);
+            la.assign(nn, 0);
+        }
+        cm_first[d] = upload_vec(fi, st);
+        cm_last[d] = upload_vec(la, st);
+        cmaps.first[d] = cm_first[d].p;
+        cmaps.last[d] = cm_last[d].p;
+    }
+    d_count.alloc(nun);
+    pou_count(g, d_fboxes.p, Pf, d_count.p, st);
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    stats.phase_ms[0] = ms_since(t0);
+
+    // ---- Dirichlet factors
+    t0 = Clock::now();
+    std::vector<int> nD(Pf), bD(Pf), nN(Pf), bN(Pf);
+    for (int j = 0; j < Pf; ++j) {
+        nD[j] = host_box_size(fboxes[j].dlo, fboxes[j].dhi, dim);
+        bD[j] = box_bandwidth(fboxes[j].dlo, fboxes[j].dhi, dim);
+        nN[j] = host_box_size(fboxes[j].nlo, fboxes[j].nhi, dim);
+        bN[j] = box_bandwidth(fboxes[j].nlo, fboxes[j].nhi, dim);
+    }
+    const int prec = opt.precision ? 1 : 0;
+    fdir.layout(nD, bD, prec, st);
+    tile_zero(fdir, st);
+    assemble_local_tiles(g, d_fboxes.p, d_count.p, fdir, 0, 0.0, st);
+    {
+        double fb = 0, ff = 0, sz = prec ? 4.0 : 8.0;
+        for (int j = 0; j < Pf; ++j) {
+            fb += 2.0 * nD[j] * (bD[j] + 1.0) * sz;
+            ff += (double)nD[j] * bD[j] * bD[j];
+        }
+        prof.begin("fine_factor", st);
+        tile_factor(fdir, 0.0, st);
+        prof.end(st, fb, ff);
+    }
+    check_status(fdir, st, "fine Dirichlet factorisation");
+    frhs.alloc(fdir.total_rows);
+    frhs.zero(st);
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    stats.phase_ms[1] = ms_since(t0);
+
+    // ---- shifted Neumann factors K = Abar + sigma B
+    t0 = Clock::now();
+    fge.K.layout(nN, bN, prec, st);
+    tile_zero(fge.K, st);
+    assemble_local_tiles(g, d_fboxes.p, d_count.p, fge.K, 1, opt.sigma, st);
+    {
+        double fb = 0, ff = 0, sz = prec ? 4.0 : 8.0;
+        for (int j = 0; j < Pf; ++j) {
+            fb += 2.0 * nN[j] * (bN[j] + 1.0) * sz;
+            ff += (double)nN[j] * bN[j] * bN[j];
+        }
+        prof.begin("fine_factor", st);
+        tile_factor(fge.K, 0.0, st);
+        prof.end(st, fb, ff);
+        prof.collect();
+    }
+    check_status(fge.K, st, "fine shifted Neumann factorisation");
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    stats.phase_ms[2] = ms_since(t0);
+
+    // ---- fine GEVPs
+    t0 = Clock::now();
+    const int block_p = opt.block_p > 0 ? opt.block_p : std::min(spec.nev_max + 8, PMAX);
+    fge.ldx = PMAX;
+    fge.p.resize(Pf);
+    for (int j = 0; j < Pf; ++j) fge.p[j] = std::min(block_p, nN[j]);
+    fge.alloc(st);
+    EigParams ep;
+    ep.sigma = opt.sigma;
+    ep.tol = opt.eig_tol;
+    ep.eta = spec.eta;
+    ep.nev_max = spec.nev_max;
+    ep.maxit = opt.eig_maxit;
+    ep.seed = opt.seed;
+    Geom gg = g;
+    const ProbBox* bx = d_fboxes.p;
+    const int* cnt = d_count.p;
+    GevpBatch* fg = &fge;
+    cudaStream_t stream = st;
+    double nav = 0;
+    for (int j = 0; j < Pf; ++j) nav += nN[j];
+    nav /= Pf;
+    run_eig(fge, ep,
+            [=](const double* X, double* AX, double* BX, const int* skip) {
+                apply_neumann(gg, bx, cnt, fg->K, X, AX, BX, fg->ldx, block_p, skip, stream);
+            },
+            st, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9));
+    fm = fge.m.download(st);
+    {
+        std::vector<int> it = fge.iters.download(st), dn = fge.done.download(st);
+        int mx = 0, mn = 1 << 30, unc = 0, mmin = 1 << 30, mmax = 0;
+        for (int j = 0; j < Pf; ++j) {
+            mx = std::max(mx, it[j]);
+            mn = std::min(mn, it[j]);
+            unc += dn[j] == 2 ? 1 : 0;
+            stats.eig_at_floor[L] += dn[j] == 3 ? 1 : 0;
+            mmin = std::min(mmin, fm[j]);
+            mmax = std::max(mmax, fm[j]);
+        }
+        stats.eig_iters_max[L] = mx;
+        stats.eig_iters_min[L] = mn;
+        stats.eig_unconverged[L] = unc;
+        stats.m_min[L] = mmin;
+        stats.m_max[L] = mmax;
+        stats.subdomains[L] = Pf;
+    }
+    d_fm = upload_vec(fm, st);
+    ldphi = std::max(1, spec.nev_max);
+    phioff.resize(Pf);
+    long long tot = 0;
+    for (int j = 0; j < Pf; ++j) {
+        phioff[j] = tot;
+        tot += (long long)nD[j] * ldphi;
+    }
+    Phi.alloc(tot);
+    d_phioff = upload_vec(phioff, st);
+    make_coarse_basis(g, d_fboxes.p, d_count.p, fge.K, fge.X.p, fge.ldx, d_fm.p, Phi.p, d_phioff.p, ldphi, Pf, st);
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    stats.phase_ms[3] = ms_since(t0);
+}
+
+void Hierarchy::build_coarse() {
+    auto t0 = Clock::now();
+    const int dim = g.dim;
+    const int P0 = cmaps.parts[0], P1 = cmaps.parts[1], P2 = cmaps.parts[2];
+    // ---- level L-1 ordering of the fine subdomains (group-major with 3 levels)
+    std::vector<int> order;
+    if (levels == 3) {
+        int G[3] = {1, 1, 1};
+        int Pp[3] = {P0, P1, P2};
+        std::vector<int> gs[3], ge[3];
+        for (int d = 0; d < 3; ++d) {
+            int gd = d < dim ? std::max(1, Pp[d] / std::max(1, dec.group[d])) : 1;
+            G[d] = gd;
+            split_axis(Pp[d], gd, gs[d], ge[d]);
+        }
+        Pm = G[0] * G[1] * G[2];
+        members.assign(Pm, {});
+        for (int qz = 0; qz < G[2]; ++qz)
+            for (int qy = 0; qy < G[1]; ++qy)
+                for (int qx = 0; qx < G[0]; ++qx) {
+                    int i = qx + G[0] * (qy + G[1] * qz);
+                    for (int pz = gs[2][qz]; pz < ge[2][qz]; ++pz)
+                        for (int py = gs[1][qy]; py < ge[1][qy]; ++py)
+                            for (int px = gs[0][qx]; px < ge[0][qx]; ++px)
+                                members[i].push_back(px + P0 * (py + P1 * pz));
+                    std::sort(members[i].begin(), members[i].end());
+                    for (int j : members[i]) order.push_back(j);
+                }
+    } else {
+        for (int j = 0; j < Pf; ++j) order.push_back(j);
+    }
+    c1off.assign(Pf, 0);
+    n1 = 0;
+    for (int j : order) {
+        c1off[j] = n1;
+        n1 += fm[j];
+    }
+    stats.level_dim[L] = nun;
+    stats.level_dim[L - 1] = n1;
+    d_c1off = upload_vec(c1off, st);
+    if (n1 == 0) throw MsddError(MSDD_ERR_UNSUPPORTED, "empty coarse space (no eigenvalue below eta)");
+
+    // ---- patches: per axis, runs of elements with equal block-membership intervals
+    struct AxisPatch { int e0, e1, plo, phi; };
+    std::vector<AxisPatch> ap[3];
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dim) { ap[d].push_back({0, 1, 0, 0}); continue; }
+        int Pd = dec.parts[d];
+        int prev_lo = -1, prev_hi = -1, start = 0;
+        for (int x = 0; x <= g.n[d]; ++x) {
+            int lo = -1, hi = -1;
+            if (x < g.n[d]) {
+                for (int p = 0; p < Pd; ++p) {
+                    int idx[3] = {0, 0, 0};
+                    idx[d] = p;
+                    const ProbBox& b = fboxes[idx[0] + P0 * (idx[1] + P1 * idx[2])];
+                    if (x >= b.elo[d] && x < b.ehi[d]) {
+                        if (lo < 0) lo = p;
+                        hi = p;
+                    }
+                }
+            }
+            if (x == g.n[d] || lo != prev_lo || hi != prev_hi) {
+                if (x > 0 && prev_lo >= 0) ap[d].push_back({start, x, prev_lo, prev_hi});
+                start = x;
+                prev_lo = lo;
+                prev_hi = hi;
+            }
+        }
+    }
+    struct Patch { int elo[3], ehi[3]; std::vector<int> mem; };
+    std::vector<Patch> patches;
+    for (auto& az : ap[2])
+        for (auto& ay : ap[1])
+            for (auto& ax : ap[0]) {
+                Patch pt;
+                const AxisPatch* a3[3] = {&ax, &ay, &az};
+                for (int d = 0; d < 3; ++d) { pt.elo[d] = a3[d]->e0; pt.ehi[d] = a3[d]->e1; }
+                for (int pz = az.plo; pz <= az.phi; ++pz)
+                    for (int py = ay.plo; py <= ay.phi; ++py)
+                        for (int px = ax.plo; px <= ax.phi; ++px) pt.mem.push_back(px + P0 * (py + P1 * pz));
+                patches.push_back(std::move(pt));
+            }
+    std::vector<GramItem> gitems;
+    std::vector<long long> gpatch;       // patch index of each item
+    long long gtot = 0;
+    for (size_t k = 0; k < patches.size(); ++k) {
+        for (int j : patches[k].mem)
+            for (int jj : patches[k].mem) {
+                if (fm[j] == 0 || fm[jj] == 0) continue;
+                GramItem it;
+                for (int d = 0; d < 3; ++d) { it.elo[d] = patches[k].elo[d]; it.ehi[d] = patches[k].ehi[d]; }
+                it.j = j;
+                it.jj = jj;
+                it.goff = gtot;
+                gtot += (long long)fm[j] * fm[jj];
+                gitems.push_back(it);
+                gpatch.push_back((long long)k);
+            }
+    }
+    DevBuf<GramItem> d_gitems = upload_vec(gitems, st);
+    DevBuf<double> G(std::max<long long>(gtot, 1));
+    patch_gram(g, d_fboxes.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_gitems.p, (int)gitems.size(), G.p, st);
+
+    // ---- Galerkin matrix of level L-1: block (j, jj) = sum over patches holding both
+    std::map<std::pair<int, int>, std::vector<long long>> pairc;
+    for (size_t k = 0; k < gitems.size(); ++k) pairc[{gitems[k].j, gitems[k].jj}].push_back(gitems[k].goff);
+    {
+        std::vector<SumItem> si;
+        std::vector<long long> contrib;
+        for (auto& kv : pairc) {
+            int j = kv.first.first, jj = kv.first.second;
+            SumItem it;
+            it.doff = c1off[j] * n1 + c1off[jj];
+            it.ld = (int)n1;
+            it.rows = fm[j];
+            it.cols = fm[jj];
+            it.cbeg = (int)contrib.size();
+            for (long long c : kv.second) contrib.push_back(c);
+            it.cend = (int)contrib.size();
+            si.push_back(it);
+        }
+        A1.alloc(n1 * n1);
+        A1.zero(st);
+        DevBuf<SumItem> d_si = upload_vec(si, st);
+        DevBuf<long long> d_contrib = upload_vec(contrib, st);
+        block_sum(d_si.p, (int)si.size(), d_contrib.p, G.p, A1.p, st);
+        MSDD_CUDA(cudaStreamSynchronize(st));
+    }
+    stats.phase_ms[4] = ms_since(t0);
+
+    if (levels == 2) {
+        t0 = Clock::now();
+        n0 = n1;
+        cdir.layout({(int)n0}, {(int)n0 - 1}, 0, st);
+        std::vector<long long> so = {0};
+        std::vector<int> ld = {(int)n1};
+        DevBuf<long long> d_so = upload_vec(so, st);
+        DevBuf<int> d_ld = upload_vec(ld, st);
+        tile_from_dense(cdir, A1.p, d_so.p, d_ld.p, st);
+        tile_factor(cdir, 0.0, st);
+        check_status(cdir, st, "coarse factorisation");
+        r0buf.alloc(cdir.total_rows);
+        r0buf.zero(st);
+        stats.level_dim[0] = n0;
+        stats.subdomains[0] = 1;
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        stats.phase_ms[6] = ms_since(t0);
+        return;
+    }
+
+    // ---- three levels: middle level 1 on the groups
+    t0 = Clock::now();
+    nown.assign(Pm, 0);
+    c1first.assign(Pm, 0);
+    for (int i = 0; i < Pm; ++i) {
+        c1first[i] = (int)c1off[members[i][0]];
+        for (int j : members[i]) nown[i] += fm[j];
+    }
+    // Dirichlet matrices: own x own blocks of A_1 (contiguous in group-major order)
+    {
+        std::vector<int> bw(Pm);
+        std::vector<long long> so(Pm);
+        std::vector<int> ld(Pm, (int)n1);
+        for (int i = 0; i < Pm; ++i) {
+            bw[i] = std::max(0, nown[i] - 1);
+            so[i] = (long long)c1first[i] * n1 + c1first[i];
+            if (nown[i] == 0) throw MsddError(MSDD_ERR_UNSUPPORTED, "level-1 subdomain without coarse functions");
+        }
+        mdir.layout(nown, bw, 0, st);
+        DevBuf<long long> d_so = upload_vec(so, st);
+        DevBuf<int> d_ld = upload_vec(ld, st);
+        tile_from_dense(mdir, A1.p, d_so.p, d_ld.p, st);
+        tile_factor(mdir, 0.0, st);
+        check_status(mdir, st, "level-1 Dirichlet factorisation");
+    }
+    // generating systems: own children, then neighbours meeting T_{1,i}
+    gens.assign(Pm, {});
+    ngen.assign(Pm, 0);
+    aoff.assign(Pm, 0);
+    std::vector<std::vector<int>> genoff(Pm);
+    std::vector<std::vector<char>> isown(Pm, std::vector<char>(Pf, 0));
+    long long atot = 0;
+    for (int i = 0; i < Pm; ++i) {
+        int tlo[3], thi[3];
+        for (int d = 0; d < 3; ++d) { tlo[d] = 1 << 30; thi[d] = -1; }
+        for (int j : members[i]) {
+            isown[i][j] = 1;
+            for (int d = 0; d < 3; ++d) {
+                tlo[d] = std::min(tlo[d], fboxes[j].elo[d]);
+                thi[d] = std::max(thi[d], fboxes[j].ehi[d]);
+            }
+            gens[i].push_back(j);
+        }
+        for (int j = 0; j < Pf; ++j) {
+            if (isown[i][j] || fm[j] == 0) continue;
+            bool meet = true;
+            for (int d = 0; d < dim; ++d)
+                if (fboxes[j].ehi[d] <= tlo[d] || fboxes[j].elo[d] >= thi[d]) meet = false;
+            if (meet) gens[i].push_back(j);
+        }
+        genoff[i].assign(Pf, -1);
+        int off = 0;
+        for (int j : gens[i]) {
+            genoff[i][j] = off;
+            off += fm[j];
+        }
+        ngen[i] = off;
+        aoff[i] = atot;
+        atot += (long long)off * off;
+    }
+    Abar_m.alloc(atot);
+    Abar_m.zero(st);
+    K_m.alloc(atot);
+    {
+        std::vector<SumItem> si;
+        std::vector<long long> contrib;
+        for (int i = 0; i < Pm; ++i) {
+            std::map<std::pair<int, int>, std::vector<long long>> pc;
+            for (size_t k = 0; k < gitems.size(); ++k) {
+                int j = gitems[k].j, jj = gitems[k].jj;
+                if (genoff[i][j] < 0 || genoff[i][jj] < 0) continue;
+                bool touches = false;
+                for (int mbr : patches[gpatch[k]].mem)
+                    if (isown[i][mbr]) { touches = true; break; }
+                if (!touches) continue;
+                pc[{j, jj}].push_back(gitems[k].goff);
+            }
+            for (auto& kv : pc) {
+                int j = kv.first.first, jj = kv.first.second;
+                SumItem it;
+                it.doff = aoff[i] + (long long)genoff[i][j] * ngen[i] + genoff[i][jj];
+                it.ld = ngen[i];
+                it.rows = fm[j];
+                it.cols = fm[jj];
+                it.cbeg = (int)contrib.size();
+                for (long long c : kv.second) contrib.push_back(c);
+                it.cend = (int)contrib.size();
+                si.push_back(it);
+            }
+        }
+        DevBuf<SumItem> d_si = upload_vec(si, st);
+        DevBuf<long long> d_contrib = upload_vec(contrib, st);
+        block_sum(d_si.p, (int)si.size(), d_contrib.p, G.p, Abar_m.p, st);
+    }
+    d_aoff = upload_vec(aoff, st);
+    d_ngen = upload_vec(ngen, st);
+    d_nown = upload_vec(nown, st);
+    int ngen_max = *std::max_element(ngen.begin(), ngen.end());
+    dense_shift(Abar_m.p, K_m.p, d_aoff.p, d_ngen.p, d_nown.p, opt.sigma, Pm, ngen_max, st);
+    {
+        std::vector<int> bw(Pm);
+        for (int i = 0; i < Pm; ++i) bw[i] = std::max(0, ngen[i] - 1);
+        mge.K.layout(ngen, bw, 0, st);
+        tile_from_dense(mge.K, K_m.p, d_aoff.p, d_ngen.p, st);
+        tile_factor(mge.K, opt.reg_tol, st);
+        stats.null_pivots[1] = sum_nreg(mge.K, st);
+    }
+    stats.phase_ms[4] += ms_since(t0);
+    t0 = Clock::now();
+    const int block_p = opt.block_p > 0 ? opt.block_p : std::min(spec.nev_max + 8, PMAX);
+    mge.ldx = PMAX;
+    mge.knorm = true;
+    mge.p.resize(Pm);
+    for (int i = 0; i < Pm; ++i) mge.p[i] = std::min(block_p, nown[i]);
+    mge.alloc(st);
+    EigParams ep;
+    ep.sigma = opt.sigma;
+    ep.tol = opt.eig_tol;
+    ep.eta = spec.eta;
+    ep.nev_max = spec.nev_max;
+    ep.maxit = opt.eig_maxit;
+    ep.seed = opt.seed + 7919;
+    const double* Ab = Abar_m.p;
+    const long long* dao = d_aoff.p;
+    const int* dng = d_ngen.p;
+    const int* dno = d_nown.p;
+    GevpBatch* mg = &mge;
+    int PmL = Pm;
+    cudaStream_t stream = st;
+    run_eig(mge, ep,
+            [=](const double* X, double* AX, double* BX, const int* skip) {
+                apply_dense_pencil(Ab, dao, dng, dno, mg->K, X, AX, BX, mg->ldx, block_p, skip, PmL, ngen_max, stream);
+            },
+            st, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
+    mm = mge.m.download(st);
+    {
+        std::vector<int> it = mge.iters.download(st), dn = mge.done.download(st);
+        int mx = 0, mn = 1 << 30, unc = 0, mmin = 1 << 30, mmax = 0;
+        for (int i = 0; i < Pm; ++i) {
+            mx = std::max(mx, it[i]);
+            mn = std::min(mn, it[i]);
+            unc += dn[i] == 2 ? 1 : 0;
+            stats.eig_at_floor[1] += dn[i] == 3 ? 1 : 0;
+            mmin = std::min(mmin, mm[i]);
+            mmax = std::max(mmax, mm[i]);
+        }
+        stats.eig_iters_max[1] = mx;
+        stats.eig_iters_min[1] = mn;
+        stats.eig_unconverged[1] = unc;
+        stats.m_min[1] = mmin;
+        stats.m_max[1] = mmax;
+        stats.subdomains[1] = Pm;
+    }
+    stats.phase_ms[5] = ms_since(t0);
+
+    // ---- Z_1 blocks (own generators' coefficients) and A_0 = Z_1^T A_1 Z_1
+    t0 = Clock::now();
+    ldz = std::max(1, spec.nev_max);
+    zoff.assign(Pm, 0);
+    c0off.assign(Pm, 0);
+    long long ztot = 0;
+    n0 = 0;
+    std::vector<CopyItem> ci;
+    for (int i = 0; i < Pm; ++i) {
+        zoff[i] = ztot;
+        ztot += (long long)nown[i] * ldz;
+        c0off[i] = n0;
+        n0 += mm[i];
+        CopyItem c;
+        c.soff = mge.K.roff[i] * mge.ldx;
+        c.lds = mge.ldx;
+        c.doff = zoff[i];
+        c.ldd = ldz;
+        c.rows = nown[i];
+        c.cols = mm[i];
+        ci.push_back(c);
+    }
+    if (n0 == 0) throw MsddError(MSDD_ERR_UNSUPPORTED, "empty coarsest space (no level-1 eigenvalue below eta)");
+    Zb.alloc(ztot);
+    Zb.zero(st);
+    {
+        DevBuf<CopyItem> d_ci = upload_vec(ci, st);
+        copy_blocks(d_ci.p, (int)ci.size(), mge.X.p, Zb.p, st);
+        MSDD_CUDA(cudaStreamSynchronize(st));
+    }
+    Tm.alloc(n1 * n0);
+    A0.alloc(n0 * n0);
+    {
+        std::vector<GemmItem> it1, it2;
+        int maxn = 0, maxm = 0;
+        for (int i = 0; i < Pm; ++i) {
+            GemmItem a;
+            a.aoff = c1first[i]; a.lda = (int)n1;
+            a.boff = zoff[i]; a.ldb = ldz;
+            a.coff = c0off[i]; a.ldc = (int)n0;
+            a.m = (int)n1; a.n = mm[i]; a.k = nown[i];
+            it1.push_back(a);
+            maxn = std::max(maxn, mm[i]);
+            GemmItem b;
+            b.aoff = zoff[i]; b.lda = ldz;
+            b.boff = (long long)c1first[i] * n0; b.ldb = (int)n0;
+            b.coff = c0off[i] * n0; b.ldc = (int)n0;
+            b.m = mm[i]; b.n = (int)n0; b.k = nown[i];
+            it2.push_back(b);
+            maxm = std::max(maxm, mm[i]);
+        }
+        DevBuf<GemmItem> d1 = upload_vec(it1, st), d2 = upload_vec(it2, st);
+        gemm_batched(d1.p, Pm, 0, 0, 1.0, A1.p, Zb.p, 0.0, Tm.p, (int)n1, maxn, st);
+        gemm_batched(d2.p, Pm, 1, 0, 1.0, Zb.p, Tm.p, 0.0, A0.p, maxm, (int)n0, st);
+        MSDD_CUDA(cudaStreamSynchronize(st));
+    }
+    cdir.layout({(int)n0}, {(int)n0 - 1}, 0, st);
+    {
+        std::vector<long long> so = {0};
+        std::vector<int> ld = {(int)n0};
+        DevBuf<long long> d_so = upload_vec(so, st);
+        DevBuf<int> d_ld = upload_vec(ld, st);
+        tile_from_dense(cdir, A0.p, d_so.p, d_ld.p, st);
+        tile_factor(cdir, 0.0, st);
+        check_status(cdir, st, "coarsest factorisation");
+    }
+    r0buf.alloc(cdir.total_rows);
+    r0buf.zero(st);
+    mrhs.alloc(mdir.total_rows);
+    mrhs.zero(st);
+    v1.alloc(n1);
+    {
+        std::vector<long long> sv(Pm), sm(Pm);
+        std::vector<int> len(Pm);
+        seg_maxlen = 0;
+        for (int i = 0; i < Pm; ++i) {
+            sv[i] = c1first[i];
+            sm[i] = mdir.roff[i];
+            len[i] = nown[i];
+            seg_maxlen = std::max(seg_maxlen, nown[i]);
+        }
+        d_seg_v1 = upload_vec(sv, st);
+        d_seg_mrhs = upload_vec(sm, st);
+        d_seg_len = upload_vec(len, st);
+        std::vector<GemmItem> g0, g1;
+        gemm_r0_maxm = 0;
+        gemm_z1_maxm = 0;
+        for (int i = 0; i < Pm; ++i) {
+            GemmItem a;   // r0_i = Zb_i^T v1_i
+            a.aoff = zoff[i]; a.lda = ldz;
+            a.boff = c1first[i]; a.ldb = 1;
+            a.coff = c0off[i]; a.ldc = 1;
+            a.m = mm[i]; a.n = 1; a.k = nown[i];
+            g0.push_back(a);
+            gemm_r0_maxm = std::max(gemm_r0_maxm, mm[i]);
+            GemmItem b;   // v1_i += Zb_i y0_i
+            b.aoff = zoff[i]; b.lda = ldz;
+            b.boff = c0off[i]; b.ldb = 1;
+            b.coff = c1first[i]; b.ldc = 1;
+            b.m = nown[i]; b.n = 1; b.k = mm[i];
+            g1.push_back(b);
+            gemm_z1_maxm = std::max(gemm_z1_maxm, nown[i]);
+        }
+        d_gemm_r0 = upload_vec(g0, st);
+        d_gemm_z1 = upload_vec(g1, st);
+    }
+    stats.level_dim[0] = n0;
+    stats.subdomains[0] = 1;
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    stats.phase_ms[6] = ms_since(t0);
+}
+
+void Hierarchy::apply_prec(const double* rr, double* zz, const int* gdone) {
+    double* r1 = levels == 2 ? r0buf.p : v1.p;
+    fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, rr, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p,
+                         d_c1off.p, r1, Pf, gdone, st);
+    tile_solve(fdir, frhs.p, 1, 1, nullptr, st, gdone);
+    const double* zc;
+    if (levels == 2) {
+        tile_solve(cdir, r0buf.p, 1, 1, nullptr, st, gdone);
+        zc = r0buf.p;
+    } else {
+        segment_copy(d_seg_v1.p, d_seg_mrhs.p, d_seg_len.p, Pm, seg_maxlen, v1.p, mrhs.p, 0, gdone, st);
+        tile_solve(mdir, mrhs.p, 1, 1, nullptr, st, gdone);
+        gemm_batched(d_gemm_r0.p, Pm, 1, 0, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, 1, st, gdone);
+        tile_solve(cdir, r0buf.p, 1, 1, nullptr, st, gdone);
+        segment_copy(d_seg_mrhs.p, d_seg_v1.p, d_seg_len.p, Pm, seg_maxlen, mrhs.p, v1.p, 0, gdone, st);
+        gemm_batched(d_gemm_z1.p, Pm, 0, 0, 1.0, Zb.p, r0buf.p, 1.0, v1.p, gemm_z1_maxm, 1, st, gdone);
+        zc = v1.p;
+    }
+    fine_combine(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p, zc, zz,
+                 rr, partial.p, nblocks, gdone, st);
+}
+
+void Hierarchy::build_graph() {
+    const int chunk = 8;
+    cudaGraph_t gr;
+    const long long c0 = kernel_launch_counter();
+    MSDD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int* gd = &sc.p->done;
+    for (int k = 0; k < chunk; ++k) {
+        apply_global_dot(g, p.p, q.p, partial.p, nblocks, gd, st);
+        pcg_fin_alpha(sc.p, partial.p, nblocks, st);
+        pcg_axpy(sc.p, x.p, r.p, p.p, q.p, nun, partial.p, nblocks, st);
+        pcg_fin_rr(sc.p, partial.p, nblocks, st);
+        apply_prec(r.p, z.p, gd);
+        pcg_fin_beta(sc.p, partial.p, nblocks, st);
+        pcg_update_p(sc.p, z.p, p.p, nun, st);
+    }
+    MSDD_CUDA(cudaStreamEndCapture(st, &gr));
+    MSDD_CUDA(cudaGraphInstantiate(&graph, gr, 0));
+    cudaGraphDestroy(gr);
+    graph_iters = chunk;
+    graph_kernels = kernel_launch_counter() - c0;   // captured, not launched
+    kernel_launch_counter() = c0;
+}
+
+int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, double* relres) {
+    auto t0 = Clock::now();
+    if (!graph) build_graph();
+    pcg_start(b, x.p, r.p, nun, partial.p, nblocks, st);
+    pcg_fin_bb(sc.p, partial.p, nblocks, tol, maxit, st);
+    apply_prec(r.p, z.p, &sc.p->done);
+    pcg_fin_rho0(sc.p, partial.p, nblocks, z.p, p.p, nun, st);
+    PcgScalars hs{};
+    // algorithmic amounts of one CG iteration: ~10 FP64 vector passes, the
+    // fine Dirichlet factors read twice, the coarse basis read twice
+    double it_bytes = 10.0 * 8.0 * nun, it_flops = 0.0;
+    {
+        double sz = fdir.prec ? 4.0 : 8.0;
+        for (int j = 0; j < Pf; ++j) {
+            it_bytes += 2.0 * fdir.n[j] * (fdir.b[j] + 1.0) * sz + 2.0 * fdir.n[j] * fm[j] * 8.0;
+            it_flops += 4.0 * fdir.n[j] * fdir.b[j] + 4.0 * fdir.n[j] * fm[j];
+        }
+        it_flops += 2.0 * (g.dim == 3 ? 27 : 9) * nun + 10.0 * nun;
+    }
+    int prev_iters = 0;
+    for (;;) {
+        prof.begin("pcg_iterations", st);
+        MSDD_CUDA(cudaGraphLaunch(graph, st));
+        kernel_launch_counter() += graph_kernels;
+        prof.end(st, 0.0, 0.0);
+        MSDD_CUDA(cudaMemcpyAsync(&hs, sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        if (prof.on) {
+            int done_it = hs.iters - prev_iters;
+            prof.pend.back().bytes = it_bytes * done_it;
+            prof.pend.back().flops = it_flops * done_it;
+            prev_iters = hs.iters;
+        }
+        if (hs.done) break;
+    }
+    prof.collect();
+    MSDD_CUDA(cudaMemcpyAsync(xout, x.p, nun * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    double rel = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+    if (relres) *relres = rel;
+    stats.pcg_iterations = hs.iters;
+    stats.pcg_rel_residual = rel;
+    stats.solve_ms = ms_since(t0);
+    export_prof();
+    if (hs.done == 3) throw MsddError(MSDD_ERR_NOT_SPD, "CG breakdown: p^T A p <= 0");
+    if (hs.done == 2) return -hs.iters;
+    return hs.iters;
+}
+
+}  // namespace msdd

@@ -1,0 +1,158 @@
+// Host orchestration of the multilevel spectral DD hierarchy (set-up and CG).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/msdd.h"
+#include "coarse.cuh"
+#include "eig.cuh"
+#include "pcg.cuh"
+#include "q1.cuh"
+#include "tile_ldlt.cuh"
+
+namespace msdd {
+
+struct MsddError : std::runtime_error {
+    msdd_status status;
+    MsddError(msdd_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+// CUDA-event timing of kernel families (options.profile); the bytes and flops
+// recorded with each launch are algorithmic amounts computed on the host.
+struct Prof {
+    bool on = false;
+    struct Fam {
+        std::string name;
+        int launches = 0;
+        double ms = 0, bytes = 0, flops = 0;
+    };
+    struct Pending {
+        int fam;
+        cudaEvent_t a, b;
+        double bytes, flops;
+    };
+    std::vector<Fam> fams;
+    std::vector<Pending> pend;
+    int family(const std::string& name) {
+        for (size_t k = 0; k < fams.size(); ++k)
+            if (fams[k].name == name) return (int)k;
+        fams.push_back(Fam{name});
+        return (int)fams.size() - 1;
+    }
+    void begin(const std::string& name, cudaStream_t s) {
+        if (!on) return;
+        Pending p{family(name), nullptr, nullptr, 0, 0};
+        MSDD_CUDA(cudaEventCreate(&p.a));
+        MSDD_CUDA(cudaEventCreate(&p.b));
+        MSDD_CUDA(cudaEventRecord(p.a, s));
+        pend.push_back(p);
+    }
+    void end(cudaStream_t s, double bytes, double flops) {
+        if (!on) return;
+        Pending& p = pend.back();
+        p.bytes = bytes;
+        p.flops = flops;
+        MSDD_CUDA(cudaEventRecord(p.b, s));
+    }
+    void collect() {
+        for (Pending& p : pend) {
+            MSDD_CUDA(cudaEventSynchronize(p.b));
+            float ms = 0.f;
+            MSDD_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+            Fam& f = fams[p.fam];
+            f.launches += 1;
+            f.ms += ms;
+            f.bytes += p.bytes;
+            f.flops += p.flops;
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        pend.clear();
+    }
+};
+
+struct Hierarchy {
+    Prof prof;
+    // ---- problem
+    Geom g{};
+    msdd_options opt{};
+    msdd_spectral spec{};
+    msdd_decomp dec{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;           // created when the caller passes no stream
+    int levels = 0, L = 0;
+    long long nun = 0;
+    msdd_stats stats{};
+
+    // ---- fine level (level L)
+    int Pf = 0;
+    std::vector<ProbBox> fboxes;
+    DevBuf<ProbBox> d_fboxes;
+    DevBuf<int> d_count;
+    TileBatch fdir;                 // Dirichlet factors A_{L,i}
+    GevpBatch fge;                  // GEVP of (Abar_i, B_i), K_i factors
+    std::vector<int> fm;            // selected counts m_i
+    DevBuf<int> d_fm;
+    int ldphi = 1;
+    std::vector<long long> phioff;
+    DevBuf<long long> d_phioff;
+    DevBuf<double> Phi;             // chi_i w_{i,k} on the Dirichlet boxes
+    std::vector<long long> c1off;   // offset of subdomain i's block in V_{h,L-1}
+    DevBuf<long long> d_c1off;
+    long long n1 = 0;
+    DevBuf<int> cm_first[3], cm_last[3];
+    CombineMaps cmaps{};
+    DevBuf<double> frhs;            // fine solve buffer
+    DevBuf<double> A1;              // dense Galerkin matrix of level L-1 (n1 x n1)
+
+    // ---- middle level (levels == 3, level 1)
+    int Pm = 0;
+    std::vector<std::vector<int>> members, gens;
+    std::vector<int> nown, ngen, c1first;
+    std::vector<long long> aoff;
+    DevBuf<long long> d_aoff;
+    DevBuf<int> d_ngen, d_nown;
+    DevBuf<double> Abar_m, K_m;
+    TileBatch mdir;
+    GevpBatch mge;
+    std::vector<int> mm;
+    int ldz = 1;
+    std::vector<long long> zoff;
+    DevBuf<double> Zb;
+    std::vector<long long> c0off;
+    DevBuf<double> Tm;              // A_1 Z_1
+    DevBuf<double> mrhs, v1;
+    DevBuf<long long> d_seg_v1, d_seg_mrhs;
+    DevBuf<int> d_seg_len;
+    int seg_maxlen = 0;
+    DevBuf<GemmItem> d_gemm_r0, d_gemm_z1;
+    int gemm_r0_maxm = 0, gemm_z1_maxm = 0;
+
+    // ---- coarsest level
+    long long n0 = 0;
+    TileBatch cdir;
+    DevBuf<double> A0;
+    DevBuf<double> r0buf;
+
+    // ---- CG
+    DevBuf<double> x, r, p, q, z, partial;
+    DevBuf<PcgScalars> sc;
+    int nblocks = 1;
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    long long graph_kernels = 0;
+
+    ~Hierarchy();
+    void setup(const msdd_mesh& mesh, const msdd_coeff& coeff);
+    void apply_prec(const double* rr, double* zz, const int* gdone);
+    int solve(const double* b, double tol, int maxit, double* xout, double* relres);
+    size_t device_bytes() const;
+
+   private:
+    void build_fine();
+    void build_coarse();
+    void build_graph();
+    void export_prof();
+};
+
+}  // namespace msdd

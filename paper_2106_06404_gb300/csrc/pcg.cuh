@@ -1,0 +1,39 @@
+// Device-resident preconditioned CG scalars and vector updates (Section 5:
+// CG stopped when ||b - A x^m|| < tol ||b - A x^0||, x^0 = 0).  Every kernel
+// reads the scalars from device memory and returns at once when `done` is
+// set, so a fixed sequence of iterations can be captured in a CUDA graph and
+// replayed until the host sees the flag.
+#pragma once
+#include "common.cuh"
+
+namespace msdd {
+
+struct PcgScalars {
+    double rho, alpha, beta, bb, rr, pq, rz;
+    double tol2;
+    int done;      // 0 running, 1 converged, 2 maxit, 3 breakdown
+    int iters;
+    int maxit;
+    int pad;
+};
+
+// r = b, x = 0, partial sums of b.b
+void pcg_start(const double* b, double* x, double* r, long long n, double* partial, int nblocks, cudaStream_t s);
+// bb = sum(partial); tol2 = tol^2; done = (bb == 0)
+void pcg_fin_bb(PcgScalars* sc, const double* partial, int nblocks, double tol, int maxit, cudaStream_t s);
+// rho = sum(partial) (r.z after the first preconditioner application); p = z
+void pcg_fin_rho0(PcgScalars* sc, const double* partial, int nblocks, const double* z, double* p, long long n,
+                  cudaStream_t s);
+// alpha = rho / sum(partial)
+void pcg_fin_alpha(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
+// x += alpha p, r -= alpha q, partial sums of r.r
+void pcg_axpy(PcgScalars* sc, double* x, double* r, const double* p, const double* q, long long n, double* partial,
+              int nblocks, cudaStream_t s);
+// rr = sum(partial); iters += 1; convergence / maxit test
+void pcg_fin_rr(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
+// beta = sum(partial) / rho; rho = sum(partial)
+void pcg_fin_beta(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
+// p = z + beta p
+void pcg_update_p(PcgScalars* sc, const double* z, double* p, long long n, cudaStream_t s);
+
+}  // namespace msdd

@@ -1,0 +1,440 @@
+// Q1 assembly and matrix-free operators on the structured mesh.
+#include "q1.cuh"
+
+#include <cmath>
+
+namespace msdd {
+
+// R[d][e][a][b] = int_tau d_d phi_a d_e phi_b (tau of size h), and the
+// scalar-coefficient sum S[a][b] = sum_d R[d][d][a][b].
+__constant__ double c_R[3][3][8][8];
+__constant__ double c_S[8][8];
+
+void upload_reference(const Geom& g) {
+    double R[3][3][8][8];
+    double S[8][8];
+    memset(R, 0, sizeof(R));
+    memset(S, 0, sizeof(S));
+    const int dim = g.dim, nloc = 1 << dim;
+    double h[3] = {1.0 / g.n[0], 1.0 / g.n[1], dim == 3 ? 1.0 / g.n[2] : 1.0};
+    // 2-point Gauss-Legendre on [0,1] per axis integrates the (bi/tri)quadratic
+    // integrand exactly.
+    const double gp[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+    double vol = h[0] * h[1] * (dim == 3 ? h[2] : 1.0);
+    int nq = 1 << dim;
+    for (int q = 0; q < nq; ++q) {
+        double xi[3] = {gp[q & 1], gp[(q >> 1) & 1], gp[(q >> 2) & 1]};
+        double grad[8][3];
+        for (int a = 0; a < nloc; ++a) {
+            int bit[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+            double val[3];
+            for (int d = 0; d < dim; ++d) val[d] = bit[d] ? xi[d] : 1.0 - xi[d];
+            for (int d = 0; d < dim; ++d) {
+                double gd = (bit[d] ? 1.0 : -1.0) / h[d];
+                for (int e = 0; e < dim; ++e)
+                    if (e != d) gd *= val[e];
+                grad[a][d] = gd;
+            }
+        }
+        double w = vol / nq;
+        for (int d = 0; d < dim; ++d)
+            for (int e = 0; e < dim; ++e)
+                for (int a = 0; a < nloc; ++a)
+                    for (int b = 0; b < nloc; ++b) R[d][e][a][b] += w * grad[a][d] * grad[b][e];
+    }
+    for (int d = 0; d < dim; ++d)
+        for (int a = 0; a < nloc; ++a)
+            for (int b = 0; b < nloc; ++b) S[a][b] += R[d][d][a][b];
+    MSDD_CUDA(cudaMemcpyToSymbol(c_R, R, sizeof(R)));
+    MSDD_CUDA(cudaMemcpyToSymbol(c_S, S, sizeof(S)));
+}
+
+namespace {
+
+__device__ __forceinline__ double elem_entry(const Geom& g, long long e, int a, int b) {
+    if (g.coeff_kind == 0) return g.coeff[e] * c_S[a][b];
+    const double* k = g.coeff + e * g.ncomp;
+    double K[3][3];
+    if (g.dim == 2) {
+        K[0][0] = k[0]; K[1][1] = k[1]; K[0][1] = K[1][0] = k[2];
+    } else {
+        K[0][0] = k[0]; K[1][1] = k[1]; K[2][2] = k[2];
+        K[1][2] = K[2][1] = k[3];
+        K[0][2] = K[2][0] = k[4];
+        K[0][1] = K[1][0] = k[5];
+    }
+    double v = 0.0;
+    for (int d = 0; d < g.dim; ++d)
+        for (int f = 0; f < g.dim; ++f) v += K[d][f] * c_R[d][f][a][b];
+    return v;
+}
+
+// sum over elements tau of the element box containing nodes x and x + o of
+// a_tau(phi_{x+o}, phi_x).
+__device__ double stencil_coef(const Geom& g, const int* elo, const int* ehi, const int x[3], const int o[3]) {
+    int lo[3], cnt[3];
+    for (int d = 0; d < 3; ++d) {
+        if (d >= g.dim) { lo[d] = 0; cnt[d] = 1; continue; }
+        if (o[d] < 0) { lo[d] = x[d] - 1; cnt[d] = 1; }
+        else if (o[d] > 0) { lo[d] = x[d]; cnt[d] = 1; }
+        else { lo[d] = x[d] - 1; cnt[d] = 2; }
+    }
+    double v = 0.0;
+    for (int kz = 0; kz < cnt[2]; ++kz)
+        for (int ky = 0; ky < cnt[1]; ++ky)
+            for (int kx = 0; kx < cnt[0]; ++kx) {
+                int l[3] = {lo[0] + kx, lo[1] + ky, lo[2] + kz};
+                bool inside = true;
+                for (int d = 0; d < g.dim; ++d)
+                    if (l[d] < elo[d] || l[d] >= ehi[d]) inside = false;
+                if (!inside) continue;
+                int a = 0, b = 0;
+                for (int d = 0; d < g.dim; ++d) {
+                    a |= (x[d] - l[d]) << d;
+                    b |= (x[d] + o[d] - l[d]) << d;
+                }
+                long long e = l[0] + (long long)g.n[0] * (l[1] + (long long)g.n[1] * l[2]);
+                v += elem_entry(g, e, a, b);
+            }
+    return v;
+}
+
+__device__ __forceinline__ double chi_at(const Geom& g, const ProbBox& pb, const int* count, const int x[3]) {
+    if (!in_box(pb.dlo, pb.dhi, x, g.dim)) return 0.0;
+    return 1.0 / (double)count[unknown_index(g, x)];
+}
+
+__global__ void k_pou_count(Geom g, const ProbBox* __restrict__ boxes, int* __restrict__ count) {
+    const ProbBox pb = boxes[blockIdx.y];
+    int n = box_size(pb.dlo, pb.dhi, g.dim);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        int x[3];
+        box_coords(r, pb.dlo, pb.dhi, g.dim, x);
+        atomicAdd(&count[unknown_index(g, x)], 1);
+    }
+}
+
+template <typename T>
+__global__ void k_assemble(Geom g, const ProbBox* __restrict__ boxes, const int* __restrict__ count, T* __restrict__ tiles,
+                           const int* __restrict__ kb_, const long long* __restrict__ toff_, int mode, double sigma) {
+    const int i = blockIdx.y;
+    const ProbBox pb = boxes[i];
+    const int* lo = mode == 0 ? pb.dlo : pb.nlo;
+    const int* hi = mode == 0 ? pb.dhi : pb.nhi;
+    const int n = box_size(lo, hi, g.dim);
+    const int kb = kb_[i];
+    const long long toff = toff_[i];
+    const int noff = g.dim == 3 ? 27 : 9;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n * noff;
+         w += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(w / noff), oi = (int)(w % noff);
+        int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+        if (g.dim == 2) o[2] = 0;
+        int x[3], y[3];
+        box_coords(r, lo, hi, g.dim, x);
+        for (int d = 0; d < 3; ++d) y[d] = x[d] + o[d];
+        if (!in_box(lo, hi, y, g.dim)) continue;
+        int c = box_index(lo, hi, y, g.dim);
+        if (c > r) continue;   // lower triangle only
+        double v = stencil_coef(g, pb.elo, pb.ehi, x, o);
+        if (mode == 1) v *= 1.0 + sigma * chi_at(g, pb, count, x) * chi_at(g, pb, count, y);
+        int R = r / NB, C = c / NB;
+        tiles[toff + ((long long)R * (kb + 1) + (R - C)) * NB2 + (r % NB) * NB + (c % NB)] = (T)v;
+    }
+}
+
+// One thread per (row, chunk of 8 columns).
+__global__ void k_apply_neumann(Geom g, const ProbBox* __restrict__ boxes, const int* __restrict__ count,
+                                const long long* __restrict__ roff_, const double* __restrict__ X,
+                                double* __restrict__ AX, double* __restrict__ BX, int ldx, int ncols,
+                                const int* __restrict__ skip) {
+    const int i = blockIdx.y;
+    if (skip && skip[i]) return;
+    const ProbBox pb = boxes[i];
+    const int n = box_size(pb.nlo, pb.nhi, g.dim);
+    const int nchunk = (ncols + 7) / 8;
+    const long long roff = roff_[i];
+    const int noff = g.dim == 3 ? 27 : 9;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n * nchunk;
+         w += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(w / nchunk), ch = (int)(w % nchunk);
+        int c0 = ch * 8, c1 = min(ncols, c0 + 8);
+        int x[3];
+        box_coords(r, pb.nlo, pb.nhi, g.dim, x);
+        double ax[8], bx[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) { ax[c] = 0.0; bx[c] = 0.0; }
+        const double chix = chi_at(g, pb, count, x);
+        for (int oi = 0; oi < noff; ++oi) {
+            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+            int y[3];
+            for (int d = 0; d < 3; ++d) y[d] = x[d] + o[d];
+            if (!in_box(pb.nlo, pb.nhi, y, g.dim)) continue;
+            double a = stencil_coef(g, pb.elo, pb.ehi, x, o);
+            if (a == 0.0) continue;
+            double chiy = chi_at(g, pb, count, y);
+            const double* xr = X + (roff + box_index(pb.nlo, pb.nhi, y, g.dim)) * ldx;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (c0 + c < c1) {
+                    double v = xr[c0 + c];
+                    ax[c] += a * v;
+                    bx[c] += a * chiy * v;
+                }
+            }
+        }
+        double* ar = AX + (roff + r) * ldx;
+        double* br = BX + (roff + r) * ldx;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c0 + c < c1) { ar[c0 + c] = ax[c]; br[c0 + c] = chix * bx[c]; }
+    }
+}
+
+__global__ void k_apply_global(Geom g, const double* __restrict__ x, double* __restrict__ y, long long nun) {
+    int elo[3] = {0, 0, 0};
+    int ehi[3] = {g.n[0], g.n[1], g.n[2]};
+    const int noff = g.dim == 3 ? 27 : 9;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
+        int xc[3];
+        long long rem = u;
+        for (int d = 0; d < 3; ++d) {
+            if (d >= g.dim) { xc[d] = 0; continue; }
+            xc[d] = g.ulo[d] + (int)(rem % g.ushape[d]);
+            rem /= g.ushape[d];
+        }
+        double acc = 0.0;
+        for (int oi = 0; oi < noff; ++oi) {
+            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+            int yc[3];
+            for (int d = 0; d < 3; ++d) yc[d] = xc[d] + o[d];
+            if (!in_box(g.ulo, g.uhi, yc, g.dim)) continue;
+            acc += stencil_coef(g, elo, ehi, xc, o) * x[unknown_index(g, yc)];
+        }
+        y[u] = acc;
+    }
+}
+
+__global__ void k_load_vector(Geom g, double f, double* __restrict__ b, long long nun) {
+    double vol = 1.0;
+    for (int d = 0; d < g.dim; ++d) vol /= g.n[d];
+    const int nloc = 1 << g.dim;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
+        long long rem = u;
+        int cnt = 1;
+        for (int d = 0; d < g.dim; ++d) {
+            int xd = g.ulo[d] + (int)(rem % g.ushape[d]);
+            rem /= g.ushape[d];
+            cnt *= (xd > 0 ? 1 : 0) + (xd < g.n[d] ? 1 : 0);
+        }
+        b[u] = f * vol * cnt / nloc;
+    }
+}
+
+__global__ void k_make_basis(Geom g, const ProbBox* __restrict__ boxes, const int* __restrict__ count,
+                             const long long* __restrict__ roff_, const double* __restrict__ X, int ldx,
+                             const int* __restrict__ m_, double* __restrict__ Phi, const long long* __restrict__ phioff,
+                             int ldphi) {
+    const int i = blockIdx.y;
+    const ProbBox pb = boxes[i];
+    const int nd = box_size(pb.dlo, pb.dhi, g.dim);
+    const int m = m_[i];
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nd * ldphi; w += gridDim.x * blockDim.x) {
+        int r = w / ldphi, k = w % ldphi;
+        int x[3];
+        box_coords(r, pb.dlo, pb.dhi, g.dim, x);
+        double v = 0.0;
+        if (k < m) {
+            int rn = box_index(pb.nlo, pb.nhi, x, g.dim);
+            v = chi_at(g, pb, count, x) * X[(roff_[i] + rn) * ldx + k];
+        }
+        Phi[phioff[i] + (long long)r * ldphi + k] = v;
+    }
+}
+
+}  // namespace
+
+void pou_count(const Geom& g, const ProbBox* d_boxes, int P, int* d_count, cudaStream_t s) {
+    long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    MSDD_CUDA(cudaMemsetAsync(d_count, 0, nun * sizeof(int), s));
+    dim3 grid(64, P);
+    k_pou_count<<<grid, 256, 0, s>>>(g, d_boxes, d_count);
+    MSDD_LAUNCH_CHECK();
+}
+
+void assemble_local_tiles(const Geom& g, const ProbBox* d_boxes, const int* d_count, TileBatch& tb, int mode,
+                          double sigma, cudaStream_t s) {
+    if (tb.P == 0) return;
+    dim3 grid(128, tb.P);
+    if (tb.prec)
+        k_assemble<float><<<grid, 256, 0, s>>>(g, d_boxes, d_count, tb.tiles_f.p, tb.d_kb.p, tb.d_toff.p, mode, sigma);
+    else
+        k_assemble<double><<<grid, 256, 0, s>>>(g, d_boxes, d_count, tb.tiles_d.p, tb.d_kb.p, tb.d_toff.p, mode, sigma);
+    MSDD_LAUNCH_CHECK();
+}
+
+void apply_neumann(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout,
+                   const double* X, double* AX, double* BX, int ldx, int ncols, const int* skip, cudaStream_t s) {
+    if (layout.P == 0) return;
+    dim3 grid(64, layout.P);
+    k_apply_neumann<<<grid, 128, 0, s>>>(g, d_boxes, d_count, layout.d_roff.p, X, AX, BX, ldx, ncols, skip);
+    MSDD_LAUNCH_CHECK();
+}
+
+void apply_global(const Geom& g, const double* x, double* y, cudaStream_t s) {
+    long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    unsigned blocks = (unsigned)std::min<long long>(ceil_div(nun, 256), 152 * 16);
+    k_apply_global<<<blocks, 256, 0, s>>>(g, x, y, nun);
+    MSDD_LAUNCH_CHECK();
+}
+
+void load_vector(const Geom& g, double f, double* b, cudaStream_t s) {
+    long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    unsigned blocks = (unsigned)std::min<long long>(ceil_div(nun, 256), 152 * 16);
+    k_load_vector<<<blocks, 256, 0, s>>>(g, f, b, nun);
+    MSDD_LAUNCH_CHECK();
+}
+
+void make_coarse_basis(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& nlayout,
+                       const double* X, int ldx, const int* d_m, double* Phi, const long long* d_phioff, int ldphi,
+                       int P, cudaStream_t s) {
+    if (P == 0) return;
+    dim3 grid(32, P);
+    k_make_basis<<<grid, 256, 0, s>>>(g, d_boxes, d_count, nlayout.d_roff.p, X, ldx, d_m, Phi, d_phioff, ldphi);
+    MSDD_LAUNCH_CHECK();
+}
+
+}  // namespace msdd
+
+namespace msdd {
+namespace {
+
+constexpr int GCH = 16;   // elements staged per chunk in patch_gram
+
+__global__ void __launch_bounds__(256) k_patch_gram(Geom g, const ProbBox* __restrict__ fine,
+                                                    const double* __restrict__ Phi, const long long* __restrict__ phioff,
+                                                    int ldphi, const int* __restrict__ m_,
+                                                    const GramItem* __restrict__ items, double* __restrict__ G) {
+    extern __shared__ double sm[];
+    const GramItem it = items[blockIdx.x];
+    const int nloc = 1 << g.dim;
+    const int mj = m_[it.j], mjj = m_[it.jj];
+    if (mj == 0 || mjj == 0) return;
+    const ProbBox bj = fine[it.j], bjj = fine[it.jj];
+    double* Pj = sm;
+    double* Pjj = Pj + GCH * nloc * ldphi;
+    double* Tm = Pjj + GCH * nloc * ldphi;
+    int w[3] = {1, 1, 1};
+    long long ne = 1;
+    for (int d = 0; d < g.dim; ++d) { w[d] = it.ehi[d] - it.elo[d]; ne *= w[d]; }
+    const int t = threadIdx.x;
+    double acc[4] = {0, 0, 0, 0};
+    const long long pj = phioff[it.j], pjj = phioff[it.jj];
+    for (long long c0 = 0; c0 < ne; c0 += GCH) {
+        __syncthreads();
+        for (int e = t; e < GCH * nloc; e += blockDim.x) {
+            long long el = c0 + e / nloc;
+            int a = e % nloc;
+            bool ok = el < ne;
+            int x[3] = {0, 0, 0};
+            if (ok) {
+                long long rem = el;
+                for (int d = 0; d < g.dim; ++d) {
+                    x[d] = it.elo[d] + (int)(rem % w[d]) + ((a >> d) & 1);
+                    rem /= w[d];
+                }
+            }
+            bool inj = ok && in_box(bj.dlo, bj.dhi, x, g.dim);
+            bool injj = ok && in_box(bjj.dlo, bjj.dhi, x, g.dim);
+            int rj = inj ? box_index(bj.dlo, bj.dhi, x, g.dim) : 0;
+            int rjj = injj ? box_index(bjj.dlo, bjj.dhi, x, g.dim) : 0;
+            for (int k = 0; k < mj; ++k) Pj[e * ldphi + k] = inj ? Phi[pj + (long long)rj * ldphi + k] : 0.0;
+            for (int k = 0; k < mjj; ++k) Pjj[e * ldphi + k] = injj ? Phi[pjj + (long long)rjj * ldphi + k] : 0.0;
+        }
+        __syncthreads();
+        for (int e = t; e < GCH * nloc * mjj; e += blockDim.x) {
+            int elc = e / (nloc * mjj), a = (e / mjj) % nloc, kk = e % mjj;
+            long long el = c0 + elc;
+            double v = 0.0;
+            if (el < ne) {
+                long long rem = el;
+                int l[3] = {0, 0, 0};
+                for (int d = 0; d < g.dim; ++d) { l[d] = it.elo[d] + (int)(rem % w[d]); rem /= w[d]; }
+                long long E = l[0] + (long long)g.n[0] * (l[1] + (long long)g.n[1] * l[2]);
+                for (int b = 0; b < nloc; ++b) v += elem_entry(g, E, a, b) * Pjj[(elc * nloc + b) * ldphi + kk];
+            }
+            Tm[(elc * nloc + a) * ldphi + kk] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = t + q * blockDim.x;
+            if (e >= mj * mjj) break;
+            int k = e / mjj, kk = e % mjj;
+            double s = 0.0;
+            for (int ea = 0; ea < GCH * nloc; ++ea) s += Pj[ea * ldphi + k] * Tm[ea * ldphi + kk];
+            acc[q] += s;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int e = t + q * blockDim.x;
+        if (e < mj * mjj) G[it.goff + e] = acc[q];
+    }
+}
+
+__global__ void k_apply_global_dot(Geom g, const double* __restrict__ x, double* __restrict__ y, long long nun,
+                                   double* __restrict__ partial, const int* __restrict__ done) {
+    __shared__ double red[256];
+    if (done && *done) return;
+    int elo[3] = {0, 0, 0};
+    int ehi[3] = {g.n[0], g.n[1], g.n[2]};
+    const int noff = g.dim == 3 ? 27 : 9;
+    double part = 0.0;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
+        int xc[3];
+        long long rem = u;
+        for (int d = 0; d < 3; ++d) {
+            if (d >= g.dim) { xc[d] = 0; continue; }
+            xc[d] = g.ulo[d] + (int)(rem % g.ushape[d]);
+            rem /= g.ushape[d];
+        }
+        double acc = 0.0;
+        for (int oi = 0; oi < noff; ++oi) {
+            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+            int yc[3];
+            for (int d = 0; d < 3; ++d) yc[d] = xc[d] + o[d];
+            if (!in_box(g.ulo, g.uhi, yc, g.dim)) continue;
+            acc += stencil_coef(g, elo, ehi, xc, o) * x[unknown_index(g, yc)];
+        }
+        y[u] = acc;
+        part += acc * x[u];
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+}  // namespace
+
+void patch_gram(const Geom& g, const ProbBox* d_fine, const double* Phi, const long long* d_phioff, int ldphi,
+                const int* d_m, const GramItem* d_items, int nitems, double* G, cudaStream_t s) {
+    if (nitems == 0) return;
+    size_t smem = (size_t)3 * GCH * (1 << g.dim) * ldphi * sizeof(double);
+    if (smem > 48 * 1024) MSDD_CUDA(cudaFuncSetAttribute(k_patch_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_patch_gram<<<nitems, 256, smem, s>>>(g, d_fine, Phi, d_phioff, ldphi, d_m, d_items, G);
+    MSDD_LAUNCH_CHECK();
+}
+
+void apply_global_dot(const Geom& g, const double* p, double* q, double* partial, int nblocks, const int* done,
+                      cudaStream_t s) {
+    long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    k_apply_global_dot<<<nblocks, 256, 0, s>>>(g, p, q, nun, partial, done);
+    MSDD_LAUNCH_CHECK();
+}
+
+}  // namespace msdd

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (FP64 unless stated):
+  * band LDL^T solves: relative error <= 1e-10 (FP64) / 1e-4 (FP32) against the
+    oracle's dense Cholesky solve on well-conditioned random SPD band matrices;
+  * eigenvalues: |theta - lambda| <= 1e-6 * max(lambda, 1e-3 eta) (the stated
+    1e-6 relative bound, with an absolute floor for eigenvalues ~ 0);
+  * selected counts m_i and coarse dimensions: exact (integers);
+  * preconditioner application z = B r: relative 2-norm difference <= 1e-6
+    (both sides' coarse spaces agree to the eigen-residual tolerance);
+  * CG iterations: equal within +-1; solution: relative error <= 1e-8 against
+    the oracle's direct solve with both solvers run to 1e-12.
+"""
+import functools
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import synthetic_inputs as si
+from oracle import fem, linalg, method
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2106_06404_gb300 as pkg  # noqa: E402
+
+EIG_TOL = 1e-10
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_case(name):
+    c = CASES[name]
+    mesh = fem.Mesh(c["n"], 0b1)
+    kap = c["kappa"]()
+    H = method.Hierarchy(mesh, kap, c["parts"], c["overlap"], c["levels"], c["group"], c["nev"], c["eta"])
+    return mesh, kap, H
+
+
+CASES = {
+    "small2": dict(n=(24, 24), parts=(3, 3), overlap=2, levels=2, group=(1, 1), nev=6, eta=0.3,
+                   kappa=lambda: si.channels_2d(24, 3, 1e4, seed=1)),
+    "channels64": dict(n=(64, 64), parts=(4, 4), overlap=2, levels=2, group=(4, 4), nev=8, eta=0.3,
+                       kappa=lambda: si.channels64().coefficient()),
+    "ragged3": dict(n=(52, 44), parts=(6, 5), overlap=2, levels=3, group=(2, 2), nev=6, eta=0.3,
+                    kappa=lambda: si.grf_channels_inclusions_2d(52, seed=3, n_channels=3, n_inclusions=4,
+                                                                inclusion_side=(3, 6))[: 52 * 44]),
+}
+
+
+def _gpu(name, precision=0, eig_tol=EIG_TOL):
+    c = CASES[name]
+    kap = torch.tensor(c["kappa"](), device="cuda")
+    return pkg.Hierarchy(c["n"], kap, c["parts"], c["overlap"], c["levels"], c["group"], c["nev"], c["eta"],
+                         precision=precision, eig_tol=eig_tol)
+
+
+def _eig_close(theta, lam, eta, m):
+    """The m selected eigenvalues to the stated tolerance (the next one only has
+    to lie above eta, which the equal counts already show)."""
+    k = min(len(theta), len(lam), m)
+    tol = 1e-6 * np.maximum(np.abs(lam[:k]), 1e-3 * eta)
+    return np.all(np.abs(theta[:k] - lam[:k]) <= tol), theta[:k], lam[:k]
+
+
+# ---------------------------------------------------------------- band solver
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+@pytest.mark.parametrize("nrhs", [1, 5])
+def test_band_solver_matches_oracle(precision, tol, nrhs):
+    rng = np.random.default_rng(7)
+    sizes = [1, 31, 32, 33, 100, 157]            # ragged tails and several tiles
+    nmax, bw = max(sizes), 40
+    A = np.zeros((len(sizes), nmax, nmax))
+    for i, n in enumerate(sizes):
+        M = rng.standard_normal((n, n))
+        band = np.abs(np.subtract.outer(np.arange(n), np.arange(n))) <= bw
+        S = np.where(band, M + M.T, 0.0)
+        S += np.diag(np.abs(S).sum(axis=1) + 1.0)    # diagonally dominant SPD band
+        A[i, :n, :n] = S
+    B = rng.standard_normal((len(sizes), nmax, nrhs))
+    bb = pkg.BandBatch(torch.tensor(A, device="cuda"), sizes, bw, precision=precision)
+    X = torch.tensor(B, device="cuda")
+    bb.solve(X)
+    X = X.cpu().numpy()
+    for i, n in enumerate(sizes):
+        ref = linalg.cho_solve(linalg.cholesky(A[i, :n, :n]), B[i, :n])
+        err = np.linalg.norm(X[i, :n] - ref.reshape(n, nrhs)) / np.linalg.norm(ref)
+        assert err < tol, (n, err)
+
+
+def test_band_solver_dense_and_semidefinite():
+    rng = np.random.default_rng(3)
+    n = 70
+    G = rng.standard_normal((n, 50))
+    G[:, 40:] = G[:, :10]                     # exact dependencies: rank 40
+    S = G @ G.T                               # n x n, rank 40, dense (bw = n - 1)
+    bb = pkg.BandBatch(torch.tensor(S[None], device="cuda"), [n], n - 1, precision=0, reg_tol=1e-10)
+    # a consistent right-hand side: b in range(S)
+    b = S @ rng.standard_normal(n)
+    X = torch.tensor(b.reshape(1, n, 1), device="cuda")
+    bb.solve(X)
+    x = X.cpu().numpy().reshape(n)
+    assert np.linalg.norm(S @ x - b) / np.linalg.norm(b) < 1e-8
+    # non-regularised factorisation of an indefinite matrix reports the pivot
+    with pytest.raises(pkg.MsddError) as e:
+        pkg.BandBatch(torch.tensor(-np.eye(5)[None], device="cuda"), [5], 1)
+    assert e.value.status == -2
+
+
+# ---------------------------------------------------------------- operator
+def test_operator_and_load_vector_match_oracle():
+    mesh, kap, H = oracle_case("small2")
+    G = _gpu("small2")
+    x = np.random.default_rng(0).standard_normal(H.n)
+    y = G.apply_operator(torch.tensor(x, device="cuda")).cpu().numpy()
+    ref = H.A @ x
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    b = pkg.assemble_rhs((24, 24)).cpu().numpy()
+    assert np.allclose(b, fem.load_vector(mesh), rtol=0, atol=1e-16)
+
+
+# ---------------------------------------------------------------- hierarchy
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3"])
+def test_setup_matches_oracle(name):
+    c = CASES[name]
+    mesh, kap, H = oracle_case(name)
+    G = _gpu(name)
+    st = G.stats()
+    L = c["levels"] - 1
+    # fine-level eigenvalues and selected counts
+    for i, lam in enumerate(H.eigenvalues(L)):
+        theta, m = G.eigenvalues(L, i)
+        assert m == H.counts(L)[i], (i, m, H.counts(L)[i], theta[:8], lam[:8])
+        ok, a, b = _eig_close(theta, lam, c["eta"], m)
+        assert ok, (i, a, b)
+    # coarse-level eigenvalues (three levels: generating systems)
+    if c["levels"] == 3:
+        for i, lam in enumerate(H.eigenvalues(1)):
+            theta, m = G.eigenvalues(1, i)
+            assert m == H.counts(1)[i], (i, m, H.counts(1)[i], theta[:8], lam[:8])
+            ok, a, b = _eig_close(theta, lam, c["eta"], m)
+            assert ok, (i, a, b)
+    dims = H.coarse_dims()
+    for lev, d in dims.items():
+        assert st["level_dim"][lev] == d
+    assert st["eig_unconverged"] == [0] * c["levels"]
+
+
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3"])
+def test_preconditioner_matches_oracle(name):
+    mesh, kap, H = oracle_case(name)
+    G = _gpu(name)
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        r = rng.standard_normal(H.n)
+        z = G.apply_preconditioner(torch.tensor(r, device="cuda")).cpu().numpy()
+        zo = H.apply_preconditioner(r)
+        assert np.linalg.norm(z - zo) / np.linalg.norm(zo) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3"])
+def test_pcg_matches_oracle(name):
+    mesh, kap, H = oracle_case(name)
+    G = _gpu(name)
+    b = fem.load_vector(mesh)
+    _, it_o, *_ = method.pcg(H.A, b, H.apply_preconditioner, 1e-8)
+    x, it, rel = G.solve(torch.tensor(b, device="cuda"), tol=1e-8)
+    assert abs(it - it_o) <= 1, (it, it_o)
+    assert rel < 1e-8
+    x12, _, _ = G.solve(torch.tensor(b, device="cuda"), tol=1e-12)
+    xd = spla.spsolve(H.A.tocsc(), b)
+    assert np.linalg.norm(x12.cpu().numpy() - xd) / np.linalg.norm(xd) < 1e-8
+
+
+def test_host_buffer_solve_equals_device_solve():
+    mesh, kap, H = oracle_case("small2")
+    G = _gpu("small2")
+    b = fem.load_vector(mesh)
+    xh, ith, relh = G.solve_host(b, tol=1e-10)
+    xd, itd, reld = G.solve(torch.tensor(b, device="cuda"), tol=1e-10)
+    assert ith == itd and np.array_equal(xh, xd.cpu().numpy())
+
+
+def test_fp32_local_form_reaches_tolerance():
+    mesh, kap, H = oracle_case("channels64")
+    G64 = _gpu("channels64", precision=0, eig_tol=1e-6)
+    G32 = _gpu("channels64", precision=1, eig_tol=1e-6)
+    b = torch.tensor(fem.load_vector(mesh), device="cuda")
+    x64, it64, _ = G64.solve(b, tol=1e-8)
+    x32, it32, rel32 = G32.solve(b, tol=1e-8)
+    true_rel = np.linalg.norm(fem.load_vector(mesh) - H.A @ x32.cpu().numpy()) / np.linalg.norm(b.cpu().numpy())
+    assert true_rel < 2e-8
+    assert it32 <= it64 + 5
+    assert G32.stats()["m_min"] == G64.stats()["m_min"]
