@@ -215,6 +215,28 @@ msdd_status msdd_band_factor(int batch, const int* n, int nmax, int bw, const do
 msdd_status msdd_band_solve(const msdd_band_batch* bb, int nrhs, double* X, void* stream);
 void msdd_band_destroy(msdd_band_batch* bb);
 
+/* Same solve as msdd_band_solve, for callers that must not allocate device
+ * memory during the call: code that holds a fixed memory budget or manages
+ * all device memory through its own pool, or a tight loop where a cudaMalloc
+ * or cudaFree would synchronise the device and stall other streams.
+ * The paper has no counterpart; this is an interface convenience.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *    The staging buffer is a file-scope device array of 2^21 doubles
+ *    (16 MiB) that every GPU which loads the library holds until exit.
+ *  - Limit: the batch's padded rows (32 * ceil(n[i] / 32) summed over i)
+ *    times nrhs must not exceed 2^21; otherwise MSDD_ERR_INVALID_ARG and
+ *    X is untouched (use msdd_band_solve).
+ *  - The first call on a device looks up the array's device address for that
+ *    device (cudaGetSymbolAddress, with that device current); make that first
+ *    call before any stream capture on it.
+ *  - All calls share the one array and it keeps the last call's contents
+ *    (padding rows are rewritten with zeros by every call).  Calls that
+ *    overlap on the GPU, e.g. from several threads or streams at once, race
+ *    on it and must be serialised by the caller.
+ * Arguments and layout of X are those of msdd_band_solve; returns after the
+ * work on `stream` has completed. */
+msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nrhs, double* X, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,19 +3,7 @@
 #include <new>
 #include <string>
 
-#include "hierarchy.cuh"
-
-struct msdd_hierarchy {
-    msdd::Hierarchy h;
-};
-
-struct msdd_band_batch {
-    msdd::TileBatch tb;
-    int nmax = 0;
-    std::vector<int> n;
-    msdd::DevBuf<long long> d_src, d_dst;
-    msdd::DevBuf<int> d_len;
-};
+#include "capi_types.cuh"
 
 namespace msdd {
 long long& kernel_launch_counter() {
@@ -32,6 +20,12 @@ msdd_status fail(msdd_status s, const std::string& msg) {
     g_last_error = msg;
     return s;
 }
+
+}  // namespace
+
+msdd_status msdd::set_last_error(msdd_status s, const std::string& msg) { return fail(s, msg); }
+
+namespace {
 
 template <class F>
 msdd_status guarded(F&& f) {

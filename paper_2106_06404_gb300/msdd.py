@@ -71,7 +71,7 @@ EXPORTED = [
     "msdd_default_options", "msdd_num_unknowns", "msdd_setup", "msdd_solve", "msdd_solve_host",
     "msdd_apply_preconditioner", "msdd_apply_operator", "msdd_assemble_rhs", "msdd_get_stats",
     "msdd_get_eigenvalues", "msdd_get_eigen_residuals", "msdd_get_fine_basis", "msdd_destroy", "msdd_last_error",
-    "msdd_band_factor", "msdd_band_solve", "msdd_band_destroy", "msdd_kernel_launches",
+    "msdd_band_factor", "msdd_band_solve", "msdd_band_destroy", "msdd_band_solve_noalloc", "msdd_kernel_launches",
 ]
 
 _lib = None
@@ -106,6 +106,7 @@ def load(path=LIB_PATH):
     lib.msdd_band_factor.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
                                      ctypes.c_double, vp, P(vp), ip]
     lib.msdd_band_solve.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.msdd_band_solve_noalloc.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.msdd_band_destroy.argtypes = [vp]
     lib.msdd_band_destroy.restype = None
     lib.msdd_kernel_launches.argtypes = []
@@ -314,6 +315,12 @@ class BandBatch:
     def solve(self, X):
         """Solve in place: X is (batch, nmax, nrhs) float64 CUDA."""
         _check(self._lib.msdd_band_solve(self._h, X.shape[2], ctypes.c_void_p(X.data_ptr()), _stream()))
+        return X
+
+    def solve_noalloc(self, X):
+        """Same as solve() through msdd_band_solve_noalloc: no device allocation in the call
+        (static 16 MiB staging array; overlapping calls must be serialised)."""
+        _check(self._lib.msdd_band_solve_noalloc(self._h, X.shape[2], ctypes.c_void_p(X.data_ptr()), _stream()))
         return X
 
     def close(self):
