@@ -86,7 +86,8 @@ typedef struct msdd_spectral {
 typedef struct msdd_options {
     int precision;       /* 0: FP64 everywhere ("plain");
                             1: FP32 fine-level factors and solves, FP64 elsewhere ("chosen") */
-    int block_p;         /* subspace block size; 0 selects min(nev_max + 8, 32) */
+    int block_p;         /* subspace block size; 0 selects min(nev_max + 4, 32) on the fine
+                            level and min(nev_max + 8, 32) on coarse levels */
     int eig_maxit;       /* subspace iterations per level (default 200) */
     double sigma;        /* shift of K = Abar + sigma B (default 1e-2) */
     double eig_tol;      /* eigen-residual tolerance (default 1e-6) */

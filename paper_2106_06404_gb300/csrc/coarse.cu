@@ -63,6 +63,31 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const GemmItem* __restrict
     }
 }
 
+// y_b = alpha * op(A_b) x_b + beta * y_b, one warp per output entry
+// (row of A, or column when transposed), eight warps per CTA.
+__global__ void __launch_bounds__(256) k_gemv_batched(const GemmItem* __restrict__ items, int transA, double alpha,
+                                                      const double* __restrict__ A, const double* __restrict__ x,
+                                                      double beta, double* __restrict__ y,
+                                                      const int* __restrict__ gdone) {
+    if (gdone && *gdone) return;
+    const GemmItem it = items[blockIdx.y];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * 8 + warp;
+    if (row >= it.m) return;
+    double s = 0.0;
+    if (transA) {
+        for (int k = lane; k < it.k; k += 32) s += A[it.aoff + (long long)k * it.lda + row] * x[it.boff + (long long)k * it.ldb];
+    } else {
+        const double* a = A + it.aoff + (long long)row * it.lda;
+        for (int k = lane; k < it.k; k += 32) s += a[k] * x[it.boff + (long long)k * it.ldb];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        double* dst = y + it.coff + (long long)row * it.ldc;
+        *dst = alpha * s + (beta != 0.0 ? beta * *dst : 0.0);
+    }
+}
+
 __global__ void k_dense_shift(const double* __restrict__ A, double* __restrict__ Kd, const long long* __restrict__ aoff,
                               const int* __restrict__ n_, const int* __restrict__ nown_, double sigma) {
     const int i = blockIdx.y;
@@ -244,6 +269,14 @@ int dot_blocks(long long n) { return (int)std::max(1u, std::min(ceil_div(n, 1024
 
 void dot_partial(const double* x, const double* y, long long n, double* partial, int nblocks, cudaStream_t s) {
     k_dot_partial<<<nblocks, 256, 0, s>>>(x, y, n, partial);
+    MSDD_LAUNCH_CHECK();
+}
+
+void gemv_batched(const GemmItem* d_items, int nitems, int transA, double alpha, const double* A, const double* x,
+                  double beta, double* y, int max_m, cudaStream_t s, const int* gdone) {
+    if (nitems == 0 || max_m == 0) return;
+    dim3 grid(ceil_div(max_m, 8), nitems);
+    k_gemv_batched<<<grid, 256, 0, s>>>(d_items, transA, alpha, A, x, beta, y, gdone);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -28,6 +28,11 @@ void gemm_batched(const GemmItem* d_items, int nitems, int transA, int transB, d
                   const double* B, double beta, double* C, int max_m, int max_n, cudaStream_t s,
                   const int* gdone = nullptr);
 
+// Batched matrix-vector products with the GemmItem geometry (n = 1 implied):
+// y[coff + r * ldc] = alpha * sum_k op(A)[r][k] x[boff + k * ldb] + beta * y[...].
+void gemv_batched(const GemmItem* d_items, int nitems, int transA, double alpha, const double* A, const double* x,
+                  double beta, double* y, int max_m, cudaStream_t s, const int* gdone = nullptr);
+
 // dst = src with rows of the own block (rows < nown) scaled by (1 + sigma)
 // on their own-own entries: K = Abar + sigma X Abar X for dense pencils.
 void dense_shift(const double* Abar, double* Kd, const long long* d_aoff, const int* d_n, const int* d_nown,

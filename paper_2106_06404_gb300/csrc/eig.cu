@@ -439,6 +439,7 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
 }
 
 // X = Y C, AX = AY C, BX = BY C on a block of 32 rows; residual partial sums.
+// Outputs (row, column < p) are spread over the threads, at most 4 each.
 __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, const double* __restrict__ AY,
                                                 const double* __restrict__ BY, double* __restrict__ X,
                                                 double* __restrict__ AX, double* __restrict__ BX,
@@ -456,21 +457,23 @@ __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, co
     if (r0 >= rows) return;
     const long long roff = roff_[i];
     const int t = threadIdx.x;
-    for (int e = t; e < PMAX * PMAX; e += TPB) sC[e / PMAX][e % PMAX] = C[(long long)i * PMAX * PMAX + e];
-    for (int e = t; e < ROWBLK * PMAX; e += TPB) {
-        int rr = e / PMAX, c = e % PMAX;
+    for (int e = t; e < p * p; e += TPB) sC[e / p][e % p] = C[(long long)i * PMAX * PMAX + (e / p) * PMAX + e % p];
+    for (int e = t; e < ROWBLK * p; e += TPB) {
+        int rr = e / p, c = e % p;
         int r = r0 + rr;
-        bool ok = r < n && c < p;
+        bool ok = r < n;
         long long idx = (roff + r) * ldx + c;
         sY[rr][c] = ok ? Y[idx] : 0.0;
         sA[rr][c] = ok ? AY[idx] : 0.0;
         sB[rr][c] = ok ? BY[idx] : 0.0;
     }
     __syncthreads();
-    const int rr = t >> 3, cb = t & 7;
-    double vnum[4], vden[4];
-    for (int q = 0; q < 4; ++q) {
-        int c = cb + 8 * q;
+    double vnum[4] = {0, 0, 0, 0}, vden[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int e = t + k * TPB;
+        if (e >= ROWBLK * p) break;
+        int rr = e / p, c = e % p;
         double x = 0.0, ax = 0.0, bx = 0.0;
         for (int j = 0; j < p; ++j) {
             double cj = sC[j][c];
@@ -479,22 +482,25 @@ __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, co
             bx += sB[rr][j] * cj;
         }
         int r = r0 + rr;
-        bool ok = r < n && c < p;
-        if (r < rows && c < ldx) {
+        if (r < rows) {
             long long idx = (roff + r) * ldx + c;
-            X[idx] = ok ? x : 0.0;
-            AX[idx] = ok ? ax : 0.0;
-            BX[idx] = ok ? bx : 0.0;
+            X[idx] = x;
+            AX[idx] = ax;
+            BX[idx] = bx;
         }
-        double th = c < p ? theta[i * PMAX + c] : 0.0;
-        double rv = ok ? ax - th * bx : 0.0;
-        vnum[q] = rv * rv;
-        vden[q] = ok ? bx * bx : 0.0;
+        double rv = ax - theta[i * PMAX + c] * bx;
+        vnum[k] = rv * rv;
+        vden[k] = bx * bx;
     }
     __syncthreads();   // sY / sA are reused for the residual sums
-    for (int q = 0; q < 4; ++q) {
-        sY[rr][cb + 8 * q] = vnum[q];
-        sA[rr][cb + 8 * q] = vden[q];
+    for (int e = t; e < ROWBLK * PMAX; e += TPB) { sY[e / PMAX][e % PMAX] = 0.0; sA[e / PMAX][e % PMAX] = 0.0; }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int e = t + k * TPB;
+        if (e >= ROWBLK * p) break;
+        sY[e / p][e % p] = vnum[k];
+        sA[e / p][e % p] = vden[k];
     }
     __syncthreads();
     if (t < PMAX) {
@@ -506,11 +512,6 @@ __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, co
     }
 }
 
-// Convergence decision shared by both residual measures.  done = 1: the m
-// selected pairs meet `tol` and the next Ritz value is settled clear of eta;
-// done = 3: the selected residuals stopped improving (no halving in 10
-// iterations) below sqrt(tol), the floor set by near-dependent directions of
-// a coarse generating system; done = 2: maxit reached.
 __device__ void decide(int i, const double* sres, const double* theta, int p, double sigma, double tol, double eta,
                        int nev_max, int it, int maxit, bool may_stop, int* done, int* m_, int* iters, int* n_active,
                        double* best, int* best_it) {

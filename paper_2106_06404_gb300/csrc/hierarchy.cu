@@ -68,12 +68,38 @@ int sum_nreg(const TileBatch& tb, cudaStream_t s) {
     return t;
 }
 
+// Dense (pseudo-)inverse of every factorised problem of a tile batch:
+// out[ooff[i] + r * ld[i] + c] = (K_i^+)[r][c] for r, c < n[i].  The identity
+// columns are solved in blocks of 32 columns, one CTA per (problem, block),
+// so the whole GPU works on it.
+void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long>& ooff, const std::vector<int>& ld,
+                   cudaStream_t st) {
+    int maxn = 0;
+    for (int v : tb.n) maxn = std::max(maxn, v);
+    const int lde = tb.max_K * NB;
+    DevBuf<double> E((size_t)tb.total_rows * lde);
+    tile_identity(tb, E.p, lde, st);
+    tile_solve(tb, E.p, lde, maxn, nullptr, st);
+    std::vector<CopyItem> ci(tb.P);
+    for (int i = 0; i < tb.P; ++i) {
+        ci[i].soff = tb.roff[i] * lde;
+        ci[i].lds = lde;
+        ci[i].doff = ooff[i];
+        ci[i].ldd = ld[i];
+        ci[i].rows = tb.n[i];
+        ci[i].cols = tb.n[i];
+    }
+    DevBuf<CopyItem> d_ci = upload_vec(ci, st);
+    copy_blocks(d_ci.p, tb.P, E.p, out, st);
+    MSDD_CUDA(cudaStreamSynchronize(st));
+}
+
 // Subspace iteration driver; `apply(X, AX, BX, skip)` applies Abar and B.
 // `tag` names the kernel families for profiling; `apply_bytes`/`apply_flops`
 // are the algorithmic amounts of one operator application per problem.
-template <class Apply>
-void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, cudaStream_t st, Prof& prof, const std::string& tag,
-             double apply_bytes, double apply_flops) {
+template <class Apply, class Solve>
+void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, cudaStream_t st, Prof& prof,
+             const std::string& tag, double apply_bytes, double apply_flops) {
     if (g.P == 0) return;
     eig_init(g, ep.seed, st);
     int pmax = 0;
@@ -96,7 +122,7 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, cudaStream_t st, Pr
         const double fr = (double)active / g.P;
         eig_form_rhs(g, ep.sigma, first, st);
         prof.begin(tag + "_solve", st);
-        tile_solve(g.K, g.W.p, g.ldx, pmax, g.done.p, st);
+        solve(pmax);
         prof.end(st, solve_b * fr, solve_f * fr);
         if (g.knorm && !first) {
             // test the current Ritz pairs before updating them
@@ -142,6 +168,12 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, cudaStream_t st, Pr
 
 Hierarchy::~Hierarchy() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (st2) {
+        cudaStreamSynchronize(st2);
+        cudaStreamDestroy(st2);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     if (own_stream && st) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
@@ -153,7 +185,8 @@ size_t Hierarchy::device_bytes() const {
     b += fdir.bytes() + fge.K.bytes() + cdir.bytes() + mdir.bytes() + mge.K.bytes();
     b += (fge.X.n + fge.AX.n + fge.BX.n + fge.Y.n + fge.AY.n + fge.BY.n + fge.W.n) * 8;
     b += (mge.X.n + mge.AX.n + mge.BX.n + mge.Y.n + mge.AY.n + mge.BY.n + mge.W.n) * 8;
-    b += (Phi.n + A1.n + Abar_m.n + K_m.n + Zb.n + Tm.n + A0.n + frhs.n + mrhs.n + v1.n + r0buf.n) * 8;
+    b += (Phi.n + A1.n + Abar_m.n + K_m.n + Zb.n + Tm.n + A0.n + frhs.n + v1.n + r0buf.n) * 8;
+    b += (Minv.n + A0inv.n + y0buf.n + z1t.n) * 8;
     b += (x.n + r.n + p.n + q.n + z.n) * 8;
     return b;
 }
@@ -166,6 +199,9 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
         MSDD_CUDA(cudaStreamCreate(&st));
         own_stream = true;
     }
+    MSDD_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     levels = dec.levels;
     L = levels - 1;
     prof.on = opt.profile != 0;
@@ -345,7 +381,7 @@ void Hierarchy::build_fine() {
 
     // ---- fine GEVPs
     t0 = Clock::now();
-    const int block_p = opt.block_p > 0 ? opt.block_p : std::min(spec.nev_max + 8, PMAX);
+    const int block_p = opt.block_p > 0 ? opt.block_p : std::min(spec.nev_max + 4, PMAX);
     fge.ldx = PMAX;
     fge.p.resize(Pf);
     for (int j = 0; j < Pf; ++j) fge.p[j] = std::min(block_p, nN[j]);
@@ -369,6 +405,7 @@ void Hierarchy::build_fine() {
             [=](const double* X, double* AX, double* BX, const int* skip) {
                 apply_neumann(gg, bx, cnt, fg->K, X, AX, BX, fg->ldx, block_p, skip, stream);
             },
+            [=](int pmax) { tile_solve(fg->K, fg->W.p, fg->ldx, pmax, fg->done.p, stream); },
             st, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9));
     fm = fge.m.download(st);
     {
@@ -546,8 +583,20 @@ void Hierarchy::build_coarse() {
         tile_from_dense(cdir, A1.p, d_so.p, d_ld.p, st);
         tile_factor(cdir, 0.0, st);
         check_status(cdir, st, "coarse factorisation");
-        r0buf.alloc(cdir.total_rows);
+        // A_0^{-1} explicitly: the coarse solve in CG is one GEMV over many CTAs
+        A0inv.alloc(n0 * n0);
+        dense_inverse(cdir, A0inv.p, {0}, {(int)n0}, st);
+        r0buf.alloc(n0);
         r0buf.zero(st);
+        y0buf.alloc(n0);
+        {
+            GemmItem a;
+            a.aoff = 0; a.lda = (int)n0;
+            a.boff = 0; a.ldb = 1;
+            a.coff = 0; a.ldc = 1;
+            a.m = (int)n0; a.n = 1; a.k = (int)n0;
+            d_gemm_y0 = upload_vec(std::vector<GemmItem>{a}, st);
+        }
         stats.level_dim[0] = n0;
         stats.subdomains[0] = 1;
         MSDD_CUDA(cudaStreamSynchronize(st));
@@ -579,6 +628,15 @@ void Hierarchy::build_coarse() {
         tile_from_dense(mdir, A1.p, d_so.p, d_ld.p, st);
         tile_factor(mdir, 0.0, st);
         check_status(mdir, st, "level-1 Dirichlet factorisation");
+        // A_{1,i}^{-1} explicitly: level-1 solves in CG are batched GEMVs
+        moff.assign(Pm, 0);
+        long long mt = 0;
+        for (int i = 0; i < Pm; ++i) {
+            moff[i] = mt;
+            mt += (long long)nown[i] * nown[i];
+        }
+        Minv.alloc(mt);
+        dense_inverse(mdir, Minv.p, moff, nown, st);
     }
     // generating systems: own children, then neighbours meeting T_{1,i}
     gens.assign(Pm, {});
@@ -661,6 +719,8 @@ void Hierarchy::build_coarse() {
         tile_from_dense(mge.K, K_m.p, d_aoff.p, d_ngen.p, st);
         tile_factor(mge.K, opt.reg_tol, st);
         stats.null_pivots[1] = sum_nreg(mge.K, st);
+        // K^+ explicitly (overwrites K_m): every later solve is a batched GEMM
+        dense_inverse(mge.K, K_m.p, aoff, ngen, st);
     }
     stats.phase_ms[4] += ms_since(t0);
     t0 = Clock::now();
@@ -684,9 +744,33 @@ void Hierarchy::build_coarse() {
     GevpBatch* mg = &mge;
     int PmL = Pm;
     cudaStream_t stream = st;
+    std::vector<GemmItem> kitems(Pm);
+    int pmax_m = 0;
+    for (int i = 0; i < Pm; ++i) {
+        GemmItem& it = kitems[i];
+        it.aoff = aoff[i];
+        it.lda = ngen[i];
+        it.boff = mge.K.roff[i] * mge.ldx;
+        it.ldb = mge.ldx;
+        it.coff = mge.K.roff[i] * mge.ldx;
+        it.ldc = mge.ldx;
+        it.m = ngen[i];
+        it.n = mge.p[i];
+        it.k = ngen[i];
+        pmax_m = std::max(pmax_m, mge.p[i]);
+    }
+    DevBuf<GemmItem> d_kitems = upload_vec(kitems, st);
+    DevBuf<double> Wt(mge.W.n);
+    const GemmItem* dki = d_kitems.p;
+    const double* Kinv = K_m.p;
+    double* Wtp = Wt.p;
     run_eig(mge, ep,
             [=](const double* X, double* AX, double* BX, const int* skip) {
                 apply_dense_pencil(Ab, dao, dng, dno, mg->K, X, AX, BX, mg->ldx, block_p, skip, PmL, ngen_max, stream);
+            },
+            [=](int) {
+                gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, mg->W.p, 0.0, Wtp, ngen_max, pmax_m, stream);
+                MSDD_CUDA(cudaMemcpyAsync(mg->W.p, Wtp, mg->W.n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
             },
             st, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
     mm = mge.m.download(st);
@@ -775,29 +859,25 @@ void Hierarchy::build_coarse() {
         tile_from_dense(cdir, A0.p, d_so.p, d_ld.p, st);
         tile_factor(cdir, 0.0, st);
         check_status(cdir, st, "coarsest factorisation");
+        A0inv.alloc(n0 * n0);
+        dense_inverse(cdir, A0inv.p, {0}, {(int)n0}, st);
     }
-    r0buf.alloc(cdir.total_rows);
+    r0buf.alloc(n0);
     r0buf.zero(st);
-    mrhs.alloc(mdir.total_rows);
-    mrhs.zero(st);
+    y0buf.alloc(n0);
     v1.alloc(n1);
+    z1t.alloc(n1);
     {
-        std::vector<long long> sv(Pm), sm(Pm);
-        std::vector<int> len(Pm);
-        seg_maxlen = 0;
+        std::vector<GemmItem> gy1, g0, g1;
+        gemm_y1_maxm = gemm_r0_maxm = gemm_z1_maxm = 0;
         for (int i = 0; i < Pm; ++i) {
-            sv[i] = c1first[i];
-            sm[i] = mdir.roff[i];
-            len[i] = nown[i];
-            seg_maxlen = std::max(seg_maxlen, nown[i]);
-        }
-        d_seg_v1 = upload_vec(sv, st);
-        d_seg_mrhs = upload_vec(sm, st);
-        d_seg_len = upload_vec(len, st);
-        std::vector<GemmItem> g0, g1;
-        gemm_r0_maxm = 0;
-        gemm_z1_maxm = 0;
-        for (int i = 0; i < Pm; ++i) {
+            GemmItem y;   // z1t_i = A_{1,i}^{-1} v1_i
+            y.aoff = moff[i]; y.lda = nown[i];
+            y.boff = c1first[i]; y.ldb = 1;
+            y.coff = c1first[i]; y.ldc = 1;
+            y.m = nown[i]; y.n = 1; y.k = nown[i];
+            gy1.push_back(y);
+            gemm_y1_maxm = std::max(gemm_y1_maxm, nown[i]);
             GemmItem a;   // r0_i = Zb_i^T v1_i
             a.aoff = zoff[i]; a.lda = ldz;
             a.boff = c1first[i]; a.ldb = 1;
@@ -805,7 +885,7 @@ void Hierarchy::build_coarse() {
             a.m = mm[i]; a.n = 1; a.k = nown[i];
             g0.push_back(a);
             gemm_r0_maxm = std::max(gemm_r0_maxm, mm[i]);
-            GemmItem b;   // v1_i += Zb_i y0_i
+            GemmItem b;   // z1t_i += Zb_i y0_i
             b.aoff = zoff[i]; b.lda = ldz;
             b.boff = c0off[i]; b.ldb = 1;
             b.coff = c1first[i]; b.ldc = 1;
@@ -813,8 +893,15 @@ void Hierarchy::build_coarse() {
             g1.push_back(b);
             gemm_z1_maxm = std::max(gemm_z1_maxm, nown[i]);
         }
+        d_gemm_y1 = upload_vec(gy1, st);
         d_gemm_r0 = upload_vec(g0, st);
         d_gemm_z1 = upload_vec(g1, st);
+        GemmItem a;   // y0 = A_0^{-1} r0
+        a.aoff = 0; a.lda = (int)n0;
+        a.boff = 0; a.ldb = 1;
+        a.coff = 0; a.ldc = 1;
+        a.m = (int)n0; a.n = 1; a.k = (int)n0;
+        d_gemm_y0 = upload_vec(std::vector<GemmItem>{a}, st);
     }
     stats.level_dim[0] = n0;
     stats.subdomains[0] = 1;
@@ -826,20 +913,23 @@ void Hierarchy::apply_prec(const double* rr, double* zz, const int* gdone) {
     double* r1 = levels == 2 ? r0buf.p : v1.p;
     fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, rr, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p,
                          d_c1off.p, r1, Pf, gdone, st);
-    tile_solve(fdir, frhs.p, 1, 1, nullptr, st, gdone);
+    // the coarse chain runs on a second stream, concurrently with the fine solves
+    MSDD_CUDA(cudaEventRecord(ev_fork, st));
+    MSDD_CUDA(cudaStreamWaitEvent(st2, ev_fork, 0));
     const double* zc;
     if (levels == 2) {
-        tile_solve(cdir, r0buf.p, 1, 1, nullptr, st, gdone);
-        zc = r0buf.p;
+        gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st2, gdone);
+        zc = y0buf.p;
     } else {
-        segment_copy(d_seg_v1.p, d_seg_mrhs.p, d_seg_len.p, Pm, seg_maxlen, v1.p, mrhs.p, 0, gdone, st);
-        tile_solve(mdir, mrhs.p, 1, 1, nullptr, st, gdone);
-        gemm_batched(d_gemm_r0.p, Pm, 1, 0, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, 1, st, gdone);
-        tile_solve(cdir, r0buf.p, 1, 1, nullptr, st, gdone);
-        segment_copy(d_seg_mrhs.p, d_seg_v1.p, d_seg_len.p, Pm, seg_maxlen, mrhs.p, v1.p, 0, gdone, st);
-        gemm_batched(d_gemm_z1.p, Pm, 0, 0, 1.0, Zb.p, r0buf.p, 1.0, v1.p, gemm_z1_maxm, 1, st, gdone);
-        zc = v1.p;
+        gemv_batched(d_gemm_y1.p, Pm, 0, 1.0, Minv.p, v1.p, 0.0, z1t.p, gemm_y1_maxm, st2, gdone);
+        gemv_batched(d_gemm_r0.p, Pm, 1, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, st2, gdone);
+        gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st2, gdone);
+        gemv_batched(d_gemm_z1.p, Pm, 0, 1.0, Zb.p, y0buf.p, 1.0, z1t.p, gemm_z1_maxm, st2, gdone);
+        zc = z1t.p;
     }
+    MSDD_CUDA(cudaEventRecord(ev_join, st2));
+    tile_solve(fdir, frhs.p, 1, 1, nullptr, st, gdone);
+    MSDD_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
     fine_combine(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p, zc, zz,
                  rr, partial.p, nblocks, gdone, st);
 }

@@ -80,6 +80,8 @@ struct Hierarchy {
     msdd_decomp dec{};
     cudaStream_t st = nullptr;
     bool own_stream = false;           // created when the caller passes no stream
+    cudaStream_t st2 = nullptr;        // coarse chain of the preconditioner
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int levels = 0, L = 0;
     long long nun = 0;
     msdd_stats stats{};
@@ -121,18 +123,18 @@ struct Hierarchy {
     DevBuf<double> Zb;
     std::vector<long long> c0off;
     DevBuf<double> Tm;              // A_1 Z_1
-    DevBuf<double> mrhs, v1;
-    DevBuf<long long> d_seg_v1, d_seg_mrhs;
-    DevBuf<int> d_seg_len;
-    int seg_maxlen = 0;
-    DevBuf<GemmItem> d_gemm_r0, d_gemm_z1;
-    int gemm_r0_maxm = 0, gemm_z1_maxm = 0;
+    DevBuf<double> v1, z1t;         // restricted residual / coarse correction on V_{h,1}
+    std::vector<long long> moff;
+    DevBuf<double> Minv;            // explicit A_{1,i}^{-1}
+    DevBuf<GemmItem> d_gemm_y1, d_gemm_r0, d_gemm_z1;
+    int gemm_y1_maxm = 0, gemm_r0_maxm = 0, gemm_z1_maxm = 0;
 
     // ---- coarsest level
     long long n0 = 0;
     TileBatch cdir;
-    DevBuf<double> A0;
-    DevBuf<double> r0buf;
+    DevBuf<double> A0, A0inv;       // A_0 and its explicit inverse
+    DevBuf<double> r0buf, y0buf;
+    DevBuf<GemmItem> d_gemm_y0;
 
     // ---- CG
     DevBuf<double> x, r, p, q, z, partial;

@@ -165,6 +165,11 @@ __global__ void __launch_bounds__(TPB) k_tile_solve(
     const int t = threadIdx.x;
     const int r = t >> 3, c0 = t & 7;
     (void)n_;
+    // this CTA handles the columns [32 * blockIdx.y, 32 * blockIdx.y + 32)
+    const int c_lo = blockIdx.y * NB;
+    X += c_lo;
+    ncols = min(NB, ncols - c_lo);
+    if (ncols <= 0) return;
 
     // forward: z_R = T_R (x_R - sum_J L_RJ z_J)
     for (int R = 0; R < K; ++R) {
@@ -290,15 +295,16 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
     const long long* __restrict__ toff_, const long long* __restrict__ roff_, double* __restrict__ X,
     const int* __restrict__ gdone)
 {
-    extern __shared__ double zs[];
-    __shared__ double accs[NB];
-    __shared__ double part[S1T / 32][NB + 1];
+    extern __shared__ __align__(16) unsigned char zs_raw[];
+    T* zs = reinterpret_cast<T*>(zs_raw);
+    __shared__ T accs[NB];
+    __shared__ T part[S1T / 32][NB + 1];
     if (gdone && *gdone) return;
     const int i = blockIdx.x;
     const int kb = kb_[i], K = K_[i];
     const long long toff = toff_[i], roff = roff_[i];
     const int t = threadIdx.x;
-    for (int e = t; e < K * NB; e += S1T) zs[e] = X[roff + e];
+    for (int e = t; e < K * NB; e += S1T) zs[e] = T(X[roff + e]);
     __syncthreads();
 
     // forward: z_R = T_R (x_R - sum_{J<R} L_RJ z_J)
@@ -308,21 +314,21 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
         load_row_chunks<T, KBP>(cur, tiles, toff, kb, 0, K, r, c0, true);
         for (int R = 0; R < K; ++R) {
             load_row_chunks<T, KBP>(nxt, tiles, toff, kb, R + 1, K, r, c0, true);
-            double acc = 0.0;
+            T acc = T(0);
 #pragma unroll
             for (int d = 1; d <= KBP; ++d) {
                 if (d > kb || R - d < 0) continue;
-                const double* zj = zs + (R - d) * NB + c0;
+                const T* zj = zs + (R - d) * NB + c0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) acc += (double)cur[d][q] * zj[q];
+                for (int q = 0; q < 8; ++q) acc += cur[d][q] * zj[q];
             }
             acc += __shfl_xor_sync(0xffffffffu, acc, 1);
             acc += __shfl_xor_sync(0xffffffffu, acc, 2);
             if ((t & 3) == 0) accs[r] = zs[R * NB + r] - acc;
             __syncthreads();
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s += (double)cur[0][q] * accs[c0 + q];
+            for (int q = 0; q < 8; ++q) s += cur[0][q] * accs[c0 + q];
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
             if ((t & 3) == 0) zs[R * NB + r] = s;
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
                 for (int q = 0; q < 8; ++q) cur[d][q] = nxt[d][q];
         }
     }
-    for (int e = t; e < K * NB; e += S1T) zs[e] *= (double)dinv[roff + e];
+    for (int e = t; e < K * NB; e += S1T) zs[e] *= dinv[roff + e];
     __syncthreads();
     // backward: x_R = T_R^T (D_R^{-1} z_R - sum_{I>R} L_IR^T x_I)
     {
@@ -342,30 +348,30 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
         load_row_chunks<T, KBP>(cur, tiles, toff, kb, K - 1, K, lane, k0, false);
         for (int R = K - 1; R >= 0; --R) {
             load_row_chunks<T, KBP>(nxt, tiles, toff, kb, R - 1, K, lane, k0, false);
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
             for (int d = 1; d <= KBP; ++d) {
                 if (d > kb || R + d >= K) continue;
-                const double* xi = zs + (R + d) * NB + k0;
+                const T* xi = zs + (R + d) * NB + k0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) s += (double)cur[d][q] * xi[q];
+                for (int q = 0; q < 8; ++q) s += cur[d][q] * xi[q];
             }
             part[warp][lane] = s;
             __syncthreads();
             if (warp == 0) {
-                double v = 0.0;
+                T v = T(0);
 #pragma unroll
                 for (int w = 0; w < S1T / 32; ++w) v += part[w][lane];
                 accs[lane] = zs[R * NB + lane] - v;
             }
             __syncthreads();
-            double s2 = 0.0;
+            T s2 = T(0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s2 += (double)cur[0][q] * accs[k0 + q];
+            for (int q = 0; q < 8; ++q) s2 += cur[0][q] * accs[k0 + q];
             part[warp][lane] = s2;
             __syncthreads();
             if (warp == 0) {
-                double v = 0.0;
+                T v = T(0);
 #pragma unroll
                 for (int w = 0; w < S1T / 32; ++w) v += part[w][lane];
                 zs[R * NB + lane] = v;
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
                 for (int q = 0; q < 8; ++q) cur[d][q] = nxt[d][q];
         }
     }
-    for (int e = t; e < K * NB; e += S1T) X[roff + e] = zs[e];
+    for (int e = t; e < K * NB; e += S1T) X[roff + e] = (double)zs[e];
 }
 
 // One right-hand side, any kb (dense coarse matrices): tiles are read as
@@ -460,6 +466,175 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1_dense(
         }
     }
     for (int e = t; e < K * NB; e += S1T) X[roff + e] = zs[e];
+}
+
+
+// ------------------------------------------------------------------ solve, several right-hand sides, band
+// For kb <= KBR: the tiles of step R+1 are copied into shared memory with
+// cp.async while step R computes, and the last kb solution blocks stay in a
+// shared ring (no re-reading of earlier blocks from global memory).  Thread
+// (row r = t/8, columns t%8 + 8q) owns up to 4 entries of a 32 x ncols block.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <typename T>
+struct RingLayout {
+    static constexpr int LDT = sizeof(T) == 4 ? NB + 4 : NB + 2;   // 16-byte aligned padded rows
+    static constexpr int LDZ = NB + 1;
+};
+
+template <typename T>
+__device__ __forceinline__ void async_tile(T* dst, const T* __restrict__ src) {
+    constexpr int PER = 16 / (int)sizeof(T);
+    constexpr int LDT = RingLayout<T>::LDT;
+    for (int ch = threadIdx.x; ch < NB2 / PER; ch += TPB) {
+        int e = ch * PER;
+        cp_async16(dst + (e / NB) * LDT + (e % NB), src + e);
+    }
+}
+
+template <typename T, int KBR>
+__global__ void __launch_bounds__(TPB) k_tile_solve_ring(
+    const T* __restrict__ tiles, const T* __restrict__ dinv, const int* __restrict__ kb_, const int* __restrict__ K_,
+    const long long* __restrict__ toff_, const long long* __restrict__ roff_, double* __restrict__ X, int ldx,
+    int ncols, const int* __restrict__ skip, const int* __restrict__ gdone)
+{
+    constexpr int LDT = RingLayout<T>::LDT, LDZ = RingLayout<T>::LDZ, S = KBR + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* St = reinterpret_cast<T*>(smem_raw);                 // [2][S][NB][LDT]
+    T* Zr = St + 2 * S * NB * LDT;                          // [S][NB][LDZ]
+    T* Acc = Zr + S * NB * LDZ;                             // [NB][LDZ]
+    const int i = blockIdx.x;
+    if (skip && skip[i]) return;
+    if (gdone && *gdone) return;
+    const int kb = kb_[i], K = K_[i];
+    const long long toff = toff_[i], roff = roff_[i];
+    const int t = threadIdx.x;
+    const int r = t >> 3, cb = t & 7;
+    auto stage_tile = [&](int st, int slot) { return St + ((st * S + slot) * NB) * LDT; };
+    auto issue = [&](int st, int R, bool fwd) {
+        if (R >= 0 && R < K) {
+            async_tile(stage_tile(st, 0), tiles + tile_index(toff, kb, R, R));
+            for (int d = 1; d <= kb; ++d) {
+                int o = fwd ? R - d : R + d;
+                if (o < 0 || o >= K) continue;
+                async_tile(stage_tile(st, d), tiles + (fwd ? tile_index(toff, kb, R, o) : tile_index(toff, kb, o, R)));
+            }
+        }
+        cp_async_commit();
+    };
+    // forward: z_R = T_R (x_R - sum_J L_RJ z_J)
+    issue(0, 0, true);
+    for (int R = 0; R < K; ++R) {
+        const int st = R & 1;
+        issue(st ^ 1, R + 1, true);
+        cp_async_wait1();
+        __syncthreads();
+        T acc[4];
+        const double* xr = X + (roff + (long long)R * NB + r) * ldx;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int c = cb + 8 * q;
+            acc[q] = c < ncols ? T(xr[c]) : T(0);
+        }
+        for (int d = 1; d <= kb; ++d) {
+            if (R - d < 0) break;
+            const T* L = stage_tile(st, d) + r * LDT;
+            const T* Z = Zr + ((R - d) % S) * NB * LDZ;
+#pragma unroll 8
+            for (int k = 0; k < NB; ++k) {
+                T l = L[k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Acc[r * LDZ + cb + 8 * q] = acc[q];
+        __syncthreads();
+        const T* Tt = stage_tile(st, 0) + r * LDT;
+        T out[4] = {0, 0, 0, 0};
+        for (int k = 0; k <= r; ++k) {
+            T l = Tt[k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) out[q] += l * Acc[k * LDZ + cb + 8 * q];
+        }
+        T* Zw = Zr + (R % S) * NB * LDZ;
+        double* xw = X + (roff + (long long)R * NB + r) * ldx;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int c = cb + 8 * q;
+            Zw[r * LDZ + c] = out[q];
+            if (c < ncols) xw[c] = (double)out[q];
+        }
+        __syncthreads();
+    }
+    // backward: x_R = T_R^T (D_R^{-1} z_R - sum_I L_IR^T x_I)
+    issue(0, K - 1, false);
+    for (int R = K - 1, it = 0; R >= 0; --R, ++it) {
+        const int st = it & 1;
+        issue(st ^ 1, R - 1, false);
+        cp_async_wait1();
+        __syncthreads();
+        T acc[4];
+        const double* xr = X + (roff + (long long)R * NB + r) * ldx;
+        const T dr = dinv[roff + (long long)R * NB + r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int c = cb + 8 * q;
+            acc[q] = c < ncols ? dr * T(xr[c]) : T(0);
+        }
+        for (int d = 1; d <= kb; ++d) {
+            if (R + d >= K) break;
+            const T* L = stage_tile(st, d);
+            const T* Z = Zr + ((R + d) % S) * NB * LDZ;
+#pragma unroll 8
+            for (int k = 0; k < NB; ++k) {
+                T l = L[k * LDT + r];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Acc[r * LDZ + cb + 8 * q] = acc[q];
+        __syncthreads();
+        const T* Tt = stage_tile(st, 0);
+        T out[4] = {0, 0, 0, 0};
+        for (int k = r; k < NB; ++k) {
+            T l = Tt[k * LDT + r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) out[q] += l * Acc[k * LDZ + cb + 8 * q];
+        }
+        T* Zw = Zr + (R % S) * NB * LDZ;
+        double* xw = X + (roff + (long long)R * NB + r) * ldx;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int c = cb + 8 * q;
+            Zw[r * LDZ + c] = out[q];
+            if (c < ncols) xw[c] = (double)out[q];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int KBR>
+size_t ring_smem_bytes() {
+    return sizeof(T) * ((size_t)2 * (KBR + 1) * NB * RingLayout<T>::LDT + (size_t)(KBR + 2) * NB * RingLayout<T>::LDZ);
+}
+
+__global__ void k_fill_identity(double* __restrict__ E, const int* __restrict__ n_, const int* __restrict__ K_,
+                                const long long* __restrict__ roff_, int lde) {
+    const int i = blockIdx.y;
+    const int n = n_[i];
+    const long long rows = (long long)K_[i] * NB;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * lde;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long r = e / lde, c = e % lde;
+        E[(roff_[i] + r) * lde + c] = (r == c && r < n) ? 1.0 : 0.0;
+    }
 }
 
 template <typename T>
@@ -549,6 +724,13 @@ void tile_from_dense(TileBatch& tb, const double* src, const long long* d_soff, 
     MSDD_LAUNCH_CHECK();
 }
 
+void tile_identity(const TileBatch& tb, double* E, int lde, cudaStream_t s) {
+    if (tb.P == 0) return;
+    dim3 grid(64, tb.P);
+    k_fill_identity<<<grid, 256, 0, s>>>(E, tb.d_n.p, tb.d_K.p, tb.d_roff.p, lde);
+    MSDD_LAUNCH_CHECK();
+}
+
 void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
     if (tb.P == 0) return;
     if (tb.prec)
@@ -563,8 +745,8 @@ void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
 void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* skip, cudaStream_t s,
                 const int* gdone) {
     if (tb.P == 0) return;
-    if (ncols > PMAX || ncols > ldx) throw std::runtime_error("tile_solve: too many columns");
-    const size_t zbytes = (size_t)tb.max_K * NB * sizeof(double);
+    if (ncols > ldx) throw std::runtime_error("tile_solve: more columns than the leading dimension");
+    const size_t zbytes = (size_t)tb.max_K * NB * sizeof(double);   // upper bound for both precisions
     if (ncols == 1 && ldx == 1 && skip == nullptr && zbytes <= 160 * 1024) {
         int maxkb = 0;
         for (int v : tb.kb) maxkb = std::max(maxkb, v);
@@ -588,11 +770,29 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
         MSDD_LAUNCH_CHECK();
         return;
     }
+    int maxkb = 0;
+    for (int v : tb.kb) maxkb = std::max(maxkb, v);
+    if (maxkb <= 2 && ncols <= NB) {
+        if (tb.prec) {
+            size_t b = ring_smem_bytes<float, 2>();
+            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_ring<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            k_tile_solve_ring<float, 2><<<tb.P, TPB, b, s>>>(
+                tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
+        } else {
+            size_t b = ring_smem_bytes<double, 2>();
+            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_ring<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            k_tile_solve_ring<double, 2><<<tb.P, TPB, b, s>>>(
+                tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
+        }
+        MSDD_LAUNCH_CHECK();
+        return;
+    }
+    const dim3 grid(tb.P, (ncols + NB - 1) / NB);
     if (tb.prec)
-        k_tile_solve<float><<<tb.P, TPB, 0, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,
+        k_tile_solve<float><<<grid, TPB, 0, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,
                                                 tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
     else
-        k_tile_solve<double><<<tb.P, TPB, 0, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,
+        k_tile_solve<double><<<grid, TPB, 0, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,
                                                  tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
     MSDD_LAUNCH_CHECK();
 }

@@ -46,8 +46,11 @@ void tile_from_dense(TileBatch& tb, const double* src, const long long* d_soff, 
                      cudaStream_t s);
 // In-place LDL^T of every problem; fills d_status (0 ok, k+1 = failing row) and d_nreg.
 void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s);
+// E (total_rows x lde) <- per problem the identity of order n[i] (zero elsewhere).
+void tile_identity(const TileBatch& tb, double* E, int lde, cudaStream_t s);
 // Solve K X = B in place.  X is double, row-major, problem i rows at
-// (roff[i] + r) * ldx, columns 0..ncols-1.  `skip` (device, per problem, may be
+// (roff[i] + r) * ldx, columns 0..ncols-1 (any ncols <= ldx; blocks of 32
+// columns go to separate CTAs).  `skip` (device, per problem, may be
 // null) skips problems whose flag is non-zero; `gdone` (device, may be null)
 // skips everything when non-zero.
 void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* skip, cudaStream_t s,
