@@ -278,7 +278,8 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel family of the chosen form (live CUDA events)
     prof = st_chosen["prof"]
-    fam = max(prof, key=lambda k: prof[k]["ms"])
+    # the dominant kernel family with algorithmic amounts attached
+    fam = max((k for k in prof if prof[k]["bytes"] > 0 or prof[k]["flops"] > 0), key=lambda k: prof[k]["ms"])
     pf = prof[fam]
     peaks = {}
     try:

@@ -58,6 +58,9 @@ void eig_form_y(GevpBatch& g, double sigma, bool first, cudaStream_t s);
 void eig_form_y_knorm(GevpBatch& g, double sigma, cudaStream_t s);
 // Convergence test on the K^+-norm residuals (regularised coarse pencils).
 void eig_check_knorm(GevpBatch& g, const EigParams& ep, int it, cudaStream_t s);
+// FP32 start phase: X <- orthonormal basis of span(W) by Euclidean CholQR
+// (Gram with FP32 products, FP64 Cholesky of the scaled p x p Gram).
+void eig_cholqr32(GevpBatch& g, cudaStream_t s);
 // H = Y^T AY, M = Y^T BY.
 void eig_gram(GevpBatch& g, cudaStream_t s);
 // Rayleigh-Ritz: theta ascending, C with C^T M C = I.

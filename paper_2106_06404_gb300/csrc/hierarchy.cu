@@ -97,11 +97,33 @@ void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long
 // Subspace iteration driver; `apply(X, AX, BX, skip)` applies Abar and B.
 // `tag` names the kernel families for profiling; `apply_bytes`/`apply_flops`
 // are the algorithmic amounts of one operator application per problem.
-template <class Apply, class Solve>
-void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, cudaStream_t st, Prof& prof,
-             const std::string& tag, double apply_bytes, double apply_flops) {
+template <class Apply, class Solve, class BApply32>
+void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply32 bapply32, int fp32_iters,
+             cudaStream_t st, Prof& prof, const std::string& tag, double apply_bytes, double apply_flops) {
     if (g.P == 0) return;
     eig_init(g, ep.seed, st);
+    // FP32 start phase: block inverse iteration Y = K~^{-1} B X with Euclidean
+    // CholQR, all in FP32 arithmetic; the FP64 phase below starts from its
+    // subspace and alone decides convergence.
+    int pm0 = 0;
+    for (int v : g.p) pm0 = std::max(pm0, v);
+    double sb0 = 0, sf0 = 0;
+    for (int i = 0; i < g.P; ++i) {
+        double n = g.K.n[i], b = g.K.b[i], p = g.p[i];
+        sb0 += 2.0 * n * (b + 1) * (g.K.prec ? 4.0 : 8.0) + 4.0 * n * p * 8.0;
+        sf0 += 4.0 * n * b * p;
+    }
+    for (int it = 0; it < fp32_iters; ++it) {
+        prof.begin(tag + "_fp32_start_other", st);
+        bapply32(g.X.p, g.W.p);
+        prof.end(st, 0.0, 0.0);
+        prof.begin(tag + "_solve", st);
+        solve(pm0);
+        prof.end(st, sb0, sf0);
+        prof.begin(tag + "_fp32_start_other", st);
+        eig_cholqr32(g, st);
+        prof.end(st, 0.0, 0.0);
+    }
     int pmax = 0;
     for (int v : g.p) pmax = std::max(pmax, v);
     // algorithmic amounts per problem: band solve (two sweeps) and the
@@ -187,7 +209,7 @@ size_t Hierarchy::device_bytes() const {
     b += (mge.X.n + mge.AX.n + mge.BX.n + mge.Y.n + mge.AY.n + mge.BY.n + mge.W.n) * 8;
     b += (Phi.n + A1.n + Abar_m.n + K_m.n + Zb.n + Tm.n + A0.n + frhs.n + v1.n + r0buf.n) * 8;
     b += (Minv.n + A0inv.n + y0buf.n + z1t.n) * 8;
-    b += (x.n + r.n + p.n + q.n + z.n) * 8;
+    b += (x.n + r.n + p.n + q.n + z.n + stencil.n) * 8;
     return b;
 }
 
@@ -230,8 +252,10 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     build_fine();
     build_coarse();
 
-    // CG buffers
+    // CG buffers and the stored global stencil
     x.alloc(nun); r.alloc(nun); p.alloc(nun); q.alloc(nun); z.alloc(nun);
+    stencil.alloc((size_t)nun * (g.dim == 3 ? 27 : 9));
+    global_stencil(g, stencil.p, st);
     nblocks = dot_blocks(nun);
     partial.alloc(nblocks);
     sc.alloc(1);
@@ -406,6 +430,8 @@ void Hierarchy::build_fine() {
                 apply_neumann(gg, bx, cnt, fg->K, X, AX, BX, fg->ldx, block_p, skip, stream);
             },
             [=](int pmax) { tile_solve(fg->K, fg->W.p, fg->ldx, pmax, fg->done.p, stream); },
+            [=](const double* X, double* W) { apply_b32(gg, bx, cnt, fg->K, X, W, fg->ldx, block_p, stream); },
+            opt.precision == 1 ? opt.fp32_start_iters : 0,
             st, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9));
     fm = fge.m.download(st);
     {
@@ -772,6 +798,7 @@ void Hierarchy::build_coarse() {
                 gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, mg->W.p, 0.0, Wtp, ngen_max, pmax_m, stream);
                 MSDD_CUDA(cudaMemcpyAsync(mg->W.p, Wtp, mg->W.n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
             },
+            [=](const double*, double*) {}, 0,
             st, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
     mm = mge.m.download(st);
     {
@@ -941,7 +968,7 @@ void Hierarchy::build_graph() {
     MSDD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const int* gd = &sc.p->done;
     for (int k = 0; k < chunk; ++k) {
-        apply_global_dot(g, p.p, q.p, partial.p, nblocks, gd, st);
+        spmv_stencil_dot(g, stencil.p, p.p, q.p, partial.p, nblocks, gd, st);
         pcg_fin_alpha(sc.p, partial.p, nblocks, st);
         pcg_axpy(sc.p, x.p, r.p, p.p, q.p, nun, partial.p, nblocks, st);
         pcg_fin_rr(sc.p, partial.p, nblocks, st);

@@ -128,8 +128,7 @@ __global__ void k_assemble(Geom g, const ProbBox* __restrict__ boxes, const int*
     for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n * noff;
          w += (long long)gridDim.x * blockDim.x) {
         int r = (int)(w / noff), oi = (int)(w % noff);
-        int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
-        if (g.dim == 2) o[2] = 0;
+        int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, g.dim == 3 ? oi / 9 - 1 : 0};
         int x[3], y[3];
         box_coords(r, lo, hi, g.dim, x);
         for (int d = 0; d < 3; ++d) y[d] = x[d] + o[d];
@@ -166,7 +165,7 @@ __global__ void k_apply_neumann(Geom g, const ProbBox* __restrict__ boxes, const
         for (int c = 0; c < 8; ++c) { ax[c] = 0.0; bx[c] = 0.0; }
         const double chix = chi_at(g, pb, count, x);
         for (int oi = 0; oi < noff; ++oi) {
-            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, g.dim == 3 ? oi / 9 - 1 : 0};
             int y[3];
             for (int d = 0; d < 3; ++d) y[d] = x[d] + o[d];
             if (!in_box(pb.nlo, pb.nhi, y, g.dim)) continue;
@@ -191,6 +190,143 @@ __global__ void k_apply_neumann(Geom g, const ProbBox* __restrict__ boxes, const
     }
 }
 
+// FP32 versions of the element entries and stencil coefficients (used only
+// by the FP32 start phase of the eigensolver).
+__device__ __forceinline__ float elem_entry_f(const Geom& g, long long e, int a, int b) {
+    if (g.coeff_kind == 0) return (float)g.coeff[e] * (float)c_S[a][b];
+    return (float)elem_entry(g, e, a, b);
+}
+
+__device__ float stencil_coef_f(const Geom& g, const int* elo, const int* ehi, const int x[3], const int o[3]) {
+    int lo[3], cnt[3];
+    for (int d = 0; d < 3; ++d) {
+        if (d >= g.dim) { lo[d] = 0; cnt[d] = 1; continue; }
+        if (o[d] < 0) { lo[d] = x[d] - 1; cnt[d] = 1; }
+        else if (o[d] > 0) { lo[d] = x[d]; cnt[d] = 1; }
+        else { lo[d] = x[d] - 1; cnt[d] = 2; }
+    }
+    float v = 0.f;
+    for (int kz = 0; kz < cnt[2]; ++kz)
+        for (int ky = 0; ky < cnt[1]; ++ky)
+            for (int kx = 0; kx < cnt[0]; ++kx) {
+                int l[3] = {lo[0] + kx, lo[1] + ky, lo[2] + kz};
+                bool inside = true;
+                for (int d = 0; d < g.dim; ++d)
+                    if (l[d] < elo[d] || l[d] >= ehi[d]) inside = false;
+                if (!inside) continue;
+                int a = 0, b = 0;
+                for (int d = 0; d < g.dim; ++d) {
+                    a |= (x[d] - l[d]) << d;
+                    b |= (x[d] + o[d] - l[d]) << d;
+                }
+                long long e = l[0] + (long long)g.n[0] * (l[1] + (long long)g.n[1] * l[2]);
+                v += elem_entry_f(g, e, a, b);
+            }
+    return v;
+}
+
+// W = X Abar X applied to X in FP32 arithmetic (one thread per row and chunk
+// of 8 columns); rows beyond n are written as zero.
+__global__ void k_apply_b32(Geom g, const ProbBox* __restrict__ boxes, const int* __restrict__ count,
+                            const long long* __restrict__ roff_, const int* __restrict__ K_,
+                            const double* __restrict__ X, double* __restrict__ W, int ldx, int ncols) {
+    const int i = blockIdx.y;
+    const ProbBox pb = boxes[i];
+    const int n = box_size(pb.nlo, pb.nhi, g.dim);
+    const int rows = K_[i] * NB;
+    const int nchunk = (ncols + 7) / 8;
+    const long long roff = roff_[i];
+    const int noff = g.dim == 3 ? 27 : 9;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)rows * nchunk;
+         w += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(w / nchunk), c0 = (int)(w % nchunk) * 8;
+        int c1 = min(ncols, c0 + 8);
+        float bx[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) bx[c] = 0.f;
+        float chix = 0.f;
+        if (r < n) {
+            int x[3];
+            box_coords(r, pb.nlo, pb.nhi, g.dim, x);
+            chix = (float)chi_at(g, pb, count, x);
+            if (chix != 0.f) {
+                for (int oi = 0; oi < noff; ++oi) {
+                    int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, g.dim == 3 ? oi / 9 - 1 : 0};
+                    int y[3];
+                    for (int d = 0; d < 3; ++d) y[d] = x[d] + o[d];
+                    if (!in_box(pb.nlo, pb.nhi, y, g.dim)) continue;
+                    float chiy = (float)chi_at(g, pb, count, y);
+                    if (chiy == 0.f) continue;
+                    float a = stencil_coef_f(g, pb.elo, pb.ehi, x, o) * chiy;
+                    const double* xr = X + (roff + box_index(pb.nlo, pb.nhi, y, g.dim)) * ldx;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c0 + c < c1) bx[c] += a * (float)xr[c0 + c];
+                }
+            }
+        }
+        double* wr = W + (roff + r) * ldx;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c0 + c < c1) wr[c0 + c] = (double)(chix * bx[c]);
+    }
+}
+
+// Stencil coefficients of the global operator: S[o * nun + u] = A(u, u + o)
+// for the 3^d offsets o (zero where the neighbour is not an unknown).
+__global__ void k_global_stencil(Geom g, double* __restrict__ S, long long nun) {
+    int elo[3] = {0, 0, 0};
+    int ehi[3] = {g.n[0], g.n[1], g.n[2]};
+    const int noff = g.dim == 3 ? 27 : 9;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
+        int xc[3];
+        long long rem = u;
+        for (int d = 0; d < 3; ++d) {
+            if (d >= g.dim) { xc[d] = 0; continue; }
+            xc[d] = g.ulo[d] + (int)(rem % g.ushape[d]);
+            rem /= g.ushape[d];
+        }
+        for (int oi = 0; oi < noff; ++oi) {
+            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, g.dim == 3 ? oi / 9 - 1 : 0};
+            int yc[3];
+            for (int d = 0; d < 3; ++d) yc[d] = xc[d] + o[d];
+            S[(long long)oi * nun + u] = in_box(g.ulo, g.uhi, yc, g.dim) ? stencil_coef(g, elo, ehi, xc, o) : 0.0;
+        }
+    }
+}
+
+// q = A p from the stored stencil (one thread per unknown, neighbours of an
+// x-row are contiguous), plus partial sums of p.q.
+__global__ void __launch_bounds__(256) k_spmv_stencil_dot(Geom g, const double* __restrict__ S,
+                                                          const double* __restrict__ p, double* __restrict__ q,
+                                                          long long nun, double* __restrict__ partial,
+                                                          const int* __restrict__ done) {
+    __shared__ double red[256];
+    if (done && *done) return;
+    const int noff = g.dim == 3 ? 27 : 9;
+    const long long sx = 1, sy = g.ushape[0], sz = (long long)g.ushape[0] * g.ushape[1];
+    double part = 0.0;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int oi = 0; oi < noff; ++oi) {
+            double c = S[(long long)oi * nun + u];
+            if (c != 0.0) {
+                long long v = u + (oi % 3 - 1) * sx + ((oi / 3) % 3 - 1) * sy + (g.dim == 3 ? oi / 9 - 1 : 0) * sz;
+                acc += c * p[v];
+            }
+        }
+        q[u] = acc;
+        part += acc * p[u];
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
 __global__ void k_apply_global(Geom g, const double* __restrict__ x, double* __restrict__ y, long long nun) {
     int elo[3] = {0, 0, 0};
     int ehi[3] = {g.n[0], g.n[1], g.n[2]};
@@ -205,7 +341,7 @@ __global__ void k_apply_global(Geom g, const double* __restrict__ x, double* __r
         }
         double acc = 0.0;
         for (int oi = 0; oi < noff; ++oi) {
-            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, g.dim == 3 ? oi / 9 - 1 : 0};
             int yc[3];
             for (int d = 0; d < 3; ++d) yc[d] = xc[d] + o[d];
             if (!in_box(g.ulo, g.uhi, yc, g.dim)) continue;
@@ -278,6 +414,28 @@ void apply_neumann(const Geom& g, const ProbBox* d_boxes, const int* d_count, co
     if (layout.P == 0) return;
     dim3 grid(64, layout.P);
     k_apply_neumann<<<grid, 128, 0, s>>>(g, d_boxes, d_count, layout.d_roff.p, X, AX, BX, ldx, ncols, skip);
+    MSDD_LAUNCH_CHECK();
+}
+
+void apply_b32(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout, const double* X,
+               double* W, int ldx, int ncols, cudaStream_t s) {
+    if (layout.P == 0) return;
+    dim3 grid(64, layout.P);
+    k_apply_b32<<<grid, 128, 0, s>>>(g, d_boxes, d_count, layout.d_roff.p, layout.d_K.p, X, W, ldx, ncols);
+    MSDD_LAUNCH_CHECK();
+}
+
+void global_stencil(const Geom& g, double* S, cudaStream_t s) {
+    long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    unsigned blocks = (unsigned)std::min<long long>(ceil_div(nun, 256), 152 * 16);
+    k_global_stencil<<<blocks, 256, 0, s>>>(g, S, nun);
+    MSDD_LAUNCH_CHECK();
+}
+
+void spmv_stencil_dot(const Geom& g, const double* S, const double* p, double* q, double* partial, int nblocks,
+                      const int* done, cudaStream_t s) {
+    long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    k_spmv_stencil_dot<<<nblocks, 256, 0, s>>>(g, S, p, q, nun, partial, done);
     MSDD_LAUNCH_CHECK();
 }
 
@@ -401,7 +559,7 @@ __global__ void k_apply_global_dot(Geom g, const double* __restrict__ x, double*
         }
         double acc = 0.0;
         for (int oi = 0; oi < noff; ++oi) {
-            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+            int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, g.dim == 3 ? oi / 9 - 1 : 0};
             int yc[3];
             for (int d = 0; d < 3; ++d) yc[d] = xc[d] + o[d];
             if (!in_box(g.ulo, g.uhi, yc, g.dim)) continue;

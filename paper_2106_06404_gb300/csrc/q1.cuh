@@ -88,6 +88,19 @@ void assemble_local_tiles(const Geom& g, const ProbBox* d_boxes, const int* d_co
 void apply_neumann(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout,
                    const double* X, double* AX, double* BX, int ldx, int ncols, const int* skip, cudaStream_t s);
 
+// W = X Abar X applied to X in FP32 arithmetic (start phase of the
+// eigensolver); padding rows of W are zeroed.
+void apply_b32(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout, const double* X,
+               double* W, int ldx, int ncols, cudaStream_t s);
+
+// Stored 3^d-point stencil of the global operator: S[o * n + u] = A(u, u + o),
+// offsets o lexicographic (x fastest) in {-1, 0, 1}^d, zero where u + o is
+// not an unknown.  n * 3^d doubles.
+void global_stencil(const Geom& g, double* S, cudaStream_t s);
+// q = A p from the stored stencil and partial sums of p.q (nblocks CTAs).
+void spmv_stencil_dot(const Geom& g, const double* S, const double* p, double* q, double* partial, int nblocks,
+                      const int* done, cudaStream_t s);
+
 // y = A x on the unknowns (Dirichlet nodes eliminated).
 void apply_global(const Geom& g, const double* x, double* y, cudaStream_t s);
 

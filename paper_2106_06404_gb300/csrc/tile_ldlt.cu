@@ -479,7 +479,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+constexpr int RING_STAGES = 3;
 
 template <typename T>
 struct RingLayout {
@@ -503,11 +505,15 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
     const long long* __restrict__ toff_, const long long* __restrict__ roff_, double* __restrict__ X, int ldx,
     int ncols, const int* __restrict__ skip, const int* __restrict__ gdone)
 {
-    constexpr int LDT = RingLayout<T>::LDT, LDZ = RingLayout<T>::LDZ, S = KBR + 1;
+    // NST-stage cp.async pipeline: stage s holds the tiles of one step and the
+    // 32 x ldx block of X (right-hand side in the forward sweep, z in the
+    // backward sweep) it starts from; NST - 1 steps are in flight.
+    constexpr int LDT = RingLayout<T>::LDT, LDZ = RingLayout<T>::LDZ, S = KBR + 1, NST = RING_STAGES;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* St = reinterpret_cast<T*>(smem_raw);                 // [2][S][NB][LDT]
-    T* Zr = St + 2 * S * NB * LDT;                          // [S][NB][LDZ]
-    T* Acc = Zr + S * NB * LDZ;                             // [NB][LDZ]
+    T* St = reinterpret_cast<T*>(smem_raw);                               // [NST][S][NB][LDT]
+    double* Sx = reinterpret_cast<double*>(St + (size_t)NST * S * NB * LDT);  // [NST][NB][ldx]
+    T* Zr = reinterpret_cast<T*>(Sx + (size_t)NST * NB * ldx);            // [S][NB][LDZ]
+    T* Acc = Zr + S * NB * LDZ;                                           // [NB][LDZ]
     const int i = blockIdx.x;
     if (skip && skip[i]) return;
     if (gdone && *gdone) return;
@@ -515,7 +521,8 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
     const long long toff = toff_[i], roff = roff_[i];
     const int t = threadIdx.x;
     const int r = t >> 3, cb = t & 7;
-    auto stage_tile = [&](int st, int slot) { return St + ((st * S + slot) * NB) * LDT; };
+    const int qn = (ncols + 7) / 8;          // columns cb + 8q, q < qn, owned by this thread
+    auto stage_tile = [&](int st, int slot) { return St + ((size_t)(st * S + slot) * NB) * LDT; };
     auto issue = [&](int st, int R, bool fwd) {
         if (R >= 0 && R < K) {
             async_tile(stage_tile(st, 0), tiles + tile_index(toff, kb, R, R));
@@ -524,22 +531,25 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
                 if (o < 0 || o >= K) continue;
                 async_tile(stage_tile(st, d), tiles + (fwd ? tile_index(toff, kb, R, o) : tile_index(toff, kb, o, R)));
             }
+            const double* src = X + (roff + (long long)R * NB) * ldx;
+            double* dst = Sx + (size_t)st * NB * ldx;
+            for (int ch = t; ch < NB * ldx / 2; ch += TPB) cp_async16(dst + 2 * ch, src + 2 * ch);
         }
         cp_async_commit();
     };
     // forward: z_R = T_R (x_R - sum_J L_RJ z_J)
-    issue(0, 0, true);
+    for (int k = 0; k < NST - 1; ++k) issue(k, k, true);
     for (int R = 0; R < K; ++R) {
-        const int st = R & 1;
-        issue(st ^ 1, R + 1, true);
-        cp_async_wait1();
+        const int st = R % NST;
+        issue((R + NST - 1) % NST, R + NST - 1, true);
+        cp_async_wait_n<NST - 1>();
         __syncthreads();
         T acc[4];
-        const double* xr = X + (roff + (long long)R * NB + r) * ldx;
+        const double* xr = Sx + (size_t)st * NB * ldx + r * ldx;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int c = cb + 8 * q;
-            acc[q] = c < ncols ? T(xr[c]) : T(0);
+            acc[q] = (q < qn && c < ncols) ? T(xr[c]) : T(0);
         }
         for (int d = 1; d <= kb; ++d) {
             if (R - d < 0) break;
@@ -549,7 +559,8 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
             for (int k = 0; k < NB; ++k) {
                 T l = L[k];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
+                for (int q = 0; q < 4; ++q)
+                    if (q < qn) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
             }
         }
 #pragma unroll
@@ -560,7 +571,8 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
         for (int k = 0; k <= r; ++k) {
             T l = Tt[k];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) out[q] += l * Acc[k * LDZ + cb + 8 * q];
+            for (int q = 0; q < 4; ++q)
+                if (q < qn) out[q] += l * Acc[k * LDZ + cb + 8 * q];
         }
         T* Zw = Zr + (R % S) * NB * LDZ;
         double* xw = X + (roff + (long long)R * NB + r) * ldx;
@@ -568,24 +580,26 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
         for (int q = 0; q < 4; ++q) {
             int c = cb + 8 * q;
             Zw[r * LDZ + c] = out[q];
-            if (c < ncols) xw[c] = (double)out[q];
+            if (q < qn && c < ncols) xw[c] = (double)out[q];
         }
         __syncthreads();
     }
+    cp_async_wait_n<0>();
+    __syncthreads();
     // backward: x_R = T_R^T (D_R^{-1} z_R - sum_I L_IR^T x_I)
-    issue(0, K - 1, false);
+    for (int k = 0; k < NST - 1; ++k) issue(k, K - 1 - k, false);
     for (int R = K - 1, it = 0; R >= 0; --R, ++it) {
-        const int st = it & 1;
-        issue(st ^ 1, R - 1, false);
-        cp_async_wait1();
+        const int st = it % NST;
+        issue((it + NST - 1) % NST, R - (NST - 1), false);
+        cp_async_wait_n<NST - 1>();
         __syncthreads();
         T acc[4];
-        const double* xr = X + (roff + (long long)R * NB + r) * ldx;
+        const double* xr = Sx + (size_t)st * NB * ldx + r * ldx;
         const T dr = dinv[roff + (long long)R * NB + r];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int c = cb + 8 * q;
-            acc[q] = c < ncols ? dr * T(xr[c]) : T(0);
+            acc[q] = (q < qn && c < ncols) ? dr * T(xr[c]) : T(0);
         }
         for (int d = 1; d <= kb; ++d) {
             if (R + d >= K) break;
@@ -595,7 +609,8 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
             for (int k = 0; k < NB; ++k) {
                 T l = L[k * LDT + r];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
+                for (int q = 0; q < 4; ++q)
+                    if (q < qn) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
             }
         }
 #pragma unroll
@@ -606,7 +621,8 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
         for (int k = r; k < NB; ++k) {
             T l = Tt[k * LDT + r];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) out[q] += l * Acc[k * LDZ + cb + 8 * q];
+            for (int q = 0; q < 4; ++q)
+                if (q < qn) out[q] += l * Acc[k * LDZ + cb + 8 * q];
         }
         T* Zw = Zr + (R % S) * NB * LDZ;
         double* xw = X + (roff + (long long)R * NB + r) * ldx;
@@ -614,15 +630,17 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
         for (int q = 0; q < 4; ++q) {
             int c = cb + 8 * q;
             Zw[r * LDZ + c] = out[q];
-            if (c < ncols) xw[c] = (double)out[q];
+            if (q < qn && c < ncols) xw[c] = (double)out[q];
         }
         __syncthreads();
     }
+    cp_async_wait_n<0>();
 }
 
 template <typename T, int KBR>
-size_t ring_smem_bytes() {
-    return sizeof(T) * ((size_t)2 * (KBR + 1) * NB * RingLayout<T>::LDT + (size_t)(KBR + 2) * NB * RingLayout<T>::LDZ);
+size_t ring_smem_bytes(int ldx) {
+    return sizeof(T) * ((size_t)RING_STAGES * (KBR + 1) * NB * RingLayout<T>::LDT + (size_t)(KBR + 2) * NB * RingLayout<T>::LDZ) +
+           sizeof(double) * (size_t)RING_STAGES * NB * ldx;
 }
 
 __global__ void k_fill_identity(double* __restrict__ E, const int* __restrict__ n_, const int* __restrict__ K_,
@@ -772,14 +790,17 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
     }
     int maxkb = 0;
     for (int v : tb.kb) maxkb = std::max(maxkb, v);
-    if (maxkb <= 2 && ncols <= NB) {
+    // the ring kernel stages whole 32 x ldx blocks of X with 16-byte copies
+    const bool ring_ok = maxkb <= 2 && ncols <= NB && ldx <= NB && ldx % 2 == 0 &&
+                         ((uintptr_t)X % 16) == 0;
+    if (ring_ok) {
         if (tb.prec) {
-            size_t b = ring_smem_bytes<float, 2>();
+            size_t b = ring_smem_bytes<float, 2>(ldx);
             MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_ring<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
             k_tile_solve_ring<float, 2><<<tb.P, TPB, b, s>>>(
                 tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
         } else {
-            size_t b = ring_smem_bytes<double, 2>();
+            size_t b = ring_smem_bytes<double, 2>(ldx);
             MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_ring<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
             k_tile_solve_ring<double, 2><<<tb.P, TPB, b, s>>>(
                 tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);

@@ -46,7 +46,8 @@ class Spectral(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("block_p", ctypes.c_int), ("eig_maxit", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("eig_tol", ctypes.c_double), ("reg_tol", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("profile", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("profile", ctypes.c_int),
+                ("fp32_start_iters", ctypes.c_int)]
 
 
 class KernelProf(ctypes.Structure):
@@ -178,7 +179,7 @@ class Hierarchy:
 
     def __init__(self, n, coeff, parts, overlap, levels, group, nev_max, eta, dirichlet_faces=0b1,
                  precision=0, block_p=0, eig_maxit=200, sigma=1e-2, eig_tol=1e-6, reg_tol=1e-10, seed=12345,
-                 allow_eig_unconverged=False, profile=False):
+                 allow_eig_unconverged=False, profile=False, fp32_start_iters=None):
         torch = _torch()
         lib = load()
         self._lib = lib
@@ -202,6 +203,8 @@ class Hierarchy:
         o.sigma, o.eig_tol, o.reg_tol, o.seed = float(sigma), float(eig_tol), float(reg_tol), int(seed)
         o.stream = torch.cuda.current_stream().cuda_stream
         o.profile = 1 if profile else 0
+        if fp32_start_iters is not None:
+            o.fp32_start_iters = int(fp32_start_iters)
         h = ctypes.c_void_p()
         st = lib.msdd_setup(ctypes.byref(self.mesh), ctypes.byref(c), ctypes.byref(d), ctypes.byref(s),
                             ctypes.byref(o), ctypes.byref(h))
