@@ -90,4 +90,43 @@ __host__ __device__ inline double hash_uniform(uint64_t key) {
     return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
+// ---- FP64 <-> FP32 conversions on the integer pipe.  On this GPU the
+// conversion instructions share the narrow FP64 pipe; these bit-level
+// versions (IEEE 754 binary64/binary32 layouts) keep mixed-precision kernels
+// off it.  Round to nearest even; magnitudes below 2^-126 are flushed to a
+// signed zero (both directions); overflow gives infinity; NaN stays NaN.
+#ifdef __CUDACC__
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const int ef = e - 1023 + 127;
+    const unsigned m = ((hi & 0x000fffffu) << 3) | (lo >> 29);   // leading 23 mantissa bits
+    const unsigned rest = lo & 0x1fffffffu;                        // the 29 dropped bits
+    unsigned v = ((unsigned)ef << 23) + m;
+    v += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;   // a carry may give infinity
+    if (ef <= 0) v = 0u;
+    if (ef >= 255) v = (e == 0x7ff && ((hi & 0x000fffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+    return __uint_as_float(sign | v);
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned m = u & 0x007fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    if (e == 0u) { hi = sign; lo = 0u; }
+    if (e == 0xffu) { hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x00080000u : 0u); lo = m << 29; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+// load a double as T / store a T as double
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return f64_to_f32(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
+#endif
+
 }  // namespace msdd

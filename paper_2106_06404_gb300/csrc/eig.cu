@@ -195,161 +195,228 @@ __global__ void __launch_bounds__(TPB) k_gram(const double* __restrict__ Y, cons
 }
 
 // ---- block-wide symmetric eigen-solver (parallel cyclic Jacobi, round robin)
+// FP64 divisions and square roots are long instruction sequences on the
+// FP64 pipe; the kernels below take their reciprocal square roots from an
+// FP32 seed refined by two Newton steps r <- r (3 - x r^2) / 2 (relative
+// error ~1e-7 -> ~1e-14 -> rounding level).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return x > 0.0 ? 1.0 / sqrt(x) : 0.0;
+    double r = f32_to_f64(rsqrtf(f64_to_f32(x)));
+    r = r * (1.5 - 0.5 * x * r * r);
+    r = r * (1.5 - 0.5 * x * r * r);
+    return r;
+}
+
+// A pair (a, b) is rotated only while |S_ab| > rel_tol sqrt(|S_aa S_bb|)
+// and |S_ab| > floor_abs (floor_abs is tied to the scale of S, so that
+// pairs with a zero diagonal entry terminate).  The test is evaluated in
+// FP32 for both precisions (a threshold test needs no more).
+__device__ __forceinline__ bool pair_active_f(float app, float aqq, float apq, float rel_tol, float floor_abs) {
+    const float a = fabsf(apq);
+    return a > floor_abs && a > rel_tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq));
+}
 template <typename T>
-__device__ void rot_params(T app, T aqq, T apq, T& c, T& s) {
-    const T tiny = sizeof(T) == 4 ? T(1e-9) : T(1e-18);
-    if (apq == T(0) || fabs(apq) <= tiny * sqrt(fabs(app * aqq))) { c = T(1); s = T(0); return; }
-    T th = (aqq - app) / (T(2) * apq);
-    T t;
-    if (fabs(th) > T(1e15)) t = T(0.5) / th;
-    else t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
-    c = T(1) / sqrt(t * t + T(1));
+__device__ __forceinline__ bool pair_active(T app, T aqq, T apq, T rel_tol, T floor_abs);
+template <>
+__device__ __forceinline__ bool pair_active<float>(float app, float aqq, float apq, float rel_tol, float floor_abs) {
+    return pair_active_f(app, aqq, apq, rel_tol, floor_abs);
+}
+template <>
+__device__ __forceinline__ bool pair_active<double>(double app, double aqq, double apq, double rel_tol,
+                                                    double floor_abs) {
+    return pair_active_f(f64_to_f32(app), f64_to_f32(aqq), f64_to_f32(apq), f64_to_f32(rel_tol),
+                         fmaxf(f64_to_f32(floor_abs), 1e-37f));
+}
+
+// FP32: the Jacobi angle with fast reciprocal / reciprocal square root (the
+// pair is then zeroed explicitly; the FP32 sweeps only seed the FP64 ones).
+__device__ __forceinline__ void rot_params(float app, float aqq, float apq, float& c, float& s) {
+    const float th = __fdividef(aqq - app, 2.0f * apq);
+    float t;
+    if (!(fabsf(th) <= 1e15f)) {
+        t = __fdividef(0.5f, th);
+    } else {
+        const float r2 = fmaf(th, th, 1.0f);
+        t = copysignf(__fdividef(1.0f, fabsf(th) + r2 * rsqrtf(r2)), th);
+    }
+    c = rsqrtf(fmaf(t, t, 1.0f));
     s = t * c;
+}
+// FP64: the angle from FP32 arithmetic; c and s are then rescaled by
+// (c^2 + s^2)^{-1/2} ~ 1 - d/2 + 3 d^2 / 8, d = c^2 + s^2 - 1 evaluated
+// without rounding error by FP32 error-free products (c^2 - 1 and the sum
+// with s^2 are exact by Sterbenz' lemma since c^2 >= 1/2), and stored as
+// FP64 sums c + c (-d/2 + 3 d^2/8).  The rotation is orthogonal to FP64
+// accuracy and reduces the pair by ~1e-7 instead of annihilating it (the
+// pair is not zeroed; later sweeps finish it).
+__device__ __forceinline__ void rot_params(double app, double aqq, double apq, double& c, double& s) {
+    const float num = f64_to_f32(aqq - app), den = 2.0f * f64_to_f32(apq);
+    if (!(den != 0.0f && isfinite(num) && isfinite(den))) {
+        const double th = (aqq - app) / (2.0 * apq);
+        const double t = (fabs(th) > 1e15) ? 0.5 / th : (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        c = 1.0 / sqrt(1.0 + t * t);
+        s = t * c;
+        return;
+    }
+    float cf, sf;
+    rot_params(0.0f, num, 0.5f * den, cf, sf);            // th = num / den
+    const float c2h = cf * cf, c2l = fmaf(cf, cf, -c2h);
+    const float s2h = sf * sf, s2l = fmaf(sf, sf, -s2h);
+    const float d = ((c2h - 1.0f) + s2h) + (c2l + s2l);
+    const float corr = d * fmaf(0.375f, d, -0.5f);
+    c = f32_to_f64(cf) + f32_to_f64(cf * corr);
+    s = f32_to_f64(sf) + f32_to_f64(sf * corr);
 }
 
 // S (q x q, q even) is overwritten by its eigenvalues on the diagonal; V =
-// eigenvectors.  Sweeps stop when the off-diagonal mass falls below
-// rel_tol^2 of the Frobenius mass, or after max_sweeps.
+// eigenvectors.  Stops after a check finds no active pair, or after
+// max_sweeps sweeps.  Diagonal entries >= 1e299 mark dropped columns (their
+// off-diagonal entries are zero) and are left out of the scale.
+//
+// One step of the round-robin ordering rotates q/2 disjoint pairs; the
+// two-sided update J^T S J is done in one pass over the 2 x 2 blocks
+// (pair j rows, pair jj columns), which the disjoint pairs cover exactly
+// once, together with the column update of V.  The pair parameters are
+// double-buffered, so a step in which no pair rotates costs one barrier.
 template <typename T>
-__device__ void block_jacobi(T (*S)[LD], T (*V)[LD], int q, T* sc, T* ss, int* sa, int* sb, double* red,
-                             double rel_tol2, int max_sweeps) {
-    const int t = threadIdx.x;
+__device__ void block_jacobi(T (*S)[LD], T (*V)[LD], int q, T rel_tol, T floor_rel, int max_sweeps) {
+    __shared__ T sc[2][PMAX / 2], ss[2][PMAX / 2];
+    __shared__ int sa[2][PMAX / 2], sb[2][PMAX / 2];
+    __shared__ double s_scale;
+    const int t = threadIdx.x, h = q / 2;
     for (int e = t; e < q * q; e += TPB) V[e / q][e % q] = (e / q == e % q) ? T(1) : T(0);
-    __syncthreads();
-    double fro = 0.0;
-    {
-        double part = 0.0;
-        for (int e = t; e < q * q; e += TPB) part += (double)S[e / q][e % q] * (double)S[e / q][e % q];
-        red[t] = part;
-        __syncthreads();
-        for (int w = TPB / 2; w > 0; w >>= 1) {
-            if (t < w) red[t] += red[t + w];
-            __syncthreads();
+    if (t < 32) {
+        double m = 0.0;
+        for (int k = t; k < q; k += 32) {
+            double v = fabs((double)S[k][k]);
+            if (v < 1e299) m = fmax(m, v);
         }
-        fro = red[0];
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (t == 0) s_scale = m;
     }
+    __syncthreads();
+    const T floor_abs = fmax((T)(floor_rel * s_scale), sizeof(T) == 4 ? T(1e-30) : T(1e-290));
+    int par = 0;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double part = 0.0;
+        int active = 0;
         for (int e = t; e < q * q; e += TPB) {
             int a = e / q, b = e % q;
-            if (a != b) part += (double)S[a][b] * (double)S[a][b];
+            if (a < b && pair_active<T>(S[a][a], S[b][b], S[a][b], rel_tol, floor_abs)) active = 1;
         }
-        red[t] = part;
-        __syncthreads();
-        for (int w = TPB / 2; w > 0; w >>= 1) {
-            if (t < w) red[t] += red[t + w];
-            __syncthreads();
-        }
-        double off = red[0];
-        __syncthreads();
-        if (off <= rel_tol2 * fro || fro == 0.0) break;
-        for (int step = 0; step < q - 1; ++step) {
-            if (t < q / 2) {
+        if (!__syncthreads_or(active)) break;
+        for (int step = 0; step < q - 1; ++step, par ^= 1) {
+            if (t < h) {
                 // circle method: position 0 fixed, the others rotate
                 int pos1 = t, pos2 = q - 1 - t;
                 int a = pos1 == 0 ? 0 : 1 + (pos1 - 1 + step) % (q - 1);
                 int b = 1 + (pos2 - 1 + step) % (q - 1);
                 if (a > b) { int tmp = a; a = b; b = tmp; }
-                T c, s;
-                rot_params<T>(S[a][a], S[b][b], S[a][b], c, s);
-                sa[t] = a; sb[t] = b; sc[t] = c; ss[t] = s;
+                T c = T(1), s = T(0);
+                if (pair_active<T>(S[a][a], S[b][b], S[a][b], rel_tol, floor_abs)) rot_params(S[a][a], S[b][b], S[a][b], c, s);
+                sa[par][t] = a; sb[par][t] = b; sc[par][t] = c; ss[par][t] = s;
             }
             __syncthreads();
-            for (int e = t; e < (q / 2) * q; e += TPB) {    // rows
-                int j = e / q, k = e % q;
-                if (ss[j] == T(0)) continue;
-                int a = sa[j], b = sb[j];
-                T x = S[a][k], y = S[b][k];
-                S[a][k] = sc[j] * x - ss[j] * y;
-                S[b][k] = ss[j] * x + sc[j] * y;
-            }
-            __syncthreads();
-            for (int e = t; e < (q / 2) * q; e += TPB) {    // columns of S and V
-                int j = e / q, k = e % q;
-                if (ss[j] == T(0)) continue;
-                int a = sa[j], b = sb[j];
-                T x = S[k][a], y = S[k][b];
-                S[k][a] = sc[j] * x - ss[j] * y;
-                S[k][b] = ss[j] * x + sc[j] * y;
-                T u = V[k][a], v = V[k][b];
-                V[k][a] = sc[j] * u - ss[j] * v;
-                V[k][b] = ss[j] * u + sc[j] * v;
+            bool any = false;
+            for (int j = 0; j < h; ++j) any |= ss[par][j] != T(0);
+            if (!any) continue;
+            const int nblk = h * h;
+            for (int e = t; e < nblk + q * h; e += TPB) {
+                if (e < nblk) {
+                    const int j = e / h, jj = e % h;
+                    const T sj = ss[par][j], sjj = ss[par][jj];
+                    if (sj == T(0) && sjj == T(0)) continue;
+                    const T cj = sc[par][j], cjj = sc[par][jj];
+                    const int x1 = sa[par][j], x2 = sb[par][j], y1 = sa[par][jj], y2 = sb[par][jj];
+                    const T b11 = S[x1][y1], b12 = S[x1][y2], b21 = S[x2][y1], b22 = S[x2][y2];
+                    const T r11 = cj * b11 - sj * b21, r12 = cj * b12 - sj * b22;      // rows x1, x2
+                    const T r21 = sj * b11 + cj * b21, r22 = sj * b12 + cj * b22;
+                    T n11 = cjj * r11 - sjj * r12, n12 = sjj * r11 + cjj * r12;          // columns y1, y2
+                    T n21 = cjj * r21 - sjj * r22, n22 = sjj * r21 + cjj * r22;
+                    if (sizeof(T) == 4 && j == jj) { n12 = T(0); n21 = T(0); }        // exact angle: annihilated
+                    S[x1][y1] = n11; S[x1][y2] = n12; S[x2][y1] = n21; S[x2][y2] = n22;
+                } else {
+                    const int e2 = e - nblk, k = e2 / h, jj = e2 % h;
+                    const T sjj = ss[par][jj];
+                    if (sjj == T(0)) continue;
+                    const T cjj = sc[par][jj];
+                    const int y1 = sa[par][jj], y2 = sb[par][jj];
+                    const T u = V[k][y1], v = V[k][y2];
+                    V[k][y1] = cjj * u - sjj * v;
+                    V[k][y2] = sjj * u + cjj * v;
+                }
             }
             __syncthreads();
         }
+    }
+}
+
+// D = E F for q x q blocks in shared memory (E transposed when tE); four
+// partial sums per entry keep the dependent FP64 chains short.
+__device__ __forceinline__ void smem_gemm(double (*D)[LD], const double (*E)[LD], const double (*F)[LD], int q,
+                                          bool tE) {
+    for (int e = threadIdx.x; e < q * q; e += TPB) {
+        const int a = e / q, b = e % q;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int j = 0;
+        if (tE) {
+            for (; j + 3 < q; j += 4) {
+                v0 += E[j][a] * F[j][b];
+                v1 += E[j + 1][a] * F[j + 1][b];
+                v2 += E[j + 2][a] * F[j + 2][b];
+                v3 += E[j + 3][a] * F[j + 3][b];
+            }
+            for (; j < q; ++j) v0 += E[j][a] * F[j][b];
+        } else {
+            for (; j + 3 < q; j += 4) {
+                v0 += E[a][j] * F[j][b];
+                v1 += E[a][j + 1] * F[j + 1][b];
+                v2 += E[a][j + 2] * F[j + 2][b];
+                v3 += E[a][j + 3] * F[j + 3][b];
+            }
+            for (; j < q; ++j) v0 += E[a][j] * F[j][b];
+        }
+        D[a][b] = (v0 + v1) + (v2 + v3);
     }
 }
 
 // Eigen-decomposition of the symmetric q x q FP64 matrix S (overwritten by
 // its eigenvalues on the diagonal, eigenvectors in V).  Most rotations are
 // done in FP32 on a copy; the FP32 eigenvectors are re-orthonormalised in
-// FP64 (modified Gram-Schmidt), S is transformed exactly in FP64 and FP64
-// sweeps (quadratic convergence from the FP32 level, normally one or two)
-// finish it.  W and U are FP64 scratch; U also holds the FP32 copies.
-__device__ void mixed_jacobi(double (*S)[LD], double (*V)[LD], double (*W)[LD], double (*U)[LD], int q,
-                             float* scf, float* ssf, double* sc, double* ss, double* coef, int* sa, int* sb,
-                             double* red) {
+// FP64 by two Newton-Schulz steps V <- V (3 I - V^T V) / 2 (orthogonality
+// error 1e-7 -> 1e-14 -> rounding level), S is transformed exactly in FP64
+// and FP64 sweeps finish it (normally one).  W and U are FP64 scratch; U
+// also holds the FP32 copies.
+__device__ void mixed_jacobi(double (*S)[LD], double (*V)[LD], double (*W)[LD], double (*U)[LD], int q) {
     const int t = threadIdx.x;
     float (*G32)[LD] = reinterpret_cast<float (*)[LD]>(&U[0][0]);
     float (*V32)[LD] = G32 + PMAX;
-    for (int e = t; e < q * q; e += TPB) G32[e / q][e % q] = (float)S[e / q][e % q];
+    for (int e = t; e < q * q; e += TPB) G32[e / q][e % q] = f64_to_f32(S[e / q][e % q]);
     __syncthreads();
-    block_jacobi<float>(G32, V32, q, scf, ssf, sa, sb, red, 1e-12, 12);
-    for (int e = t; e < q * q; e += TPB) V[e / q][e % q] = (double)V32[e / q][e % q];
+    block_jacobi<float>(G32, V32, q, 1e-6f, 1e-9f, 12);
+    for (int e = t; e < q * q; e += TPB) V[e / q][e % q] = f32_to_f64(V32[e / q][e % q]);
     __syncthreads();
-    for (int k = 0; k < q; ++k) {
-        if (t < 32) {
-            double s2 = 0.0;
-            for (int r = t; r < q; r += 32) s2 += V[r][k] * V[r][k];
-            for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            if (t == 0) red[0] = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-        }
+    for (int it = 0; it < 2; ++it) {
+        smem_gemm(W, V, V, q, true);                 // W = V^T V
         __syncthreads();
-        const double inv = red[0];
+        for (int e = t; e < q * q; e += TPB) W[e / q][e % q] = ((e / q == e % q) ? 1.5 : 0.0) - 0.5 * W[e / q][e % q];
         __syncthreads();
-        for (int r = t; r < q; r += TPB) V[r][k] *= inv;
+        smem_gemm(U, V, W, q, false);                // U = V (3 I - V^T V) / 2
         __syncthreads();
-        for (int j = k + 1 + t; j < q; j += TPB) {
-            double d = 0.0;
-            for (int r = 0; r < q; ++r) d += V[r][k] * V[r][j];
-            coef[j] = d;
-        }
-        __syncthreads();
-        for (int e = t; e < q * q; e += TPB) {
-            int r = e / q, j = e % q;
-            if (j > k) V[r][j] -= coef[j] * V[r][k];
-        }
+        for (int e = t; e < q * q; e += TPB) V[e / q][e % q] = U[e / q][e % q];
         __syncthreads();
     }
-    // S <- V^T S V in FP64
-    for (int e = t; e < q * q; e += TPB) {
-        int a = e / q, b = e % q;
-        double v = 0.0;
-        for (int j = 0; j < q; ++j) v += S[a][j] * V[j][b];
-        W[a][b] = v;
-    }
+    // S <- V^T S V in FP64 (W = S V, U = V^T W)
+    smem_gemm(W, S, V, q, false);
     __syncthreads();
-    for (int e = t; e < q * q; e += TPB) {
-        int a = e / q, b = e % q;
-        double v = 0.0;
-        for (int j = 0; j < q; ++j) v += V[j][a] * W[j][b];
-        U[a][b] = v;
-    }
+    smem_gemm(U, V, W, q, true);
     __syncthreads();
     for (int e = t; e < q * q; e += TPB) {
         int a = e / q, b = e % q;
         S[a][b] = 0.5 * (U[a][b] + U[b][a]);
     }
     __syncthreads();
-    block_jacobi<double>(S, W, q, sc, ss, sa, sb, red, 1e-30, 30);
-    // V <- V W
-    for (int e = t; e < q * q; e += TPB) {
-        int a = e / q, b = e % q;
-        double v = 0.0;
-        for (int j = 0; j < q; ++j) v += V[a][j] * W[j][b];
-        U[a][b] = v;
-    }
+    block_jacobi<double>(S, W, q, 1e-10, 1e-15, 8);
+    smem_gemm(U, V, W, q, false);                    // V <- V W
     __syncthreads();
     for (int e = t; e < q * q; e += TPB) V[e / q][e % q] = U[e / q][e % q];
     __syncthreads();
@@ -357,15 +424,16 @@ __device__ void mixed_jacobi(double (*S)[LD], double (*V)[LD], double (*W)[LD], 
 
 // Rayleigh-Ritz on (H, M): column scaling D = diag(M)^{-1/2}, Cholesky of
 // D M D (Jacobi-based pseudo-inverse square root if it is not numerically
-// positive definite), Jacobi on the reduced standard problem.
+// positive definite), eigen-decomposition of the reduced standard problem.
+// C = D L^{-T} V with theta ascending; columns of dropped (dependent)
+// directions get theta = +inf and zero columns of C.
 __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict__ H, const double* __restrict__ M,
                                                        double* __restrict__ C, double* __restrict__ theta,
                                                        const int* __restrict__ p_, int* __restrict__ rank,
                                                        const int* __restrict__ done) {
     __shared__ double S[PMAX][LD], V[PMAX][LD], L[PMAX][LD], T[PMAX][LD], U[PMAX][LD];
-    __shared__ double dsc[PMAX], sc[PMAX / 2], ss[PMAX / 2], red[TPB], th[PMAX], coef[PMAX];
-    __shared__ float scf[PMAX / 2], ssf[PMAX / 2];
-    __shared__ int sa[PMAX / 2], sb[PMAX / 2], perm[PMAX];
+    __shared__ double dsc[PMAX], th[PMAX], linv[PMAX];
+    __shared__ int perm[PMAX];
     __shared__ int s_fail;
     const int i = blockIdx.x;
     if (done[i]) return;
@@ -376,9 +444,8 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
     const double* Mi = M + (long long)i * PMAX * PMAX;
     if (t < PMAX) {
         double mkk = t < p ? Mi[t * PMAX + t] : 0.0;
-        dsc[t] = mkk > 0.0 ? 1.0 / sqrt(mkk) : 0.0;
+        dsc[t] = mkk > 0.0 ? rsqrt_nr(mkk) : 0.0;
     }
-    if (t == 0) s_fail = 0;
     __syncthreads();
     // scaled M into L, scaled H into T (q x q, dummy rows zero)
     for (int e = t; e < q * q; e += TPB) {
@@ -388,62 +455,70 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
         T[a][b] = ok ? dsc[a] * Hi[a * PMAX + b] * dsc[b] : 0.0;
     }
     __syncthreads();
-    // Cholesky of L in place (lower), columns with dsc == 0 are dropped
-    for (int k = 0; k < p; ++k) {
-        if (t == 0) {
-            double d = L[k][k];
-            if (dsc[k] == 0.0) L[k][k] = 0.0;
-            else if (!(d > 1e-13)) { s_fail = 1; L[k][k] = 0.0; }
-            else L[k][k] = sqrt(d);
+    // warp 0: Cholesky of L in place (lane a owns row a), then U = L^{-1}
+    // (lane c owns column c).  A column with dsc == 0 is dropped (linv = 0);
+    // any other pivot <= 1e-13 sends the problem to the pseudo-inverse path.
+    if (t < 32) {
+        const int lane = t;
+        int fail = 0;
+        for (int k = 0; k < p; ++k) {
+            const double d = L[k][k];
+            double lkk = 0.0, r = 0.0;
+            if (dsc[k] != 0.0) {
+                if (d > 1e-13) { r = rsqrt_nr(d); lkk = d * r; }
+                else fail = 1;
+            }
+            __syncwarp();
+            if (lane == k) { L[k][k] = lkk; linv[k] = r; }
+            if (lane > k && lane < p) L[lane][k] *= r;
+            __syncwarp();
+            if (lane > k && lane < p)
+                for (int b = k + 1; b <= lane; ++b) L[lane][b] -= L[lane][k] * L[b][k];
+            __syncwarp();
         }
-        __syncthreads();
-        double lkk = L[k][k];
-        if (t > k && t < p) L[t][k] = lkk > 0.0 ? L[t][k] / lkk : 0.0;
-        __syncthreads();
-        for (int e = t; e < p * p; e += TPB) {
-            int a = e / p, b = e % p;
-            if (b > k && a >= b) L[a][b] -= L[a][k] * L[b][k];
+        if (lane < q) {
+            const int c = lane;
+            for (int r = 0; r < q; ++r) {
+                double v = 0.0;
+                if (c < p && r >= c && r < p) {
+                    double a0 = (r == c) ? 1.0 : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                    int j = c;
+                    for (; j + 3 < r; j += 4) {
+                        a0 -= L[r][j] * U[j][c];
+                        a1 -= L[r][j + 1] * U[j + 1][c];
+                        a2 -= L[r][j + 2] * U[j + 2][c];
+                        a3 -= L[r][j + 3] * U[j + 3][c];
+                    }
+                    for (; j < r; ++j) a0 -= L[r][j] * U[j][c];
+                    v = ((a0 + a1) + (a2 + a3)) * linv[r];
+                }
+                U[r][c] = v;
+            }
         }
-        __syncthreads();
+        if (lane == 0) s_fail = fail;
     }
+    __syncthreads();
     int r = 0;
     if (!s_fail) {
-        // G = L^{-1} T L^{-T}: first S = L^{-1} T (column-parallel forward substitution)
-        for (int k = 0; k < p; ++k) {
-            if (t < p) {
-                double v = T[k][t];
-                for (int j = 0; j < k; ++j) v -= L[k][j] * S[j][t];
-                S[k][t] = L[k][k] > 0.0 ? v / L[k][k] : 0.0;
-            }
-            __syncthreads();
-        }
-        // V = L^{-1} S^T  -> G (symmetric); reuse V as temporary
-        for (int k = 0; k < p; ++k) {
-            if (t < p) {
-                double v = S[t][k];
-                for (int j = 0; j < k; ++j) v -= L[k][j] * V[j][t];
-                V[k][t] = L[k][k] > 0.0 ? v / L[k][k] : 0.0;
-            }
-            __syncthreads();
-        }
+        // G = U T U^T  (S = U T, then V = S U^T)
+        smem_gemm(S, U, T, q, false);
+        __syncthreads();
+        for (int e = t; e < q * q; e += TPB) T[e % q][e / q] = U[e / q][e % q];   // T = U^T
+        __syncthreads();
+        smem_gemm(V, S, T, q, false);
+        __syncthreads();
         for (int e = t; e < q * q; e += TPB) {
             int a = e / q, b = e % q;
             double v = (a < p && b < p) ? 0.5 * (V[a][b] + V[b][a]) : 0.0;
-            if (a < p && b < p && (L[a][a] == 0.0 || L[b][b] == 0.0)) v = (a == b) ? 1e300 : 0.0;
+            if (a < p && b < p && (linv[a] == 0.0 || linv[b] == 0.0)) v = (a == b) ? 1e300 : 0.0;
             S[a][b] = v;
         }
         __syncthreads();
-        mixed_jacobi(S, V, T, U, q, scf, ssf, sc, ss, coef, sa, sb, red);
-        // C = D L^{-T} V  (backward substitution, column-parallel), into T
-        for (int k = p - 1; k >= 0; --k) {
-            if (t < q) {
-                double v = V[k][t];
-                for (int j = k + 1; j < p; ++j) v -= L[j][k] * T[j][t];
-                T[k][t] = L[k][k] > 0.0 ? v / L[k][k] : 0.0;
-            }
-            __syncthreads();
-        }
-        for (int k = 0; k < p; ++k) r += L[k][k] > 0.0 ? 1 : 0;
+        mixed_jacobi(S, V, T, L, q);
+        // C' = U^T V into T (the D scaling is applied on output)
+        smem_gemm(T, U, V, q, true);
+        __syncthreads();
+        for (int k = 0; k < p; ++k) r += linv[k] > 0.0 ? 1 : 0;
     } else {
         // pseudo-inverse square root of D M D via its eigen-decomposition
         for (int e = t; e < q * q; e += TPB) {
@@ -451,32 +526,20 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
             S[a][b] = (a < p && b < p) ? dsc[a] * Mi[a * PMAX + b] * dsc[b] : 0.0;
         }
         __syncthreads();
-        block_jacobi<double>(S, V, q, sc, ss, sa, sb, red, 1e-30, 30);   // S diag = s, V = U
+        block_jacobi<double>(S, V, q, 1e-12, 1e-15, 30);   // S diag = s, V = U
         double smax = 0.0;
         for (int k = 0; k < p; ++k) smax = fmax(smax, S[k][k]);
         __syncthreads();
-        if (t < PMAX) th[t] = (t < p && S[t][t] > 1e-13 * smax) ? 1.0 / sqrt(S[t][t]) : 0.0;
-        // L <- U diag(th): reuse L as U_scaled
+        if (t < PMAX) th[t] = (t < p && S[t][t] > 1e-13 * smax) ? rsqrt_nr(S[t][t]) : 0.0;
         __syncthreads();
-        for (int e = t; e < q * q; e += TPB) {
+        for (int e = t; e < q * q; e += TPB) {              // L = U diag(th)
             int a = e / q, b = e % q;
             L[a][b] = (a < p && b < p) ? V[a][b] * th[b] : 0.0;
         }
         __syncthreads();
-        // G = L^T T L  (T holds scaled H);  S = T L first
-        for (int e = t; e < q * q; e += TPB) {
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < p; ++j) v += T[a][j] * L[j][b];
-            S[a][b] = v;
-        }
+        smem_gemm(S, T, L, q, false);                       // S = T L (T holds scaled H)
         __syncthreads();
-        for (int e = t; e < q * q; e += TPB) {
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < p; ++j) v += L[j][a] * S[j][b];
-            V[a][b] = v;
-        }
+        smem_gemm(V, L, S, q, true);                        // V = L^T S
         __syncthreads();
         for (int e = t; e < q * q; e += TPB) {
             int a = e / q, b = e % q;
@@ -485,14 +548,8 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
             S[a][b] = v;
         }
         __syncthreads();
-        block_jacobi<double>(S, V, q, sc, ss, sa, sb, red, 1e-30, 30);
-        // C = L V into T
-        for (int e = t; e < q * q; e += TPB) {
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < p; ++j) v += L[a][j] * V[j][b];
-            T[a][b] = v;
-        }
+        block_jacobi<double>(S, V, q, 1e-12, 1e-15, 30);
+        smem_gemm(T, L, V, q, false);                       // C' = L V
         __syncthreads();
         for (int k = 0; k < p; ++k) r += th[k] > 0.0 ? 1 : 0;
     }
@@ -516,283 +573,6 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
         C[(long long)i * PMAX * PMAX + e] = v;
     }
     if (t == 0) rank[i] = r;
-}
-
-// ---- Rayleigh-Ritz, one warp per problem (p <= 32), the same steps as
-// k_rayleigh_ritz with __syncwarp in place of block barriers: column scaling
-// D = diag(M)^{-1/2}, Cholesky D M D = L L^T, reduced matrix
-// G = L^{-1} (D H D) L^{-T}, FP32 Jacobi sweeps on G, FP64 modified
-// Gram-Schmidt of the eigenvectors V, exact FP64 V^T G V and FP64 sweeps to
-// convergence, C = D L^{-T} V; the pseudo-inverse path when D M D is not
-// numerically positive definite.
-namespace wrr {
-
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <typename T>
-__device__ void jacobi(T (*S)[LD], T (*V)[LD], int q, double rel_tol2, int max_sweeps, bool init_v) {
-    __shared__ T sc[PMAX / 2], ss[PMAX / 2];
-    __shared__ int sa[PMAX / 2], sb[PMAX / 2];
-    const int lane = threadIdx.x & 31;
-    if (init_v)
-        for (int e = lane; e < q * q; e += 32) V[e / q][e % q] = (e / q == e % q) ? T(1) : T(0);
-    __syncwarp();
-    double fro = 0.0;
-    for (int e = lane; e < q * q; e += 32) fro += (double)S[e / q][e % q] * (double)S[e / q][e % q];
-    fro = warp_sum(fro);
-    const int h = q / 2;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double off = 0.0;
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            if (a != b) off += (double)S[a][b] * (double)S[a][b];
-        }
-        off = warp_sum(off);
-        if (off <= rel_tol2 * fro || fro == 0.0) break;
-        for (int step = 0; step < q - 1; ++step) {
-            // round-robin pairing: position 0 fixed, the others rotate
-            if (lane < h) {
-                int a = lane == 0 ? 0 : 1 + (lane - 1 + step) % (q - 1);
-                int b = 1 + (q - 1 - lane - 1 + step) % (q - 1);
-                if (a > b) { int tmp = a; a = b; b = tmp; }
-                T c, s;
-                rot_params<T>(S[a][a], S[b][b], S[a][b], c, s);
-                sa[lane] = a; sb[lane] = b; sc[lane] = c; ss[lane] = s;
-            }
-            __syncwarp();
-            for (int e = lane; e < h * q; e += 32) {    // rows a, b
-                int j = e / q, k = e % q;
-                T sj = ss[j];
-                if (sj == T(0)) continue;
-                int a = sa[j], b = sb[j];
-                T cj = sc[j];
-                T x = S[a][k], y = S[b][k];
-                S[a][k] = cj * x - sj * y;
-                S[b][k] = sj * x + cj * y;
-            }
-            __syncwarp();
-            for (int e = lane; e < h * q; e += 32) {    // columns a, b of S and V
-                int j = e / q, k = e % q;
-                T sj = ss[j];
-                if (sj == T(0)) continue;
-                int a = sa[j], b = sb[j];
-                T cj = sc[j];
-                T x = S[k][a], y = S[k][b];
-                S[k][a] = cj * x - sj * y;
-                S[k][b] = sj * x + cj * y;
-                T u = V[k][a], v = V[k][b];
-                V[k][a] = cj * u - sj * v;
-                V[k][b] = sj * u + cj * v;
-            }
-            __syncwarp();
-        }
-    }
-}
-
-}  // namespace wrr
-
-__global__ void __launch_bounds__(32) k_rr_warp(const double* __restrict__ H, const double* __restrict__ M,
-                                                double* __restrict__ C, double* __restrict__ theta,
-                                                const int* __restrict__ p_, int* __restrict__ rank,
-                                                const int* __restrict__ done) {
-    __shared__ double L[PMAX][LD], Tm[PMAX][LD], S[PMAX][LD], V[PMAX][LD], W[PMAX][LD];
-    __shared__ double dsc[PMAX], coef[PMAX];
-    __shared__ int perm[PMAX];
-    // the FP32 Jacobi works in W's storage (two float q x q arrays fit in one double array)
-    float (*G32)[LD] = reinterpret_cast<float (*)[LD]>(&W[0][0]);
-    float (*V32)[LD] = G32 + PMAX;
-    const int i = blockIdx.x;
-    if (done[i]) return;
-    const int p = p_[i];
-    const int q = p + (p & 1);
-    const int lane = threadIdx.x;
-    const double* Hi = H + (long long)i * PMAX * PMAX;
-    const double* Mi = M + (long long)i * PMAX * PMAX;
-    {
-        double m = lane < p ? Mi[lane * PMAX + lane] : 0.0;
-        dsc[lane] = m > 0.0 ? 1.0 / sqrt(m) : 0.0;
-    }
-    __syncwarp();
-    for (int e = lane; e < q * q; e += 32) {
-        int a = e / q, b = e % q;
-        bool ok = a < p && b < p;
-        L[a][b] = ok ? dsc[a] * Mi[a * PMAX + b] * dsc[b] : 0.0;
-        Tm[a][b] = ok ? dsc[a] * Hi[a * PMAX + b] * dsc[b] : 0.0;
-    }
-    __syncwarp();
-    // Cholesky of L in place (lower); lane a owns row a.  A column with
-    // dsc == 0 is dropped; any other pivot <= 1e-13 sends the problem to
-    // the pseudo-inverse path below.
-    bool fail = false;
-    for (int k = 0; k < p; ++k) {
-        const double d = L[k][k];
-        double lkk;
-        if (dsc[k] == 0.0) lkk = 0.0;
-        else if (!(d > 1e-13)) { fail = true; lkk = 0.0; }
-        else lkk = sqrt(d);
-        __syncwarp();
-        if (lane == k) L[k][k] = lkk;
-        if (lane > k && lane < p) L[lane][k] = lkk > 0.0 ? L[lane][k] / lkk : 0.0;
-        __syncwarp();
-        if (lane > k && lane < p)
-            for (int b = k + 1; b <= lane; ++b) L[lane][b] -= L[lane][k] * L[b][k];
-        __syncwarp();
-    }
-    int r = 0;
-    if (!fail) {
-        // S = L^{-1} Tm, then W = L^{-1} S^T = G (lane = column)
-        if (lane < p)
-            for (int k = 0; k < p; ++k) {
-                double v = Tm[k][lane];
-                for (int j = 0; j < k; ++j) v -= L[k][j] * S[j][lane];
-                S[k][lane] = L[k][k] > 0.0 ? v / L[k][k] : 0.0;
-            }
-        __syncwarp();
-        if (lane < p)
-            for (int k = 0; k < p; ++k) {
-                double v = S[lane][k];
-                for (int j = 0; j < k; ++j) v -= L[k][j] * V[j][lane];
-                V[k][lane] = L[k][k] > 0.0 ? v / L[k][k] : 0.0;
-            }
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            double v = (a < p && b < p) ? 0.5 * (V[a][b] + V[b][a]) : 0.0;
-            if (a < p && b < p && (L[a][a] == 0.0 || L[b][b] == 0.0)) v = (a == b) ? 1e300 : 0.0;
-            S[a][b] = v;
-        }
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) G32[e / q][e % q] = (float)S[e / q][e % q];
-        __syncwarp();
-        // FP32 sweeps, then FP64 modified Gram-Schmidt on the eigenvectors
-        wrr::jacobi<float>(G32, V32, q, 1e-12, 12, true);
-        for (int e = lane; e < q * q; e += 32) V[e / q][e % q] = (double)V32[e / q][e % q];
-        __syncwarp();
-        for (int k = 0; k < q; ++k) {
-            double s2 = 0.0;
-            for (int rr = lane; rr < q; rr += 32) s2 += V[rr][k] * V[rr][k];
-            s2 = wrr::warp_sum(s2);
-            const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-            if (lane < q) V[lane][k] *= inv;
-            __syncwarp();
-            if (lane > k && lane < q) {
-                double d = 0.0;
-                for (int rr = 0; rr < q; ++rr) d += V[rr][k] * V[rr][lane];
-                coef[lane] = d;
-            }
-            __syncwarp();
-            if (lane < q)
-                for (int j = k + 1; j < q; ++j) V[lane][j] -= coef[j] * V[lane][k];
-            __syncwarp();
-        }
-        // S <- V^T S V exactly in FP64 (W = S V, Tm = V^T W), then FP64 sweeps
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < q; ++j) v += S[a][j] * V[j][b];
-            W[a][b] = v;
-        }
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < q; ++j) v += V[j][a] * W[j][b];
-            Tm[a][b] = v;
-        }
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            S[a][b] = 0.5 * (Tm[a][b] + Tm[b][a]);
-        }
-        __syncwarp();
-        wrr::jacobi<double>(S, W, q, 1e-30, 30, true);
-        // Tm = V W (eigenvectors of G); W = L^{-T} Tm (lane = column)
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < q; ++j) v += V[a][j] * W[j][b];
-            Tm[a][b] = v;
-        }
-        __syncwarp();
-        if (lane < q)
-            for (int k = p - 1; k >= 0; --k) {
-                double v = Tm[k][lane];
-                for (int j = k + 1; j < p; ++j) v -= L[j][k] * W[j][lane];
-                W[k][lane] = L[k][k] > 0.0 ? v / L[k][k] : 0.0;
-            }
-        __syncwarp();
-        for (int k = 0; k < p; ++k) r += L[k][k] > 0.0 ? 1 : 0;
-    } else {
-        // pseudo-inverse square root of D M D from its eigen-decomposition
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            S[a][b] = (a < p && b < p) ? dsc[a] * Mi[a * PMAX + b] * dsc[b] : 0.0;
-        }
-        __syncwarp();
-        wrr::jacobi<double>(S, V, q, 1e-30, 30, true);
-        double smax = 0.0;
-        for (int k = 0; k < p; ++k) smax = fmax(smax, S[k][k]);
-        coef[lane] = (lane < p && S[lane][lane] > 1e-13 * smax) ? 1.0 / sqrt(S[lane][lane]) : 0.0;
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) {          // L = U diag(th)
-            int a = e / q, b = e % q;
-            L[a][b] = (a < p && b < p) ? V[a][b] * coef[b] : 0.0;
-        }
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) {          // S = Tm L
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < p; ++j) v += Tm[a][j] * L[j][b];
-            S[a][b] = v;
-        }
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) {          // V = L^T S
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < p; ++j) v += L[j][a] * S[j][b];
-            V[a][b] = v;
-        }
-        __syncwarp();
-        for (int e = lane; e < q * q; e += 32) {
-            int a = e / q, b = e % q;
-            double v = (a < p && b < p) ? 0.5 * (V[a][b] + V[b][a]) : 0.0;
-            if (a < p && b < p && (coef[a] == 0.0 || coef[b] == 0.0)) v = (a == b) ? 1e300 : 0.0;
-            S[a][b] = v;
-        }
-        __syncwarp();
-        wrr::jacobi<double>(S, V, q, 1e-30, 30, true);
-        for (int e = lane; e < q * q; e += 32) {          // W = L V
-            int a = e / q, b = e % q;
-            double v = 0.0;
-            for (int j = 0; j < p; ++j) v += L[a][j] * V[j][b];
-            W[a][b] = v;
-        }
-        __syncwarp();
-        for (int k = 0; k < p; ++k) r += coef[k] > 0.0 ? 1 : 0;
-    }
-    // ascending order; rows of C scaled by D
-    if (lane < p) {
-        double v = S[lane][lane];
-        int rk = 0;
-        for (int j = 0; j < p; ++j) {
-            double w = S[j][j];
-            if (w < v || (w == v && j < lane)) ++rk;
-        }
-        perm[rk] = lane;
-    }
-    __syncwarp();
-    theta[i * PMAX + lane] = lane < p ? S[perm[lane]][perm[lane]] : 1e300;
-    for (int e = lane; e < PMAX * PMAX; e += 32) {
-        int a = e / PMAX, k = e % PMAX;
-        double v = 0.0;
-        if (a < p && k < p) v = dsc[a] * W[a][perm[k]];
-        if (k < p && S[perm[k]][perm[k]] >= 1e299) v = 0.0;
-        C[(long long)i * PMAX * PMAX + e] = v;
-    }
-    if (lane == 0) rank[i] = r;
 }
 
 // X = Y C, AX = AY C, BX = BY C on a block of 32 rows; residual partial sums.
@@ -1003,14 +783,14 @@ __global__ void __launch_bounds__(TPB) k_gram32(const double* __restrict__ W, do
 // diagonal is dependent on the previous ones: it is reset to its scaled self
 // (R row e_k) so that the basis stays finite; the FP64 phase removes it.
 __global__ void k_cholqr(const double* __restrict__ G, double* __restrict__ C, const int* __restrict__ p_) {
-    __shared__ double R[PMAX][LD], Ri[PMAX][LD], d[PMAX];
+    __shared__ double R[PMAX][LD], Ri[PMAX][LD], d[PMAX], d_inv[PMAX];
     const int i = blockIdx.x;
     const int p = p_[i];
     const int t = threadIdx.x;
     const double* Gi = G + (long long)i * PMAX * PMAX;
     if (t < PMAX) {
         double g = t < p ? Gi[t * PMAX + t] : 0.0;
-        d[t] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+        d[t] = g > 0.0 ? rsqrt_nr(g) : 0.0;
     }
     __syncwarp();
     for (int e = t; e < PMAX * PMAX; e += 32) {
@@ -1023,10 +803,10 @@ __global__ void k_cholqr(const double* __restrict__ G, double* __restrict__ C, c
     for (int k = 0; k < p; ++k) {
         double piv = R[k][k];
         bool ok = piv > 1e-10;
-        double u = ok ? sqrt(piv) : 1.0;
+        const double ru = ok ? rsqrt_nr(piv) : 1.0;
         __syncwarp();
-        if (t == 0) R[k][k] = u;
-        for (int j = k + 1 + t; j < p; j += 32) R[k][j] = ok ? R[k][j] / u : 0.0;
+        if (t == 0) { R[k][k] = ok ? piv * ru : 1.0; d_inv[k] = ru; }
+        for (int j = k + 1 + t; j < p; j += 32) R[k][j] = ok ? R[k][j] * ru : 0.0;
         __syncwarp();
         for (int e = t; e < p * p; e += 32) {
             int a = e / p, b = e % p;
@@ -1039,7 +819,7 @@ __global__ void k_cholqr(const double* __restrict__ G, double* __restrict__ C, c
         for (int r = t; r >= 0; --r) {
             double v = (r == t) ? 1.0 : 0.0;
             for (int j = r + 1; j <= t; ++j) v -= R[r][j] * Ri[j][t];
-            Ri[r][t] = v / R[r][r];
+            Ri[r][t] = v * d_inv[r];
         }
     }
     __syncwarp();

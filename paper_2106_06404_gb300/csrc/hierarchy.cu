@@ -210,6 +210,7 @@ size_t Hierarchy::device_bytes() const {
     b += (Phi.n + A1.n + Abar_m.n + K_m.n + Zb.n + Tm.n + A0.n + frhs.n + v1.n + r0buf.n) * 8;
     b += (Minv.n + A0inv.n + y0buf.n + z1t.n) * 8;
     b += (x.n + r.n + p.n + q.n + z.n + stencil.n) * 8;
+    b += (fst.a.n + fst.b.n) * 8 + fst.b32.n * 4;
     return b;
 }
 
@@ -417,9 +418,9 @@ void Hierarchy::build_fine() {
     ep.nev_max = spec.nev_max;
     ep.maxit = opt.eig_maxit;
     ep.seed = opt.seed;
-    Geom gg = g;
+    build_local_stencil(g, d_fboxes.p, d_count.p, fge.K, fst, st);
     const ProbBox* bx = d_fboxes.p;
-    const int* cnt = d_count.p;
+    const LocalStencil* ls = &fst;
     GevpBatch* fg = &fge;
     cudaStream_t stream = st;
     double nav = 0;
@@ -427,10 +428,10 @@ void Hierarchy::build_fine() {
     nav /= Pf;
     run_eig(fge, ep,
             [=](const double* X, double* AX, double* BX, const int* skip) {
-                apply_neumann(gg, bx, cnt, fg->K, X, AX, BX, fg->ldx, block_p, skip, stream);
+                apply_local(*ls, bx, dim, fg->K, X, AX, BX, fg->ldx, block_p, skip, stream);
             },
             [=](int pmax) { tile_solve(fg->K, fg->W.p, fg->ldx, pmax, fg->done.p, stream); },
-            [=](const double* X, double* W) { apply_b32(gg, bx, cnt, fg->K, X, W, fg->ldx, block_p, stream); },
+            [=](const double* X, double* W) { apply_local_b32(*ls, bx, dim, fg->K, X, W, fg->ldx, block_p, stream); },
             opt.precision == 1 ? opt.fp32_start_iters : 0,
             st, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9));
     fm = fge.m.download(st);

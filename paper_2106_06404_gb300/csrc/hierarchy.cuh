@@ -93,6 +93,7 @@ struct Hierarchy {
     DevBuf<int> d_count;
     TileBatch fdir;                 // Dirichlet factors A_{L,i}
     GevpBatch fge;                  // GEVP of (Abar_i, B_i), K_i factors
+    LocalStencil fst;               // stored stencils of Abar_i and B_i (rows of fge)
     std::vector<int> fm;            // selected counts m_i
     DevBuf<int> d_fm;
     int ldphi = 1;

@@ -272,6 +272,123 @@ __global__ void k_apply_b32(Geom g, const ProbBox* __restrict__ boxes, const int
     }
 }
 
+// ---- stored local stencils
+__global__ void k_local_stencil(Geom g, const ProbBox* __restrict__ boxes, const int* __restrict__ count,
+                                const long long* __restrict__ roff_, const int* __restrict__ K_,
+                                double* __restrict__ A, double* __restrict__ B, float* __restrict__ B32) {
+    const int i = blockIdx.y;
+    const ProbBox pb = boxes[i];
+    const int n = box_size(pb.nlo, pb.nhi, g.dim);
+    const int rows = K_[i] * NB;
+    const int noff = g.dim == 3 ? 27 : 9;
+    const long long base = roff_[i] * noff;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)rows * noff;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(w / noff), oi = (int)(w % noff);
+        double a = 0.0, b = 0.0;
+        if (r < n) {
+            int x[3], y[3];
+            box_coords(r, pb.nlo, pb.nhi, g.dim, x);
+            const int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, g.dim == 3 ? oi / 9 - 1 : 0};
+            for (int d = 0; d < 3; ++d) y[d] = x[d] + o[d];
+            if (in_box(pb.nlo, pb.nhi, y, g.dim)) {
+                a = stencil_coef(g, pb.elo, pb.ehi, x, o);
+                b = chi_at(g, pb, count, x) * a * chi_at(g, pb, count, y);
+            }
+        }
+        A[base + w] = a;
+        B[base + w] = b;
+        B32[base + w] = (float)b;
+    }
+}
+
+// row offset of neighbour oi in the lexicographic Neumann-box layout
+__device__ __forceinline__ int nbr_offset(int oi, int w0, int w1, int dim) {
+    return (oi % 3 - 1) + w0 * ((oi / 3) % 3 - 1) + (dim == 3 ? w0 * w1 * (oi / 9 - 1) : 0);
+}
+
+// One thread per (row, chunk of 8 columns).  A zero coefficient marks a
+// neighbour outside the box (its row is not read).
+__global__ void __launch_bounds__(128) k_apply_local(const ProbBox* __restrict__ boxes, int dim,
+                                                     const long long* __restrict__ roff_, const double* __restrict__ A,
+                                                     const double* __restrict__ B, const double* __restrict__ X,
+                                                     double* __restrict__ AX, double* __restrict__ BX, int ldx,
+                                                     int ncols, const int* __restrict__ skip) {
+    const int i = blockIdx.y;
+    if (skip && skip[i]) return;
+    const ProbBox pb = boxes[i];
+    const int n = box_size(pb.nlo, pb.nhi, dim);
+    const int w0 = pb.nhi[0] - pb.nlo[0] + 1, w1 = dim >= 2 ? pb.nhi[1] - pb.nlo[1] + 1 : 1;
+    const int noff = dim == 3 ? 27 : 9;
+    const int nchunk = (ncols + 7) / 8;
+    const long long roff = roff_[i];
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n * nchunk;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(w / nchunk), c0 = (int)(w % nchunk) * 8;
+        const int c1 = min(ncols, c0 + 8);
+        double ax[8], bx[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) { ax[c] = 0.0; bx[c] = 0.0; }
+        const double* ar = A + (roff + r) * noff;
+        const double* br = B + (roff + r) * noff;
+        for (int oi = 0; oi < noff; ++oi) {
+            const double a = ar[oi], b = br[oi];
+            if (a == 0.0 && b == 0.0) continue;
+            const double* xr = X + (roff + r + nbr_offset(oi, w0, w1, dim)) * ldx;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c0 + c < c1) {
+                    const double v = xr[c0 + c];
+                    ax[c] += a * v;
+                    bx[c] += b * v;
+                }
+        }
+        double* aw = AX + (roff + r) * ldx;
+        double* bw = BX + (roff + r) * ldx;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c0 + c < c1) { aw[c0 + c] = ax[c]; bw[c0 + c] = bx[c]; }
+    }
+}
+
+// FP32 arithmetic, conversions on the integer pipe; padding rows zeroed.
+__global__ void __launch_bounds__(128) k_apply_local_b32(const ProbBox* __restrict__ boxes, int dim,
+                                                         const long long* __restrict__ roff_, const int* __restrict__ K_,
+                                                         const float* __restrict__ B32, const double* __restrict__ X,
+                                                         double* __restrict__ W, int ldx, int ncols) {
+    const int i = blockIdx.y;
+    const ProbBox pb = boxes[i];
+    const int n = box_size(pb.nlo, pb.nhi, dim);
+    const int rows = K_[i] * NB;
+    const int w0 = pb.nhi[0] - pb.nlo[0] + 1, w1 = dim >= 2 ? pb.nhi[1] - pb.nlo[1] + 1 : 1;
+    const int noff = dim == 3 ? 27 : 9;
+    const int nchunk = (ncols + 7) / 8;
+    const long long roff = roff_[i];
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)rows * nchunk;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(w / nchunk), c0 = (int)(w % nchunk) * 8;
+        const int c1 = min(ncols, c0 + 8);
+        float acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+        if (r < n) {
+            const float* br = B32 + (roff + r) * noff;
+            for (int oi = 0; oi < noff; ++oi) {
+                const float b = br[oi];
+                if (b == 0.f) continue;
+                const double* xr = X + (roff + r + nbr_offset(oi, w0, w1, dim)) * ldx;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c0 + c < c1) acc[c] += b * f64_to_f32(xr[c0 + c]);
+            }
+        }
+        double* wr = W + (roff + r) * ldx;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c0 + c < c1) wr[c0 + c] = f32_to_f64(acc[c]);
+    }
+}
+
 // Stencil coefficients of the global operator: S[o * nun + u] = A(u, u + o)
 // for the 3^d offsets o (zero where the neighbour is not an unknown).
 __global__ void k_global_stencil(Geom g, double* __restrict__ S, long long nun) {
@@ -422,6 +539,35 @@ void apply_b32(const Geom& g, const ProbBox* d_boxes, const int* d_count, const 
     if (layout.P == 0) return;
     dim3 grid(64, layout.P);
     k_apply_b32<<<grid, 128, 0, s>>>(g, d_boxes, d_count, layout.d_roff.p, layout.d_K.p, X, W, ldx, ncols);
+    MSDD_LAUNCH_CHECK();
+}
+
+void build_local_stencil(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout,
+                         LocalStencil& ls, cudaStream_t s) {
+    ls.noff = g.dim == 3 ? 27 : 9;
+    const size_t len = (size_t)layout.total_rows * ls.noff;
+    ls.a.alloc(len);
+    ls.b.alloc(len);
+    ls.b32.alloc(len);
+    if (layout.P == 0) return;
+    dim3 grid(64, layout.P);
+    k_local_stencil<<<grid, 256, 0, s>>>(g, d_boxes, d_count, layout.d_roff.p, layout.d_K.p, ls.a.p, ls.b.p, ls.b32.p);
+    MSDD_LAUNCH_CHECK();
+}
+
+void apply_local(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout, const double* X,
+                 double* AX, double* BX, int ldx, int ncols, const int* skip, cudaStream_t s) {
+    if (layout.P == 0) return;
+    dim3 grid(64, layout.P);
+    k_apply_local<<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, ls.a.p, ls.b.p, X, AX, BX, ldx, ncols, skip);
+    MSDD_LAUNCH_CHECK();
+}
+
+void apply_local_b32(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout,
+                     const double* X, double* W, int ldx, int ncols, cudaStream_t s) {
+    if (layout.P == 0) return;
+    dim3 grid(64, layout.P);
+    k_apply_local_b32<<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, layout.d_K.p, ls.b32.p, X, W, ldx, ncols);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -93,6 +93,27 @@ void apply_neumann(const Geom& g, const ProbBox* d_boxes, const int* d_count, co
 void apply_b32(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout, const double* X,
                double* W, int ldx, int ncols, cudaStream_t s);
 
+// The local Neumann operators of the fine problems as stored 3^d-point
+// stencils over the rows of the Neumann box (the layout of the GEVP
+// vectors):  a[row][o] = abar(phi_{x+o}, phi_x) and
+// b[row][o] = chi(x) a[row][o] chi(x+o)  (so that B = X Abar X), zero where
+// x + o leaves the Neumann box and on padding rows; b32 is b rounded to FP32.
+// Built once per set-up; the eigensolver's operator applications then read
+// coefficients instead of recomputing element integrals and chi.
+struct LocalStencil {
+    int noff = 0;
+    DevBuf<double> a, b;
+    DevBuf<float> b32;
+};
+void build_local_stencil(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout,
+                         LocalStencil& ls, cudaStream_t s);
+// AX = Abar X, BX = X Abar X from the stored stencils (same contract as apply_neumann).
+void apply_local(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout, const double* X,
+                 double* AX, double* BX, int ldx, int ncols, const int* skip, cudaStream_t s);
+// W = X Abar X X in FP32 arithmetic from b32 (same contract as apply_b32).
+void apply_local_b32(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout,
+                     const double* X, double* W, int ldx, int ncols, cudaStream_t s);
+
 // Stored 3^d-point stencil of the global operator: S[o * n + u] = A(u, u + o),
 // offsets o lexicographic (x fastest) in {-1, 0, 1}^d, zero where u + o is
 // not an unknown.  n * 3^d doubles.

@@ -262,6 +262,15 @@ __global__ void __launch_bounds__(TPB) k_tile_solve(
 }
 
 
+// cp.async (16-byte global -> shared copies, completion by groups)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 // ------------------------------------------------------------------ solve, one right-hand side
 // The PCG local solves.  One CTA of 128 threads per matrix; the whole local
 // vector lives in shared memory.  Forward sweep: thread (row r = t/4, chunk
@@ -273,21 +282,10 @@ __global__ void __launch_bounds__(TPB) k_tile_solve(
 // loaded into registers while step R computes.
 constexpr int S1T = 128;
 
+constexpr int S1_STAGES = 4;
+
 template <typename T, int KBP>
-__device__ __forceinline__ void load_row_chunks(T (&v)[KBP + 1][8], const T* __restrict__ tiles, long long toff, int kb,
-                                                int R, int K, int r, int c0, bool fwd) {
-#pragma unroll
-    for (int d = 0; d <= KBP; ++d) {
-        int other = fwd ? R - d : R + d;   // fwd: tile (R, R-d); bwd: tile (R+d, R)
-        bool ok = d <= kb && other >= 0 && other < K && R >= 0 && R < K;
-        const T* src = ok ? tiles + (fwd ? tile_index(toff, kb, R, other) : tile_index(toff, kb, other, R)) : nullptr;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            // fwd: row r, columns c0..c0+7; bwd: rows c0..c0+7 (c0 = 8 * warp), column r (= lane)
-            v[d][q] = ok ? (fwd ? src[r * NB + c0 + q] : src[(c0 + q) * NB + r]) : T(0);
-        }
-    }
-}
+constexpr size_t solve1_ring_bytes() { return sizeof(T) * (size_t)S1_STAGES * (KBP + 1) * NB2; }
 
 template <typename T, int KBP>
 __global__ void __launch_bounds__(S1T) k_tile_solve1(
@@ -295,8 +293,12 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
     const long long* __restrict__ toff_, const long long* __restrict__ roff_, double* __restrict__ X,
     const int* __restrict__ gdone)
 {
+    // The tiles of step R + S1_STAGES - 1 are copied into a shared ring with
+    // cp.async while step R computes; zs holds the whole local vector.
+    constexpr int NST = S1_STAGES;
     extern __shared__ __align__(16) unsigned char zs_raw[];
-    T* zs = reinterpret_cast<T*>(zs_raw);
+    T* ring = reinterpret_cast<T*>(zs_raw);                       // [NST][KBP + 1][32 * 32]
+    T* zs = ring + (size_t)NST * (KBP + 1) * NB2;                 // [K * 32]
     __shared__ T accs[NB];
     __shared__ T part[S1T / 32][NB + 1];
     if (gdone && *gdone) return;
@@ -304,57 +306,75 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
     const int kb = kb_[i], K = K_[i];
     const long long toff = toff_[i], roff = roff_[i];
     const int t = threadIdx.x;
-    for (int e = t; e < K * NB; e += S1T) zs[e] = T(X[roff + e]);
-    __syncthreads();
+    auto stage = [&](int st, int d) { return ring + ((size_t)st * (KBP + 1) + d) * NB2; };
+    auto issue = [&](int st, int R, bool fwd) {
+        if (R >= 0 && R < K) {
+            for (int d = 0; d <= KBP; ++d) {
+                const int other = fwd ? R - d : R + d;
+                if (d > kb || other < 0 || other >= K) continue;
+                const T* src = tiles + (fwd ? tile_index(toff, kb, R, other) : tile_index(toff, kb, other, R));
+                T* dst = stage(st, d);
+                constexpr int PER = 16 / (int)sizeof(T);
+                for (int ch = t; ch < NB2 / PER; ch += S1T) cp_async16(dst + ch * PER, src + ch * PER);
+            }
+        }
+        cp_async_commit();
+    };
+    for (int k = 0; k < NST - 1; ++k) issue(k, k, true);
+    for (int e = t; e < K * NB; e += S1T) zs[e] = from_f64<T>(X[roff + e]);
 
-    // forward: z_R = T_R (x_R - sum_{J<R} L_RJ z_J)
+    // forward: z_R = T_R (x_R - sum_{J<R} L_RJ z_J); thread (row r = t/4,
+    // columns c0..c0+7) with the 4 partial sums of a row combined by shuffles
     {
         const int r = t >> 2, c0 = (t & 3) * 8;
-        T cur[KBP + 1][8], nxt[KBP + 1][8];
-        load_row_chunks<T, KBP>(cur, tiles, toff, kb, 0, K, r, c0, true);
         for (int R = 0; R < K; ++R) {
-            load_row_chunks<T, KBP>(nxt, tiles, toff, kb, R + 1, K, r, c0, true);
+            const int st = R % NST;
+            cp_async_wait_n<NST - 2>();
+            __syncthreads();
+            issue((R + NST - 1) % NST, R + NST - 1, true);
             T acc = T(0);
 #pragma unroll
             for (int d = 1; d <= KBP; ++d) {
                 if (d > kb || R - d < 0) continue;
+                const T* lt = stage(st, d) + r * NB + c0;
                 const T* zj = zs + (R - d) * NB + c0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) acc += cur[d][q] * zj[q];
+                for (int q = 0; q < 8; ++q) acc += lt[q] * zj[q];
             }
             acc += __shfl_xor_sync(0xffffffffu, acc, 1);
             acc += __shfl_xor_sync(0xffffffffu, acc, 2);
             if ((t & 3) == 0) accs[r] = zs[R * NB + r] - acc;
             __syncthreads();
+            const T* tt = stage(st, 0) + r * NB + c0;
             T s = T(0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s += cur[0][q] * accs[c0 + q];
+            for (int q = 0; q < 8; ++q) s += tt[q] * accs[c0 + q];
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
             if ((t & 3) == 0) zs[R * NB + r] = s;
-            __syncthreads();
-#pragma unroll
-            for (int d = 0; d <= KBP; ++d)
-#pragma unroll
-                for (int q = 0; q < 8; ++q) cur[d][q] = nxt[d][q];
         }
     }
-    for (int e = t; e < K * NB; e += S1T) zs[e] *= dinv[roff + e];
+    cp_async_wait_n<0>();
     __syncthreads();
-    // backward: x_R = T_R^T (D_R^{-1} z_R - sum_{I>R} L_IR^T x_I)
+    for (int k = 0; k < NST - 1; ++k) issue(k, K - 1 - k, false);
+    for (int e = t; e < K * NB; e += S1T) zs[e] *= dinv[roff + e];
+    // backward: x_R = T_R^T (D_R^{-1} z_R - sum_{I>R} L_IR^T x_I); thread
+    // (column = lane, rows k0..k0+7 of the tile), warps combined in shared memory
     {
         const int lane = t & 31, warp = t >> 5, k0 = warp * 8;
-        T cur[KBP + 1][8], nxt[KBP + 1][8];
-        load_row_chunks<T, KBP>(cur, tiles, toff, kb, K - 1, K, lane, k0, false);
-        for (int R = K - 1; R >= 0; --R) {
-            load_row_chunks<T, KBP>(nxt, tiles, toff, kb, R - 1, K, lane, k0, false);
+        for (int R = K - 1, it = 0; R >= 0; --R, ++it) {
+            const int st = it % NST;
+            cp_async_wait_n<NST - 2>();
+            __syncthreads();
+            issue((it + NST - 1) % NST, R - (NST - 1), false);
             T s = T(0);
 #pragma unroll
             for (int d = 1; d <= KBP; ++d) {
                 if (d > kb || R + d >= K) continue;
+                const T* lt = stage(st, d) + k0 * NB + lane;
                 const T* xi = zs + (R + d) * NB + k0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) s += cur[d][q] * xi[q];
+                for (int q = 0; q < 8; ++q) s += lt[q * NB] * xi[q];
             }
             part[warp][lane] = s;
             __syncthreads();
@@ -365,9 +385,10 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
                 accs[lane] = zs[R * NB + lane] - v;
             }
             __syncthreads();
+            const T* tt = stage(st, 0) + k0 * NB + lane;
             T s2 = T(0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s2 += cur[0][q] * accs[k0 + q];
+            for (int q = 0; q < 8; ++q) s2 += tt[q * NB] * accs[k0 + q];
             part[warp][lane] = s2;
             __syncthreads();
             if (warp == 0) {
@@ -376,14 +397,11 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1(
                 for (int w = 0; w < S1T / 32; ++w) v += part[w][lane];
                 zs[R * NB + lane] = v;
             }
-            __syncthreads();
-#pragma unroll
-            for (int d = 0; d <= KBP; ++d)
-#pragma unroll
-                for (int q = 0; q < 8; ++q) cur[d][q] = nxt[d][q];
         }
     }
-    for (int e = t; e < K * NB; e += S1T) X[roff + e] = (double)zs[e];
+    cp_async_wait_n<0>();
+    __syncthreads();
+    for (int e = t; e < K * NB; e += S1T) X[roff + e] = to_f64(zs[e]);
 }
 
 // One right-hand side, any kb (dense coarse matrices): tiles are read as
@@ -470,119 +488,198 @@ __global__ void __launch_bounds__(S1T) k_tile_solve1_dense(
 
 
 // ------------------------------------------------------------------ solve, several right-hand sides, band
-// For kb <= KBR: the tiles of step R+1 are copied into shared memory with
-// cp.async while step R computes, and the last kb solution blocks stay in a
-// shared ring (no re-reading of earlier blocks from global memory).  Thread
-// (row r = t/8, columns t%8 + 8q) owns up to 4 entries of a 32 x ncols block.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-constexpr int RING_STAGES = 3;
+// For kb <= 2, one 64-thread CTA per problem.  Step R needs the diagonal
+// tile, the kb off-diagonal tiles of block row (forward) or block column
+// (backward) R, the 32 x ncols block R of X and D_R^{-1}; these are copied
+// into shared memory with cp.async BAND_STAGES - 1 steps ahead.  The last kb
+// solution blocks stay in a shared ring.  Thread t owns the register block
+// rows 4 (t >> 3) + i, i < 4, columns CPT (t & 7) + j, j < CPT.
+//
+// Tiles are stored in shared memory as 32 x 32 with the 4-element groups of
+// a row permuted: group g of row r sits at position g ^ ((r >> 2) & 7).  The
+// four rows 4 rg + i a warp reads together for one group (forward), and the
+// four groups rg of one row (backward), then fall in distinct banks.
+constexpr int BAND_STAGES = 3;
+constexpr int BAND_SLOTS = 3;      // diagonal tile + at most 2 off-diagonal tiles per step
 
-template <typename T>
-struct RingLayout {
-    static constexpr int LDT = sizeof(T) == 4 ? NB + 4 : NB + 2;   // 16-byte aligned padded rows
-    static constexpr int LDZ = NB + 1;
-};
+__device__ __forceinline__ int band_swz(int row) { return (row >> 2) & 7; }
 
-template <typename T>
-__device__ __forceinline__ void async_tile(T* dst, const T* __restrict__ src) {
-    constexpr int PER = 16 / (int)sizeof(T);
-    constexpr int LDT = RingLayout<T>::LDT;
-    for (int ch = threadIdx.x; ch < NB2 / PER; ch += TPB) {
-        int e = ch * PER;
-        cp_async16(dst + (e / NB) * LDT + (e % NB), src + e);
+// copy one 32 x 32 tile (row-major in global memory) into the permuted layout
+template <typename T, int NT>
+__device__ __forceinline__ void band_async_tile(T* dst, const T* __restrict__ src) {
+    constexpr int PER = 16 / (int)sizeof(T);           // elements per 16-byte chunk
+    for (int ch = threadIdx.x; ch < NB2 / PER; ch += NT) {
+        const int e = ch * PER, r = e / NB, c = e % NB;
+        const int g = c >> 2, within = c & 3;
+        cp_async16(dst + r * NB + ((g ^ band_swz(r)) << 2) + within, src + e);
     }
 }
 
-template <typename T, int KBR>
-__global__ void __launch_bounds__(TPB) k_tile_solve_ring(
+// four consecutive elements of a permuted tile: row r, group g
+template <typename T>
+__device__ __forceinline__ void band_load4(const T* tile, int r, int g, T (&v)[4]);
+template <>
+__device__ __forceinline__ void band_load4<float>(const float* tile, int r, int g, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(tile + r * NB + ((g ^ band_swz(r)) << 2));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+template <>
+__device__ __forceinline__ void band_load4<double>(const double* tile, int r, int g, double (&v)[4]) {
+    const double2* p = reinterpret_cast<const double2*>(tile + r * NB + ((g ^ band_swz(r)) << 2));
+    const double2 a = p[0], b = p[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename T, int CPT, int CG>
+struct BandSmem {
+    static constexpr int ZLD = CG * CPT;                // columns held in the ring and Acc
+    static size_t bytes(int sxld) {
+        return sizeof(T) * ((size_t)BAND_STAGES * BAND_SLOTS * NB2 + (size_t)BAND_STAGES * NB + (size_t)(BAND_SLOTS + 1) * NB * ZLD) +
+               sizeof(double) * (size_t)BAND_STAGES * NB * sxld;
+    }
+};
+
+template <typename T, int CPT, int CG>
+__global__ void __launch_bounds__(8 * CG) k_tile_solve_band(
     const T* __restrict__ tiles, const T* __restrict__ dinv, const int* __restrict__ kb_, const int* __restrict__ K_,
     const long long* __restrict__ toff_, const long long* __restrict__ roff_, double* __restrict__ X, int ldx,
     int ncols, const int* __restrict__ skip, const int* __restrict__ gdone)
 {
-    // NST-stage cp.async pipeline: stage s holds the tiles of one step and the
-    // 32 x ldx block of X (right-hand side in the forward sweep, z in the
-    // backward sweep) it starts from; NST - 1 steps are in flight.
-    constexpr int LDT = RingLayout<T>::LDT, LDZ = RingLayout<T>::LDZ, S = KBR + 1, NST = RING_STAGES;
+    constexpr int NST = BAND_STAGES, ZLD = BandSmem<T, CPT, CG>::ZLD, NT = 8 * CG;
+    const int sxld = ((ncols + 1) / 2) * 2;             // staged columns of X (whole 16-byte chunks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* St = reinterpret_cast<T*>(smem_raw);                               // [NST][S][NB][LDT]
-    double* Sx = reinterpret_cast<double*>(St + (size_t)NST * S * NB * LDT);  // [NST][NB][ldx]
-    T* Zr = reinterpret_cast<T*>(Sx + (size_t)NST * NB * ldx);            // [S][NB][LDZ]
-    T* Acc = Zr + S * NB * LDZ;                                           // [NB][LDZ]
+    T* St = reinterpret_cast<T*>(smem_raw);                                   // [NST][SLOTS][32*32]
+    T* Sd = St + (size_t)NST * BAND_SLOTS * NB2;                              // [NST][32]   D^{-1}
+    T* Zr = Sd + (size_t)NST * NB;                                            // [SLOTS][32][ZLD]
+    T* Acc = Zr + (size_t)BAND_SLOTS * NB * ZLD;                              // [32][ZLD]
+    double* Sx = reinterpret_cast<double*>(Acc + (size_t)NB * ZLD);           // [NST][32][sxld]
     const int i = blockIdx.x;
     if (skip && skip[i]) return;
     if (gdone && *gdone) return;
     const int kb = kb_[i], K = K_[i];
     const long long toff = toff_[i], roff = roff_[i];
     const int t = threadIdx.x;
-    const int r = t >> 3, cb = t & 7;
-    const int qn = (ncols + 7) / 8;          // columns cb + 8q, q < qn, owned by this thread
-    auto stage_tile = [&](int st, int slot) { return St + ((size_t)(st * S + slot) * NB) * LDT; };
+    const int rg = t / CG, cg = t % CG, warp = t >> 5;
+    const int r0 = 4 * rg, c0 = CPT * cg;
+    // rows of this warp: 4 * (32 warp / CG) ... 4 * ((32 warp + 31) / CG) + 3
+    const int wrow_lo = 4 * ((32 * warp) / CG), wgrp_hi = (32 * warp + 31) / CG;
+    auto stile = [&](int st, int slot) { return St + (size_t)(st * BAND_SLOTS + slot) * NB2; };
     auto issue = [&](int st, int R, bool fwd) {
         if (R >= 0 && R < K) {
-            async_tile(stage_tile(st, 0), tiles + tile_index(toff, kb, R, R));
+            band_async_tile<T, NT>(stile(st, 0), tiles + tile_index(toff, kb, R, R));
             for (int d = 1; d <= kb; ++d) {
-                int o = fwd ? R - d : R + d;
+                const int o = fwd ? R - d : R + d;
                 if (o < 0 || o >= K) continue;
-                async_tile(stage_tile(st, d), tiles + (fwd ? tile_index(toff, kb, R, o) : tile_index(toff, kb, o, R)));
+                band_async_tile<T, NT>(stile(st, d), tiles + (fwd ? tile_index(toff, kb, R, o) : tile_index(toff, kb, o, R)));
             }
+            if (!fwd) {
+                constexpr int PER = 16 / (int)sizeof(T);
+                for (int ch = t; ch < NB / PER; ch += NT)
+                    cp_async16(Sd + st * NB + ch * PER, dinv + roff + (long long)R * NB + ch * PER);
+            }
+            const int cpr = sxld / 2;                    // 16-byte chunks per row
             const double* src = X + (roff + (long long)R * NB) * ldx;
-            double* dst = Sx + (size_t)st * NB * ldx;
-            for (int ch = t; ch < NB * ldx / 2; ch += TPB) cp_async16(dst + 2 * ch, src + 2 * ch);
+            double* dst = Sx + (size_t)st * NB * sxld;
+            for (int ch = t; ch < NB * cpr; ch += NT) {
+                const int r = ch / cpr, c = (ch % cpr) * 2;
+                cp_async16(dst + r * sxld + c, src + (long long)r * ldx + c);
+            }
         }
         cp_async_commit();
     };
+    auto finish = [&](T (&acc)[4][CPT], int R, const T* Tt, bool fwd) {
+        // Acc <- acc; out = T_R acc (forward) or T_R^T acc (backward)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) Acc[(r0 + a) * ZLD + c0 + j] = acc[a][j];
+        __syncthreads();
+        T out[4][CPT];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) out[a][j] = T(0);
+        if (fwd) {
+            // T_R is lower triangular with zeros above the diagonal: the
+            // groups up to the warp's last row suffice
+            const int gmax = wgrp_hi + 1;
+#pragma unroll 4
+            for (int g = 0; g < gmax; ++g) {
+                T l[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) band_load4<T>(Tt, r0 + a, g, l[a]);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const T* z = Acc + (4 * g + kk) * ZLD + c0;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        const T zv = z[j];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) out[a][j] += l[a][kk] * zv;
+                    }
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int k = wrow_lo; k < NB; ++k) {
+                T l[4];
+                band_load4<T>(Tt, k, rg, l);
+                const T* z = Acc + k * ZLD + c0;
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    const T zv = z[j];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) out[a][j] += l[a] * zv;
+                }
+            }
+        }
+        T* Zw = Zr + (size_t)(R % BAND_SLOTS) * NB * ZLD;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            double* xw = X + (roff + (long long)R * NB + r0 + a) * ldx;
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                Zw[(r0 + a) * ZLD + c0 + j] = out[a][j];
+                if (c0 + j < ncols) xw[c0 + j] = to_f64(out[a][j]);
+            }
+        }
+    };
+
     // forward: z_R = T_R (x_R - sum_J L_RJ z_J)
     for (int k = 0; k < NST - 1; ++k) issue(k, k, true);
     for (int R = 0; R < K; ++R) {
         const int st = R % NST;
-        issue((R + NST - 1) % NST, R + NST - 1, true);
-        cp_async_wait_n<NST - 1>();
+        cp_async_wait_n<NST - 2>();
         __syncthreads();
-        T acc[4];
-        const double* xr = Sx + (size_t)st * NB * ldx + r * ldx;
+        issue((R + NST - 1) % NST, R + NST - 1, true);
+        T acc[4][CPT];
+        const double* xs = Sx + (size_t)st * NB * sxld;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int c = cb + 8 * q;
-            acc[q] = (q < qn && c < ncols) ? T(xr[c]) : T(0);
-        }
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) acc[a][j] = (c0 + j < ncols) ? from_f64<T>(xs[(r0 + a) * sxld + c0 + j]) : T(0);
         for (int d = 1; d <= kb; ++d) {
             if (R - d < 0) break;
-            const T* L = stage_tile(st, d) + r * LDT;
-            const T* Z = Zr + ((R - d) % S) * NB * LDZ;
-#pragma unroll 8
-            for (int k = 0; k < NB; ++k) {
-                T l = L[k];
+            const T* L = stile(st, d);
+            const T* Z = Zr + (size_t)((R - d) % BAND_SLOTS) * NB * ZLD;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < qn) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
+            for (int g = 0; g < NB / 4; ++g) {
+                T l[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) band_load4<T>(L, r0 + a, g, l[a]);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const T* z = Z + (4 * g + kk) * ZLD + c0;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        const T zv = z[j];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) acc[a][j] -= l[a][kk] * zv;
+                    }
+                }
             }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Acc[r * LDZ + cb + 8 * q] = acc[q];
-        __syncthreads();
-        const T* Tt = stage_tile(st, 0) + r * LDT;
-        T out[4] = {0, 0, 0, 0};
-        for (int k = 0; k <= r; ++k) {
-            T l = Tt[k];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < qn) out[q] += l * Acc[k * LDZ + cb + 8 * q];
-        }
-        T* Zw = Zr + (R % S) * NB * LDZ;
-        double* xw = X + (roff + (long long)R * NB + r) * ldx;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int c = cb + 8 * q;
-            Zw[r * LDZ + c] = out[q];
-            if (q < qn && c < ncols) xw[c] = (double)out[q];
-        }
-        __syncthreads();
+        finish(acc, R, stile(st, 0), true);
     }
     cp_async_wait_n<0>();
     __syncthreads();
@@ -590,57 +687,56 @@ __global__ void __launch_bounds__(TPB) k_tile_solve_ring(
     for (int k = 0; k < NST - 1; ++k) issue(k, K - 1 - k, false);
     for (int R = K - 1, it = 0; R >= 0; --R, ++it) {
         const int st = it % NST;
-        issue((it + NST - 1) % NST, R - (NST - 1), false);
-        cp_async_wait_n<NST - 1>();
+        cp_async_wait_n<NST - 2>();
         __syncthreads();
-        T acc[4];
-        const double* xr = Sx + (size_t)st * NB * ldx + r * ldx;
-        const T dr = dinv[roff + (long long)R * NB + r];
+        issue((it + NST - 1) % NST, R - (NST - 1), false);
+        T acc[4][CPT];
+        const double* xs = Sx + (size_t)st * NB * sxld;
+        const T* dv = Sd + st * NB;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int c = cb + 8 * q;
-            acc[q] = (q < qn && c < ncols) ? dr * T(xr[c]) : T(0);
-        }
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                acc[a][j] = (c0 + j < ncols) ? dv[r0 + a] * from_f64<T>(xs[(r0 + a) * sxld + c0 + j]) : T(0);
         for (int d = 1; d <= kb; ++d) {
             if (R + d >= K) break;
-            const T* L = stage_tile(st, d);
-            const T* Z = Zr + ((R + d) % S) * NB * LDZ;
+            const T* L = stile(st, d);
+            const T* Z = Zr + (size_t)((R + d) % BAND_SLOTS) * NB * ZLD;
 #pragma unroll 8
             for (int k = 0; k < NB; ++k) {
-                T l = L[k * LDT + r];
+                T l[4];
+                band_load4<T>(L, k, rg, l);
+                const T* z = Z + k * ZLD + c0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < qn) acc[q] -= l * Z[k * LDZ + cb + 8 * q];
+                for (int j = 0; j < CPT; ++j) {
+                    const T zv = z[j];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) acc[a][j] -= l[a] * zv;
+                }
             }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Acc[r * LDZ + cb + 8 * q] = acc[q];
-        __syncthreads();
-        const T* Tt = stage_tile(st, 0);
-        T out[4] = {0, 0, 0, 0};
-        for (int k = r; k < NB; ++k) {
-            T l = Tt[k * LDT + r];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < qn) out[q] += l * Acc[k * LDZ + cb + 8 * q];
-        }
-        T* Zw = Zr + (R % S) * NB * LDZ;
-        double* xw = X + (roff + (long long)R * NB + r) * ldx;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int c = cb + 8 * q;
-            Zw[r * LDZ + c] = out[q];
-            if (q < qn && c < ncols) xw[c] = (double)out[q];
-        }
-        __syncthreads();
+        finish(acc, R, stile(st, 0), false);
     }
     cp_async_wait_n<0>();
 }
 
-template <typename T, int KBR>
-size_t ring_smem_bytes(int ldx) {
-    return sizeof(T) * ((size_t)RING_STAGES * (KBR + 1) * NB * RingLayout<T>::LDT + (size_t)(KBR + 2) * NB * RingLayout<T>::LDZ) +
-           sizeof(double) * (size_t)RING_STAGES * NB * ldx;
+template <typename T, int CPT, int CG>
+void launch_band(const TileBatch& tb, const T* tiles, const T* dinv, double* X, int ldx, int ncols, const int* skip,
+                 cudaStream_t s, const int* gdone) {
+    const size_t b = BandSmem<T, CPT, CG>::bytes(((ncols + 1) / 2) * 2);
+    MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_band<T, CPT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+    k_tile_solve_band<T, CPT, CG><<<tb.P, 8 * CG, b, s>>>(tiles, dinv, tb.d_kb.p, tb.d_K.p, tb.d_toff.p,
+                                                          tb.d_roff.p, X, ldx, ncols, skip, gdone);
+    MSDD_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_band_cols(const TileBatch& tb, const T* tiles, const T* dinv, double* X, int ldx, int ncols,
+                      const int* skip, cudaStream_t s, const int* gdone) {
+    // 16 column groups (128 threads) unless the block is narrow
+    if (ncols <= 8) launch_band<T, 1, 8>(tb, tiles, dinv, X, ldx, ncols, skip, s, gdone);
+    else if (ncols <= 16) launch_band<T, 1, 16>(tb, tiles, dinv, X, ldx, ncols, skip, s, gdone);
+    else launch_band<T, 2, 16>(tb, tiles, dinv, X, ldx, ncols, skip, s, gdone);
 }
 
 __global__ void k_fill_identity(double* __restrict__ E, const int* __restrict__ n_, const int* __restrict__ K_,
@@ -765,47 +861,43 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
     if (tb.P == 0) return;
     if (ncols > ldx) throw std::runtime_error("tile_solve: more columns than the leading dimension");
     const size_t zbytes = (size_t)tb.max_K * NB * sizeof(double);   // upper bound for both precisions
-    if (ncols == 1 && ldx == 1 && skip == nullptr && zbytes <= 160 * 1024) {
+    if (ncols == 1 && ldx == 1 && skip == nullptr) {
         int maxkb = 0;
         for (int v : tb.kb) maxkb = std::max(maxkb, v);
-        if (zbytes > 48 * 1024) {
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
+        const size_t zt = (size_t)tb.max_K * NB * (tb.prec ? sizeof(float) : sizeof(double));
+        const size_t ring_bytes = (tb.prec ? (maxkb <= 1 ? solve1_ring_bytes<float, 1>() : solve1_ring_bytes<float, 2>())
+                                           : (maxkb <= 1 ? solve1_ring_bytes<double, 1>() : solve1_ring_bytes<double, 2>())) + zt;
+        if (maxkb <= 2 && ring_bytes <= 200 * 1024) {
+            if (tb.prec) {
+                auto k = maxkb <= 1 ? k_tile_solve1<float, 1> : k_tile_solve1<float, 2>;
+                MSDD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_bytes));
+                k<<<tb.P, S1T, ring_bytes, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
+            } else {
+                auto k = maxkb <= 1 ? k_tile_solve1<double, 1> : k_tile_solve1<double, 2>;
+                MSDD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_bytes));
+                k<<<tb.P, S1T, ring_bytes, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
+            }
+            MSDD_LAUNCH_CHECK();
+            return;
         }
-        if (tb.prec) {
-            if (maxkb <= 1) k_tile_solve1<float, 1><<<tb.P, S1T, zbytes, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
-            else if (maxkb <= 2) k_tile_solve1<float, 2><<<tb.P, S1T, zbytes, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
-            else k_tile_solve1_dense<float><<<tb.P, S1T, zbytes, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
-        } else {
-            if (maxkb <= 1) k_tile_solve1<double, 1><<<tb.P, S1T, zbytes, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
-            else if (maxkb <= 2) k_tile_solve1<double, 2><<<tb.P, S1T, zbytes, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
+        if (maxkb > 2 && zbytes <= 160 * 1024) {
+            if (zbytes > 48 * 1024) {
+                MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
+                MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
+            }
+            if (tb.prec) k_tile_solve1_dense<float><<<tb.P, S1T, zbytes, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
             else k_tile_solve1_dense<double><<<tb.P, S1T, zbytes, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
+            MSDD_LAUNCH_CHECK();
+            return;
         }
-        MSDD_LAUNCH_CHECK();
-        return;
     }
     int maxkb = 0;
     for (int v : tb.kb) maxkb = std::max(maxkb, v);
-    // the ring kernel stages whole 32 x ldx blocks of X with 16-byte copies
-    const bool ring_ok = maxkb <= 2 && ncols <= NB && ldx <= NB && ldx % 2 == 0 &&
-                         ((uintptr_t)X % 16) == 0;
-    if (ring_ok) {
-        if (tb.prec) {
-            size_t b = ring_smem_bytes<float, 2>(ldx);
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_ring<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-            k_tile_solve_ring<float, 2><<<tb.P, TPB, b, s>>>(
-                tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
-        } else {
-            size_t b = ring_smem_bytes<double, 2>(ldx);
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_ring<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-            k_tile_solve_ring<double, 2><<<tb.P, TPB, b, s>>>(
-                tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
-        }
-        MSDD_LAUNCH_CHECK();
+    // the band kernel stages blocks of X with 16-byte copies
+    const bool band_ok = maxkb <= 2 && ncols <= NB && ldx % 2 == 0 && ((uintptr_t)X % 16) == 0;
+    if (band_ok) {
+        if (tb.prec) launch_band_cols<float>(tb, tb.tiles_f.p, tb.dinv_f.p, X, ldx, ncols, skip, s, gdone);
+        else launch_band_cols<double>(tb, tb.tiles_d.p, tb.dinv_d.p, X, ldx, ncols, skip, s, gdone);
         return;
     }
     const dim3 grid(tb.P, (ncols + NB - 1) / NB);
