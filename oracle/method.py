@@ -96,6 +96,26 @@ def select_count(lam, nev_max, eta):
     return int(min(nev_max, int(np.sum(lam < eta))))
 
 
+def fine_pencil(mesh, Ke, en, sub, chi):
+    """Dense Neumann matrix Abar_i (Eq. locala_cg: the element forms of
+    T_{h,L,i} on all non-Dirichlet nodes of the closed subdomain) and
+    B_i = X_i Abar_i X_i (b^1, Eq. cg_rhs_blf) of one fine subdomain, rows in
+    its lexicographic Neumann-node order; Ke / en are the element matrices
+    and element nodes of the whole mesh, chi the subdomain's partition of
+    unity on those nodes (Section 2.3)."""
+    nn = sub.neumann_nodes()
+    pos = -np.ones(mesh.num_nodes, dtype=np.int64)
+    pos[nn] = np.arange(len(nn))
+    Abar = np.zeros((len(nn), len(nn)))
+    for e in np.nonzero(sub.element_mask)[0]:
+        loc = pos[en[e]]
+        ok = loc >= 0
+        li = loc[ok]
+        Abar[np.ix_(li, li)] += Ke[e][np.ix_(ok, ok)]
+    B = chi[:, None] * Abar * chi[None, :]
+    return nn, Abar, B
+
+
 class Level:
     pass
 
@@ -135,18 +155,8 @@ class Hierarchy:
 
         def local(i):
             s = dec.fine[i]
-            nn = s.neumann_nodes()
-            pos = -np.ones(mesh.num_nodes, dtype=np.int64)
-            pos[nn] = np.arange(len(nn))
-            # Neumann matrix: elements of T_{h,L,i} on the non-Dirichlet nodes
-            Abar = np.zeros((len(nn), len(nn)))
-            for e in np.nonzero(s.element_mask)[0]:
-                loc = pos[en[e]]
-                ok = loc >= 0
-                li = loc[ok]
-                Abar[np.ix_(li, li)] += Ke[e][np.ix_(ok, ok)]
+            nn, Abar, B = fine_pencil(mesh, Ke, en, s, chis[i])
             chi = chis[i]
-            B = chi[:, None] * Abar * chi[None, :]
             lam, W = gevp(Abar, B, rank_reveal=False)
             m = select_count(lam, self.nev_max, self.eta)
             Wm = normalise_sign(W[:, :m])

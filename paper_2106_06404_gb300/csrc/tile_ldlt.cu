@@ -542,10 +542,15 @@ struct BandSmem {
 template <typename T, int CPT, int CG>
 __global__ void __launch_bounds__(8 * CG) k_tile_solve_band(
     const T* __restrict__ tiles, const T* __restrict__ dinv, const int* __restrict__ kb_, const int* __restrict__ K_,
-    const long long* __restrict__ toff_, const long long* __restrict__ roff_, double* __restrict__ X, int ldx,
-    int ncols, const int* __restrict__ skip, const int* __restrict__ gdone)
+    const long long* __restrict__ toff_, const long long* __restrict__ roff_, double* __restrict__ Xall, int ldx,
+    int ncols_all, const int* __restrict__ skip, const int* __restrict__ gdone)
 {
+    // blockIdx.y selects a chunk of ZLD columns (an independent set of
+    // right-hand sides solved by its own CTA)
     constexpr int NST = BAND_STAGES, ZLD = BandSmem<T, CPT, CG>::ZLD, NT = 8 * CG;
+    const int cbase = blockIdx.y * ZLD;
+    const int ncols = min(ZLD, ncols_all - cbase);
+    double* __restrict__ X = Xall + cbase;
     const int sxld = ((ncols + 1) / 2) * 2;             // staged columns of X (whole 16-byte chunks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* St = reinterpret_cast<T*>(smem_raw);                                   // [NST][SLOTS][32*32]
@@ -723,20 +728,21 @@ __global__ void __launch_bounds__(8 * CG) k_tile_solve_band(
 template <typename T, int CPT, int CG>
 void launch_band(const TileBatch& tb, const T* tiles, const T* dinv, double* X, int ldx, int ncols, const int* skip,
                  cudaStream_t s, const int* gdone) {
-    const size_t b = BandSmem<T, CPT, CG>::bytes(((ncols + 1) / 2) * 2);
+    constexpr int ZLD = BandSmem<T, CPT, CG>::ZLD;
+    const int chunks = (ncols + ZLD - 1) / ZLD;
+    const size_t b = BandSmem<T, CPT, CG>::bytes(((std::min(ncols, ZLD) + 1) / 2) * 2);
     MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_band<T, CPT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-    k_tile_solve_band<T, CPT, CG><<<tb.P, 8 * CG, b, s>>>(tiles, dinv, tb.d_kb.p, tb.d_K.p, tb.d_toff.p,
-                                                          tb.d_roff.p, X, ldx, ncols, skip, gdone);
+    k_tile_solve_band<T, CPT, CG><<<dim3(tb.P, chunks), 8 * CG, b, s>>>(tiles, dinv, tb.d_kb.p, tb.d_K.p, tb.d_toff.p,
+                                                                         tb.d_roff.p, X, ldx, ncols, skip, gdone);
     MSDD_LAUNCH_CHECK();
 }
 
 template <typename T>
 void launch_band_cols(const TileBatch& tb, const T* tiles, const T* dinv, double* X, int ldx, int ncols,
                       const int* skip, cudaStream_t s, const int* gdone) {
-    // 16 column groups (128 threads) unless the block is narrow
-    if (ncols <= 8) launch_band<T, 1, 8>(tb, tiles, dinv, X, ldx, ncols, skip, s, gdone);
-    else if (ncols <= 16) launch_band<T, 1, 16>(tb, tiles, dinv, X, ldx, ncols, skip, s, gdone);
-    else launch_band<T, 2, 16>(tb, tiles, dinv, X, ldx, ncols, skip, s, gdone);
+    // chunks of 8 columns, one 64-thread CTA each (more independent
+    // sequential sweeps in flight per SM than wider CTAs)
+    launch_band<T, 1, 8>(tb, tiles, dinv, X, ldx, ncols, skip, s, gdone);
 }
 
 __global__ void k_fill_identity(double* __restrict__ E, const int* __restrict__ n_, const int* __restrict__ K_,
