@@ -96,7 +96,7 @@ typedef struct msdd_options {
     void* stream;        /* cudaStream_t */
     int profile;         /* 1: time kernel families with CUDA events (see msdd_stats.prof) */
     int fp32_start_iters;/* precision 1: fine-level FP32 subspace iterations (FP32 B apply and
-                            solve, Euclidean CholQR) before the FP64 iterations (default 12) */
+                            solve, Euclidean CholQR) before the FP64 iterations (default 20) */
 } msdd_options;
 
 /* Per kernel family timing, filled when options.profile = 1.  bytes and flops

@@ -86,6 +86,7 @@ extern "C" msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nr
         k_stage_out<<<grid, 256, 0, st>>>(X, scratch, bb->tb.d_n.p, bb->tb.d_roff.p, bb->nmax, nrhs);
         MSDD_LAUNCH_CHECK();
         MSDD_CUDA(cudaStreamSynchronize(st));
+        msdd::tile_check_waits();
     } catch (const std::exception& ex) {
         return noalloc_fail(MSDD_ERR_CUDA, ex.what());
     }

@@ -84,7 +84,7 @@ msdd_status msdd_default_options(msdd_options* opt) {
     opt->seed = 12345;
     opt->stream = nullptr;
     opt->profile = 0;
-    opt->fp32_start_iters = 12;
+    opt->fp32_start_iters = 20;
     return MSDD_OK;
 }
 
@@ -356,6 +356,7 @@ msdd_status msdd_band_solve(const msdd_band_batch* bb, int nrhs, double* X, void
         msdd::tile_solve(bb->tb, stage.p, nrhs, nrhs, nullptr, st);
         msdd::segment_copy(d_do.p, d_so.p, d_len.p, P, maxlen, stage.p, X, 0, nullptr, st);
         MSDD_CUDA(cudaStreamSynchronize(st));
+        msdd::tile_check_waits();
         return MSDD_OK;
     });
 }

@@ -262,6 +262,7 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     sc.alloc(1);
     MSDD_CUDA(cudaMemsetAsync(sc.p, 0, sizeof(PcgScalars), st));
     MSDD_CUDA(cudaStreamSynchronize(st));
+    tile_check_waits();
     stats.setup_ms = ms_since(t_all);
     stats.device_bytes = device_bytes();
     export_prof();
@@ -1023,6 +1024,7 @@ int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, doubl
     prof.collect();
     MSDD_CUDA(cudaMemcpyAsync(xout, x.p, nun * sizeof(double), cudaMemcpyDeviceToDevice, st));
     MSDD_CUDA(cudaStreamSynchronize(st));
+    tile_check_waits();
     double rel = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
     if (relres) *relres = rel;
     stats.pcg_iterations = hs.iters;

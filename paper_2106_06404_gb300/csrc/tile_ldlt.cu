@@ -2,6 +2,9 @@
 // local matrix).  See tile_ldlt.cuh for the storage format.
 #include "tile_ldlt.cuh"
 
+#include <cuda.h>
+#include <mutex>
+
 namespace msdd {
 
 namespace {
@@ -725,6 +728,276 @@ __global__ void __launch_bounds__(8 * CG) k_tile_solve_band(
     cp_async_wait_n<0>();
 }
 
+// ---- the FP32 band solve with TMA tile loads
+// Same steps and thread mapping as k_tile_solve_band<float, 1, 16> (128
+// threads, 16 right-hand sides per CTA); the tiles of a step and D^{-1} are
+// fetched by one thread with cp.async.bulk(.tensor) into 128-byte-swizzled
+// shared tiles (16-byte chunk g of row r at g ^ (r & 7)), completion tracked
+// by one mbarrier per stage.  Every mbarrier wait is bounded: on timeout the
+// CTA sets *err, waits (bounded) for its copies in flight and returns.
+__device__ int g_wait_timeouts;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+constexpr long long kWaitTries = 1LL << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (long long k = 0; k < kWaitTries; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, int row, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(0), "r"(row), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load4(const float* tile, int r, int g, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(tile + r * NB + ((g ^ (r & 7)) << 2));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+
+constexpr int BT_NT = 128, BT_CG = 16, BT_ZLD = 16, BT_NST = 3;
+constexpr size_t band_tma_smem_bytes() {
+    return 1024 + sizeof(float) * ((size_t)BT_NST * BAND_SLOTS * NB2) + sizeof(double) * (size_t)BT_NST * NB * BT_ZLD +
+           sizeof(float) * ((size_t)BT_NST * NB + (size_t)(BAND_SLOTS + 1) * NB * BT_ZLD) + 8 * BT_NST;
+}
+
+__global__ void __launch_bounds__(BT_NT) k_tile_solve_band_tma(
+    const __grid_constant__ CUtensorMap tmt, const float* __restrict__ dinv, const int* __restrict__ kb_,
+    const int* __restrict__ K_, const long long* __restrict__ toff_, const long long* __restrict__ roff_,
+    double* __restrict__ Xall, int ldx, int ncols_all, const int* __restrict__ skip, const int* __restrict__ gdone)
+{
+    constexpr int NST = BT_NST, ZLD = BT_ZLD, NT = BT_NT;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    float* St = reinterpret_cast<float*>(base);                               // [NST][SLOTS][32*32]
+    double* Sx = reinterpret_cast<double*>(St + (size_t)NST * BAND_SLOTS * NB2); // [NST][32][ZLD]
+    float* Sd = reinterpret_cast<float*>(Sx + (size_t)NST * NB * ZLD);         // [NST][32]
+    float* Zr = Sd + (size_t)NST * NB;                                         // [SLOTS][32][ZLD]
+    float* Acc = Zr + (size_t)BAND_SLOTS * NB * ZLD;                           // [32][ZLD]
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(Acc + (size_t)NB * ZLD);
+    const int i = blockIdx.x;
+    if (skip && skip[i]) return;
+    if (gdone && *gdone) return;
+    const int cbase = blockIdx.y * ZLD;
+    const int ncols = min(ZLD, ncols_all - cbase);
+    double* __restrict__ X = Xall + cbase;
+    const int cpr = (ncols + 1) / 2;                    // 16-byte chunks of a staged X row
+    const int kb = kb_[i], K = K_[i];
+    const long long toff = toff_[i], roff = roff_[i];
+    const int t = threadIdx.x;
+    const int rg = t / BT_CG, c0 = t % BT_CG, warp = t >> 5;
+    const int r0 = 4 * rg;
+    const int wrow_lo = 8 * warp, wgrp_hi = 2 * warp + 1;   // rows 8 warp .. 8 warp + 7
+    if (t == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        fence_async_smem();
+    }
+    __syncthreads();
+    unsigned phase = 0, pending = 0;                   // per-stage parity; stages with copies in flight (thread 0)
+    auto stile = [&](int st, int slot) { return St + (size_t)(st * BAND_SLOTS + slot) * NB2; };
+    auto issue = [&](int st, int R, bool fwd) {
+        if (R >= 0 && R < K) {
+            if (t == 0) {
+                fence_async_smem();
+                int nt = 1;
+                for (int d = 1; d <= kb; ++d) {
+                    const int o = fwd ? R - d : R + d;
+                    if (o >= 0 && o < K) ++nt;
+                }
+                mbar_expect_tx(&bars[st], nt * NB2 * 4 + (fwd ? 0 : NB * 4));
+                tma_load_tile(stile(st, 0), &tmt, (int)(tile_index(toff, kb, R, R) / NB), &bars[st]);
+                for (int d = 1; d <= kb; ++d) {
+                    const int o = fwd ? R - d : R + d;
+                    if (o < 0 || o >= K) continue;
+                    const long long ti = fwd ? tile_index(toff, kb, R, o) : tile_index(toff, kb, o, R);
+                    tma_load_tile(stile(st, d), &tmt, (int)(ti / NB), &bars[st]);
+                }
+                if (!fwd) bulk_load(Sd + st * NB, dinv + roff + (long long)R * NB, NB * 4, &bars[st]);
+                pending |= 1u << st;
+            }
+            const double* src = X + (roff + (long long)R * NB) * ldx;
+            double* dst = Sx + (size_t)st * NB * ZLD;
+            for (int ch = t; ch < NB * cpr; ch += NT) {
+                const int r = ch / cpr, c = (ch % cpr) * 2;
+                cp_async16(dst + r * ZLD + c, src + (long long)r * ldx + c);
+            }
+        }
+        cp_async_commit();
+    };
+    // wait for stage st (TMA part: bounded); false if any thread gave up
+    auto wait_stage = [&](int st) -> bool {
+        cp_async_wait_n<NST - 2>();
+        const bool ok = mbar_wait_bounded(&bars[st], (phase >> st) & 1u);
+        phase ^= 1u << st;
+        if (t == 0) pending &= ~(1u << st);
+        return !__syncthreads_or(!ok);
+    };
+    auto abort_cta = [&]() {
+        if (t == 0) {
+            atomicAdd(&g_wait_timeouts, 1);
+            for (int s = 0; s < NST; ++s)
+                if (pending & (1u << s)) mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
+        }
+        cp_async_wait_n<0>();
+        __syncthreads();
+    };
+    auto finish = [&](float (&acc)[4], int R, const float* Tt, bool fwd) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) Acc[(r0 + a) * ZLD + c0] = acc[a];
+        __syncthreads();
+        float out[4] = {0.f, 0.f, 0.f, 0.f};
+        if (fwd) {
+#pragma unroll 4
+            for (int g = 0; g <= wgrp_hi; ++g) {
+                float l[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) tma_load4(Tt, r0 + a, g, l[a]);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float zv = Acc[(4 * g + kk) * ZLD + c0];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) out[a] += l[a][kk] * zv;
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int k = wrow_lo; k < NB; ++k) {
+                float l[4];
+                tma_load4(Tt, k, rg, l);
+                const float zv = Acc[k * ZLD + c0];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) out[a] += l[a] * zv;
+            }
+        }
+        float* Zw = Zr + (size_t)(R % BAND_SLOTS) * NB * ZLD;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            Zw[(r0 + a) * ZLD + c0] = out[a];
+            if (c0 < ncols) X[(roff + (long long)R * NB + r0 + a) * ldx + c0] = f32_to_f64(out[a]);
+        }
+    };
+
+    // forward: z_R = T_R (x_R - sum_J L_RJ z_J)
+    for (int k = 0; k < NST - 1; ++k) issue(k, k, true);
+    for (int R = 0; R < K; ++R) {
+        const int st = R % NST;
+        if (!wait_stage(st)) { abort_cta(); return; }
+        issue((R + NST - 1) % NST, R + NST - 1, true);
+        float acc[4];
+        const double* xs = Sx + (size_t)st * NB * ZLD;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a] = c0 < ncols ? f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
+        for (int d = 1; d <= kb; ++d) {
+            if (R - d < 0) break;
+            const float* L = stile(st, d);
+            const float* Z = Zr + (size_t)((R - d) % BAND_SLOTS) * NB * ZLD;
+#pragma unroll
+            for (int g = 0; g < NB / 4; ++g) {
+                float l[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) tma_load4(L, r0 + a, g, l[a]);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float zv = Z[(4 * g + kk) * ZLD + c0];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) acc[a] -= l[a][kk] * zv;
+                }
+            }
+        }
+        finish(acc, R, stile(st, 0), true);
+    }
+    cp_async_wait_n<0>();
+    __syncthreads();
+    // backward: x_R = T_R^T (D_R^{-1} z_R - sum_I L_IR^T x_I)
+    for (int k = 0; k < NST - 1; ++k) issue(k, K - 1 - k, false);
+    for (int R = K - 1, it = 0; R >= 0; --R, ++it) {
+        const int st = it % NST;
+        if (!wait_stage(st)) { abort_cta(); return; }
+        issue((it + NST - 1) % NST, R - (NST - 1), false);
+        float acc[4];
+        const double* xs = Sx + (size_t)st * NB * ZLD;
+        const float* dv = Sd + st * NB;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a] = c0 < ncols ? dv[r0 + a] * f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
+        for (int d = 1; d <= kb; ++d) {
+            if (R + d >= K) break;
+            const float* L = stile(st, d);
+            const float* Z = Zr + (size_t)((R + d) % BAND_SLOTS) * NB * ZLD;
+#pragma unroll 8
+            for (int k = 0; k < NB; ++k) {
+                float l[4];
+                tma_load4(L, k, rg, l);
+                const float zv = Z[k * ZLD + c0];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a] -= l[a] * zv;
+            }
+        }
+        finish(acc, R, stile(st, 0), false);
+    }
+    cp_async_wait_n<0>();
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// The tile descriptor of an FP32 batch (built once per tiles_f allocation).
+const CUtensorMap* tile_tensor_map(const TileBatch& tb) {
+    if (!tb.prec || !tb.tiles_f.p || tb.total_tile_elems <= 0) return nullptr;
+    if (tb.tmap_base == tb.tiles_f.p) return reinterpret_cast<const CUtensorMap*>(tb.tmap_tiles);
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return nullptr;
+    const cuuint64_t dims[2] = {(cuuint64_t)NB, (cuuint64_t)(tb.total_tile_elems / NB)};
+    const cuuint64_t strides[1] = {(cuuint64_t)NB * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)NB, (cuuint32_t)NB};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(tb.tmap_tiles);
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)tb.tiles_f.p, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nullptr;
+    tb.tmap_base = tb.tiles_f.p;
+    return m;
+}
+
 template <typename T, int CPT, int CG>
 void launch_band(const TileBatch& tb, const T* tiles, const T* dinv, double* X, int ldx, int ncols, const int* skip,
                  cudaStream_t s, const int* gdone) {
@@ -785,6 +1058,7 @@ __global__ void k_tile_from_dense(T* __restrict__ tiles, const int* __restrict__
 void TileBatch::layout(const std::vector<int>& n_, const std::vector<int>& b_, int precision, cudaStream_t s) {
     P = (int)n_.size();
     prec = precision;
+    tmap_base = nullptr;
     n = n_;
     kb.resize(P);
     K.resize(P);
@@ -862,6 +1136,16 @@ void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
     MSDD_LAUNCH_CHECK();
 }
 
+void tile_check_waits() {
+    int n = 0;
+    MSDD_CUDA(cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof(int)));
+    if (n) {
+        const int zero = 0;
+        MSDD_CUDA(cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(int)));
+        throw std::runtime_error("a band solve gave up waiting for its tile copies (" + std::to_string(n) + " CTAs)");
+    }
+}
+
 void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* skip, cudaStream_t s,
                 const int* gdone) {
     if (tb.P == 0) return;
@@ -902,8 +1186,18 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
     // the band kernel stages blocks of X with 16-byte copies
     const bool band_ok = maxkb <= 2 && ncols <= NB && ldx % 2 == 0 && ((uintptr_t)X % 16) == 0;
     if (band_ok) {
-        if (tb.prec) launch_band_cols<float>(tb, tb.tiles_f.p, tb.dinv_f.p, X, ldx, ncols, skip, s, gdone);
-        else launch_band_cols<double>(tb, tb.tiles_d.p, tb.dinv_d.p, X, ldx, ncols, skip, s, gdone);
+        const CUtensorMap* tm = tile_tensor_map(tb);
+        if (tm) {
+            const size_t b = band_tma_smem_bytes();
+            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_band_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            k_tile_solve_band_tma<<<dim3(tb.P, (ncols + BT_ZLD - 1) / BT_ZLD), BT_NT, b, s>>>(
+                *tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
+            MSDD_LAUNCH_CHECK();
+        } else if (tb.prec) {
+            launch_band_cols<float>(tb, tb.tiles_f.p, tb.dinv_f.p, X, ldx, ncols, skip, s, gdone);
+        } else {
+            launch_band_cols<double>(tb, tb.tiles_d.p, tb.dinv_d.p, X, ldx, ncols, skip, s, gdone);
+        }
         return;
     }
     const dim3 grid(tb.P, (ncols + NB - 1) / NB);

@@ -29,6 +29,10 @@ struct TileBatch {
     DevBuf<long long> d_toff, d_roff;
     DevBuf<double> tiles_d, dinv_d;
     DevBuf<float> tiles_f, dinv_f;
+    // TMA descriptor (opaque CUtensorMap) of the FP32 tiles viewed as a
+    // [total_tile_elems / 32][32] matrix, built on first use for tiles_f.p
+    alignas(64) mutable unsigned char tmap_tiles[128] = {};
+    mutable const float* tmap_base = nullptr;
 
     // Layout from per-problem sizes and half-bandwidths.
     void layout(const std::vector<int>& n_, const std::vector<int>& b_, int precision, cudaStream_t s);
@@ -55,5 +59,8 @@ void tile_identity(const TileBatch& tb, double* E, int lde, cudaStream_t s);
 // skips everything when non-zero.
 void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* skip, cudaStream_t s,
                 const int* gdone = nullptr);
+// Throws if a bounded wait in a solve kernel gave up (its error flag is
+// reset); call after a synchronisation point.
+void tile_check_waits();
 
 }  // namespace msdd
