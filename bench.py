@@ -31,6 +31,30 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64, nominal (used only for "alu"-bound kernels)
 
 
+def measured_traffic(family):
+    """DRAM traffic of the family's kernel from the committed ncu summary
+    (profiles/traffic.txt: key=value lines).  The figure holds only for the
+    kernel source it was captured from: null when that file's SHA-256 differs."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
+    except OSError:
+        return {}
+    if kv.get("family") != family:
+        return {}
+    src = os.path.join(ROOT, kv.get("source", ""))
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return {}
+    if digest != kv.get("source_sha256"):
+        return {"traffic": None, "traffic_note": "kernel source changed since the ncu capture"}
+    return {"traffic": float(kv["dram_bytes_per_launch"]),
+            "traffic_launch_algorithmic_bytes": float(kv["algorithmic_bytes_captured_launch"]),
+            "traffic_kernel": kv.get("kernel"), "traffic_source": "profiles/traffic.txt"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +328,7 @@ def run_ours(args, rank, world, local_rank):
                  "arith_intensity_flop_per_byte": round(intensity, 3),
                  "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
                  "traffic": None, "share_of_step": round(pf["ms"] / 1e3 / (total / args.steps) / args.steps, 4)})
+    roof.update(measured_traffic(fam))
 
     cpu = None
     if cpu_p is not None:
