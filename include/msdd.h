@@ -91,7 +91,9 @@ typedef struct msdd_options {
     int eig_maxit;       /* subspace iterations per level (default 200) */
     double sigma;        /* shift of K = Abar + sigma B (default 1e-2) */
     double eig_tol;      /* eigen-residual tolerance (default 1e-6) */
-    double reg_tol;      /* null-pivot threshold for coarse generating systems (default 1e-10) */
+    double reg_tol;      /* null-pivot threshold for coarse generating systems, pivots
+                            d_k <= reg_tol * K_kk are null; < 0 (default) selects 1e-10 in 2D
+                            and 1e-6 in 3D; must be < 1 */
     unsigned long long seed;  /* start vectors of the subspace iteration */
     void* stream;        /* cudaStream_t */
     int profile;         /* 1: time kernel families with CUDA events (see msdd_stats.prof) */

@@ -73,6 +73,31 @@ class FineSubdomain:
         return self._box_nodes(self.mesh, self.dirichlet_box)
 
 
+def fine_subdomain(mesh, parts, overlap, pidx):
+    """Fine subdomain with grid index pidx (x fastest): its core element block
+    of the box split, extended by `overlap` layers and clipped (Section 2.2)."""
+    core = [split_axis(mesh.n[d], parts[d])[pidx[d]] for d in range(mesh.dim)]
+    ext = [(max(0, c[0] - overlap), min(mesh.n[d], c[1] + overlap)) for d, c in enumerate(core)]
+    return FineSubdomain(mesh, ext, core)
+
+
+def pou_counts(mesh, subs):
+    """N(x): the number of subdomains in `subs` for which node x is interior
+    (its hat function supported in the closed subdomain)."""
+    counts = np.zeros(mesh.num_nodes)
+    for s in subs:
+        counts[s.dirichlet_nodes()] += 1.0
+    return counts
+
+
+def pou_chi(mesh, sub, counts):
+    """chi of `sub` on its Neumann nodes: 1 / N(x) at its interior nodes, 0 elsewhere."""
+    nn = sub.neumann_nodes()
+    interior = np.zeros(mesh.num_nodes, dtype=bool)
+    interior[sub.dirichlet_nodes()] = True
+    return np.where(interior[nn], 1.0 / np.maximum(counts[nn], 1.0), 0.0)
+
+
 class Decomposition:
     """Fine subdomains plus the coarse grouping for `levels` levels.
 
@@ -91,14 +116,11 @@ class Decomposition:
         self.levels = levels
         self.L = levels - 1
         dim = mesh.dim
-        splits = [split_axis(mesh.n[d], parts[d]) for d in range(dim)]
         self.fine = []
         self.fine_grid = []
         for pidx in np.ndindex(*[parts[d] for d in reversed(range(dim))]):
             pidx = tuple(reversed(pidx))                     # x fastest
-            core = [splits[d][pidx[d]] for d in range(dim)]
-            ext = [(max(0, c[0] - overlap), min(mesh.n[d], c[1] + overlap)) for d, c in enumerate(core)]
-            self.fine.append(FineSubdomain(mesh, ext, core))
+            self.fine.append(fine_subdomain(mesh, parts, overlap, pidx))
             self.fine_grid.append(pidx)
         # coarse grouping
         self.grid_shape = {self.L: tuple(parts)}
@@ -139,17 +161,8 @@ class Decomposition:
 
     def partition_of_unity(self):
         """chi_i as arrays over each subdomain's Neumann nodes (fine level)."""
-        counts = np.zeros(self.mesh.num_nodes)
-        for s in self.fine:
-            counts[s.dirichlet_nodes()] += 1.0
-        chis = []
-        for s in self.fine:
-            nn = s.neumann_nodes()
-            interior = np.zeros(self.mesh.num_nodes, dtype=bool)
-            interior[s.dirichlet_nodes()] = True
-            chi = np.where(interior[nn], 1.0 / np.maximum(counts[nn], 1.0), 0.0)
-            chis.append(chi)
-        return chis, counts
+        counts = pou_counts(self.mesh, self.fine)
+        return [pou_chi(self.mesh, s, counts) for s in self.fine], counts
 
     def neighbours(self, l, i):
         """Level-(l+1) subdomains j not in J_{l,i} with T_{l+1,j} meeting T_{l,i} (Section 4.2)."""

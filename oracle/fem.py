@@ -157,7 +157,8 @@ def q1_element_matrix_2d_scalar(kappa, hx, hy):
 
 
 def element_matrices(mesh, coeff):
-    """(num_elements, 2^d, 2^d) element stiffness matrices."""
+    """(len(coeff), 2^d, 2^d) element stiffness matrices of the elements whose
+    coefficients are given (all elements of the mesh, or a subset)."""
     K = tensor_from_coefficient(mesh.dim, coeff)
     coeff = np.asarray(coeff, dtype=np.float64)
     if coeff.ndim == 1:
@@ -165,7 +166,7 @@ def element_matrices(mesh, coeff):
         return coeff[:, None, None] * ref[None]
     # general tensor: the element matrix is linear in K; build from the
     # d*(d+1)/2 basis tensors
-    out = np.zeros((mesh.num_elements, 2 ** mesh.dim, 2 ** mesh.dim))
+    out = np.zeros((coeff.shape[0], 2 ** mesh.dim, 2 ** mesh.dim))
     for i in range(mesh.dim):
         for j in range(mesh.dim):
             E = np.zeros((mesh.dim, mesh.dim))

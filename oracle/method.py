@@ -96,22 +96,23 @@ def select_count(lam, nev_max, eta):
     return int(min(nev_max, int(np.sum(lam < eta))))
 
 
-def fine_pencil(mesh, Ke, en, sub, chi):
+def fine_pencil(mesh, Ke, en, sub, chi, Ke_of_subdomain=False):
     """Dense Neumann matrix Abar_i (Eq. locala_cg: the element forms of
     T_{h,L,i} on all non-Dirichlet nodes of the closed subdomain) and
     B_i = X_i Abar_i X_i (b^1, Eq. cg_rhs_blf) of one fine subdomain, rows in
-    its lexicographic Neumann-node order; Ke / en are the element matrices
-    and element nodes of the whole mesh, chi the subdomain's partition of
-    unity on those nodes (Section 2.3)."""
+    its lexicographic Neumann-node order; en are the element nodes of the
+    whole mesh, Ke the element matrices of the whole mesh (or, with
+    Ke_of_subdomain, of the subdomain's elements in ascending order), chi the
+    subdomain's partition of unity on its Neumann nodes (Section 2.3)."""
     nn = sub.neumann_nodes()
     pos = -np.ones(mesh.num_nodes, dtype=np.int64)
     pos[nn] = np.arange(len(nn))
     Abar = np.zeros((len(nn), len(nn)))
-    for e in np.nonzero(sub.element_mask)[0]:
+    for k, e in enumerate(np.nonzero(sub.element_mask)[0]):
         loc = pos[en[e]]
         ok = loc >= 0
         li = loc[ok]
-        Abar[np.ix_(li, li)] += Ke[e][np.ix_(ok, ok)]
+        Abar[np.ix_(li, li)] += (Ke[k] if Ke_of_subdomain else Ke[e])[np.ix_(ok, ok)]
     B = chi[:, None] * Abar * chi[None, :]
     return nn, Abar, B
 

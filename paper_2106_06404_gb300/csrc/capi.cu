@@ -80,7 +80,7 @@ msdd_status msdd_default_options(msdd_options* opt) {
     opt->eig_maxit = 200;
     opt->sigma = 1e-2;
     opt->eig_tol = 1e-6;
-    opt->reg_tol = 1e-10;
+    opt->reg_tol = -1.0;            // automatic: 1e-10 in 2D, 1e-6 in 3D
     opt->seed = 12345;
     opt->stream = nullptr;
     opt->profile = 0;
@@ -120,7 +120,7 @@ msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msd
         if (opt.block_p < 0 || opt.block_p > msdd::PMAX) return fail(MSDD_ERR_INVALID_ARG, "block_p out of range");
         if (opt.block_p > 0 && opt.block_p <= spectral->nev_max)
             return fail(MSDD_ERR_INVALID_ARG, "block_p must exceed nev_max");
-        if (!(opt.sigma > 0.0) || !(opt.eig_tol > 0.0) || opt.eig_maxit < 1 || opt.reg_tol < 0.0 ||
+        if (!(opt.sigma > 0.0) || !(opt.eig_tol > 0.0) || opt.eig_maxit < 1 || !(opt.reg_tol < 1.0) ||
             opt.fp32_start_iters < 0 || opt.fp32_start_iters > 1000)
             return fail(MSDD_ERR_INVALID_ARG, "invalid eigensolver options");
         msdd_hierarchy* H = new msdd_hierarchy();

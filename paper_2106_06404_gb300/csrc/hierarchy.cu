@@ -745,7 +745,10 @@ void Hierarchy::build_coarse() {
         for (int i = 0; i < Pm; ++i) bw[i] = std::max(0, ngen[i] - 1);
         mge.K.layout(ngen, bw, 0, st);
         tile_from_dense(mge.K, K_m.p, d_aoff.p, d_ngen.p, st);
-        tile_factor(mge.K, opt.reg_tol, st);
+        // null-pivot threshold of the generating systems: negative = automatic
+        // (3D generating systems carry more near-dependent neighbour generators)
+        const double reg_tol = opt.reg_tol >= 0.0 ? opt.reg_tol : (g.dim == 3 ? 1e-6 : 1e-10);
+        tile_factor(mge.K, reg_tol, st);
         stats.null_pivots[1] = sum_nreg(mge.K, st);
         // K^+ explicitly (overwrites K_m): every later solve is a batched GEMM
         dense_inverse(mge.K, K_m.p, aoff, ngen, st);

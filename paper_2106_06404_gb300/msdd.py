@@ -178,7 +178,7 @@ class Hierarchy:
     """
 
     def __init__(self, n, coeff, parts, overlap, levels, group, nev_max, eta, dirichlet_faces=0b1,
-                 precision=0, block_p=0, eig_maxit=200, sigma=1e-2, eig_tol=1e-6, reg_tol=1e-10, seed=12345,
+                 precision=0, block_p=0, eig_maxit=200, sigma=1e-2, eig_tol=1e-6, reg_tol=-1.0, seed=12345,
                  allow_eig_unconverged=False, profile=False, fp32_start_iters=None):
         torch = _torch()
         lib = load()

@@ -1,0 +1,110 @@
+"""Parity at the full size of the 3D composite workload: 128^3 Q1 hexahedra
+(2,130,048 unknowns), layered anisotropic tensor coefficient, 8 x 8 x 8 fine
+subdomains with overlap 1, 3 levels (2 x 2 x 2 groups), nev <= 16, eta = 0.3,
+chosen form (FP32 local factors, FP64 outer iteration).
+
+As for the 2D workload, the oracle cannot run the whole set-up at this size,
+so two sampled fine subdomains (a corner on the Dirichlet face and an
+interior one, 6859 nodes, half-bandwidth 381) are checked against the
+oracle's dense pencils (Abar_i, B_i):
+
+* Sylvester inertia brackets around selected Ritz values (the first two and
+  the last two selected), see tests/test_gpu_fullsize.py;
+* the selection count m_i = min(nev_max, #{lambda < eta});
+* b(w, w) = 1 of the exported coarse basis functions (phi^T Abar_i phi = I).
+
+Globally: the PCG stopping rule (recursive residual below 1e-8 of ||b||,
+Section 5) within the iteration limit, all generating-system GEVPs of the
+middle level converged, and the coarse dimensions sum of the selected counts.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2106_06404_gb300 as pkg  # noqa: E402
+from oracle import fem, linalg  # noqa: E402
+from oracle.decomposition import fine_subdomain, pou_chi, pou_counts  # noqa: E402
+from oracle.method import fine_pencil  # noqa: E402
+from synthetic_inputs import composite128  # noqa: E402
+
+SIGMA = 1e-2
+SAMPLE = ((0, 0, 0), (3, 4, 3))          # fine grid indices, x fastest
+
+
+def flat(pidx, parts):
+    return pidx[0] + parts[0] * (pidx[1] + parts[1] * pidx[2])
+
+
+@pytest.fixture(scope="module")
+def case():
+    w = composite128()
+    kappa = w.coefficient()
+    mesh = fem.Mesh(w.n, w.dirichlet_faces)
+    H = pkg.Hierarchy(w.n, torch.tensor(kappa, device="cuda"), w.parts, w.overlap, w.levels, w.group,
+                      w.nev_max, w.eta, dirichlet_faces=w.dirichlet_faces, precision=1, sigma=SIGMA)
+    en = mesh.element_nodes()
+    pencils = {}
+    for pidx in SAMPLE:
+        sub = fine_subdomain(mesh, w.parts, w.overlap, pidx)
+        # N(x) at this subdomain's nodes only involves its neighbours
+        near = []
+        for off in np.ndindex(3, 3, 3):
+            q = tuple(pidx[d] + off[d] - 1 for d in range(3))
+            if all(0 <= q[d] < w.parts[d] for d in range(3)):
+                near.append(fine_subdomain(mesh, w.parts, w.overlap, q))
+        chi = pou_chi(mesh, sub, pou_counts(mesh, near))
+        els = np.nonzero(sub.element_mask)[0]
+        Ke = fem.element_matrices(mesh, kappa[els])
+        pencils[flat(pidx, w.parts)] = fine_pencil(mesh, Ke, en, sub, chi, Ke_of_subdomain=True)
+    yield w, mesh, H, pencils
+    H.close()
+
+
+def count_below(Abar, B, t):
+    return linalg.negative_count(Abar - t * B)
+
+
+@pytest.mark.parametrize("pidx", SAMPLE)
+def test_fine_ritz_values_and_selection(case, pidx):
+    w, _, H, pencils = case
+    i = flat(pidx, w.parts)
+    _, Abar, B = pencils[i]
+    theta, m = H.eigenvalues(w.levels - 1, i)
+    assert 1 <= m <= w.nev_max
+    for k in sorted({1, 2, m - 1, m} - {0}):
+        th = theta[k - 1]
+        d = 1e-4 * (th + SIGMA)
+        assert count_below(Abar, B, th - d) <= k - 1, (i, k, th)
+        assert count_below(Abar, B, th + d) >= k, (i, k, th)
+    lo = min(w.nev_max, count_below(Abar, B, w.eta * (1 - 1e-6)))
+    hi = min(w.nev_max, count_below(Abar, B, w.eta * (1 + 1e-6)))
+    assert lo <= m <= hi, (i, m, lo, hi)
+
+
+@pytest.mark.parametrize("pidx", SAMPLE)
+def test_fine_basis_b_orthonormal(case, pidx):
+    w, mesh, H, pencils = case
+    i = flat(pidx, w.parts)
+    nn, Abar, _ = pencils[i]
+    phi = H.fine_basis(i)
+    u = mesh.node_to_unknown()[nn]
+    assert np.all(u >= 0)
+    P = phi[u]
+    G = P.T @ Abar @ P
+    assert np.max(np.abs(G - np.eye(G.shape[0]))) < 1e-8
+
+
+def test_hierarchy_and_pcg(case):
+    w, mesh, H, _ = case
+    st = H.stats()
+    assert st["eig_unconverged"] == [0] * w.levels
+    assert st["level_dim"][-1] == mesh.node_to_unknown().max() + 1
+    b = pkg.assemble_rhs(w.n, w.dirichlet_faces)
+    x, it, rel = H.solve(b, tol=1e-8, maxit=1000)
+    assert rel < 1e-8 and it < 1000
+    assert torch.isfinite(x).all()
