@@ -149,3 +149,16 @@ def composite128(seed=0):
     """3D, 128^3 Q1, layered anisotropic tensor, 8^3 subdomains, overlap 1, three levels, nev <= 16."""
     return Workload("composite3d_128_8x8x8_3lvl", (128, 128, 128), (8, 8, 8), 1, 3, (2, 2, 2), 16, 0.3,
                     seed=seed, kind="composite")
+
+
+def mlp_init(seed, shapes):
+    """Seeded He-normal weights (std sqrt(2 / fan_in) for 2-D shapes (fan_out, fan_in)),
+    zero biases (1-D shapes), concatenated row-major as float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in shapes:
+        if len(s) == 2:
+            parts.append(rng.standard_normal(s) * np.sqrt(2.0 / s[1]))
+        else:
+            parts.append(np.zeros(s))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
