@@ -99,6 +99,12 @@ typedef struct msdd_options {
     int profile;         /* 1: time kernel families with CUDA events (see msdd_stats.prof) */
     int fp32_start_iters;/* precision 1: fine-level FP32 subspace iterations (FP32 B apply and
                             solve, Euclidean CholQR) before the FP64 iterations (default 20) */
+    const double* warm_start; /* device, may be NULL (default): start vectors of the fine-level
+                            subspace iteration, rows = the fine subdomains' Neumann-box nodes
+                            (subdomain order, each box lexicographic, x fastest) and warm_cols
+                            columns (row-major); they replace the first warm_cols random start
+                            columns.  Read during msdd_setup only (see msdd_nn_start_vectors) */
+    int warm_cols;       /* 0 .. block size (default 0) */
 } msdd_options;
 
 /* Per kernel family timing, filled when options.profile = 1.  bytes and flops
@@ -139,6 +145,9 @@ typedef struct msdd_stats {
     size_t device_bytes;                      /* held by the hierarchy */
     int nprof;
     msdd_kernel_prof prof[MSDD_MAX_PROF];     /* accumulated over set-up and solves */
+    long long eig_iters_total[MSDD_MAX_LEVELS]; /* subspace iterations summed over the level's
+                                                 subdomains (FP64 phase; the fine FP32 start
+                                                 phase adds fp32_start_iters per subdomain) */
 } msdd_stats;
 
 typedef struct msdd_hierarchy msdd_hierarchy;   /* opaque, library-owned */
@@ -241,6 +250,66 @@ void msdd_band_destroy(msdd_band_batch* bb);
  * Arguments and layout of X are those of msdd_band_solve; returns after the
  * work on `stream` has completed. */
 msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nrhs, double* X, void* stream);
+
+/* ---- learned warm start of the fine subspace iteration ----------------------
+ * Not part of the paper's method (its eigensolver starts without a learned
+ * guess): a small network maps a fine subdomain's coefficient patch to start
+ * vectors for the subspace iteration of Eq. theGEVP; the Rayleigh-Ritz step
+ * and the residual test stay the judge, so a poor prediction costs
+ * iterations, never accuracy.  2D scalar coefficients only.
+ *
+ * Network: input = log10 kappa of the subdomain's element box area-averaged
+ * onto MSDD_NN_PATCH^2 equal cells, minus its mean, divided by 6; MLP
+ * IN -> HIDDEN -> HIDDEN -> OUT with ReLU; weights rounded to bfloat16 (to
+ * nearest even) when used, biases and arithmetic FP32; output = MSDD_NN_NVEC
+ * vectors on an MSDD_NN_GRID^2 node grid over the Neumann box (vector k at
+ * k * GRID^2, node (gx, gy) at gx + GRID gy).  Parameters: one FP32 array of
+ * MSDD_NN_NPARAM values, W1 (HIDDEN x IN, row-major), b1, W2 (HIDDEN x
+ * HIDDEN), b2, W3 (OUT x HIDDEN), b3, in this order.
+ * Loss of a sample with unit targets T (GRID^2 x m) and prediction Y
+ * (GRID^2 x NVEC): (min_C |T - Y C|_F^2 + 1e-6 |C|_F^2) / m, independent of
+ * the basis of span(Y); batch loss = mean over samples.
+ * All pointers are device pointers unless stated; calls are asynchronous
+ * on `stream` except where a host output is written. */
+#define MSDD_NN_PATCH 24
+#define MSDD_NN_HIDDEN 48
+#define MSDD_NN_GRID 13
+#define MSDD_NN_NVEC 12
+#define MSDD_NN_IN (MSDD_NN_PATCH * MSDD_NN_PATCH)
+#define MSDD_NN_OUT (MSDD_NN_NVEC * MSDD_NN_GRID * MSDD_NN_GRID)
+#define MSDD_NN_NPARAM (MSDD_NN_HIDDEN * MSDD_NN_IN + MSDD_NN_HIDDEN + MSDD_NN_HIDDEN * MSDD_NN_HIDDEN + \
+                        MSDD_NN_HIDDEN + MSDD_NN_OUT * MSDD_NN_HIDDEN + MSDD_NN_OUT)
+
+/* Number of fine subdomains and, per subdomain (host, 4 * count ints), the
+ * node counts of its Neumann box (nx, ny, 1) and the row offset of the box
+ * in warm_start layouts (as int, rows < 2^31).  count receives the number. */
+msdd_status msdd_fine_layout(const msdd_mesh* mesh, const msdd_decomp* decomp, int* out, int cap, int* count);
+/* Network inputs of all fine subdomains: X (count x MSDD_NN_IN floats). */
+msdd_status msdd_nn_patches(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp, float* X,
+                            void* stream);
+/* Bytes of caller-owned device workspace for a batch of `batch` samples. */
+size_t msdd_nn_workspace_bytes(int batch);
+/* out (batch x MSDD_NN_OUT floats) = network(params, X). */
+msdd_status msdd_nn_forward(const float* params, int batch, const float* X, float* out, void* work, void* stream);
+/* Batch loss (one double) and its gradient with respect to params (grad,
+ * MSDD_NN_NPARAM floats).  T: batch x MSDD_NN_NVEC x GRID^2 floats, unit
+ * columns, sample s column k at T[(s NVEC + k) GRID^2]; m: targets per sample
+ * (first m[s] columns used, 0..NVEC). */
+msdd_status msdd_nn_loss_grad(const float* params, int batch, const float* X, const float* T, const int* m,
+                              double* loss, float* grad, void* work, void* stream);
+/* Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step t >= 1) on
+ * params with moments m1, m2 (MSDD_NN_NPARAM floats each). */
+msdd_status msdd_nn_adam(float* params, const float* grad, float* m1, float* m2, int t, float lr, void* stream);
+/* Start vectors for options.warm_start: Y (count x MSDD_NN_OUT) bilinearly
+ * interpolated to every Neumann-box node (rows as msdd_fine_layout, NVEC
+ * columns, row-major doubles). */
+msdd_status msdd_nn_start_vectors(const msdd_mesh* mesh, const msdd_decomp* decomp, const float* Y, double* out,
+                                  void* stream);
+/* Training targets from a hierarchy: each fine subdomain's selected
+ * eigenvectors (first min(m, NVEC)) sampled at the grid nodes by bilinear
+ * interpolation of its node grid, unit 2-norm: T as in msdd_nn_loss_grad and
+ * m (count ints). */
+msdd_status msdd_nn_targets(const msdd_hierarchy* h, float* T, int* m, void* stream);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,7 @@
 #include <string>
 
 #include "capi_types.cuh"
+#include "warmstart.cuh"
 
 namespace msdd {
 long long& kernel_launch_counter() {
@@ -67,6 +68,20 @@ long long unknowns_of(const msdd_mesh* m) {
     return n;
 }
 
+bool decomp_parts_ok(const msdd_mesh* mesh, const msdd_decomp* dec) {
+    if (!dec || dec->overlap < 1) return false;
+    for (int d = 0; d < mesh->dim; ++d)
+        if (dec->parts[d] < 1 || dec->parts[d] > mesh->n[d]) return false;
+    return true;
+}
+
+// fine boxes of a 2D scalar-coefficient problem for the warm-start calls
+std::vector<msdd::ProbBox> warm_boxes(const msdd_mesh* mesh, const msdd_decomp* decomp, msdd::Geom& g) {
+    msdd_coeff none{0, nullptr};
+    g = msdd::make_geom(*mesh, none);
+    return msdd::make_fine_boxes(g, *decomp);
+}
+
 }  // namespace
 
 extern "C" {
@@ -85,6 +100,8 @@ msdd_status msdd_default_options(msdd_options* opt) {
     opt->stream = nullptr;
     opt->profile = 0;
     opt->fp32_start_iters = 20;
+    opt->warm_start = nullptr;
+    opt->warm_cols = 0;
     return MSDD_OK;
 }
 
@@ -123,6 +140,8 @@ msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msd
         if (!(opt.sigma > 0.0) || !(opt.eig_tol > 0.0) || opt.eig_maxit < 1 || !(opt.reg_tol < 1.0) ||
             opt.fp32_start_iters < 0 || opt.fp32_start_iters > 1000)
             return fail(MSDD_ERR_INVALID_ARG, "invalid eigensolver options");
+        if (opt.warm_start && (opt.warm_cols < 1 || opt.warm_cols > msdd::PMAX))
+            return fail(MSDD_ERR_INVALID_ARG, "warm_cols must be in 1..32 with warm_start");
         msdd_hierarchy* H = new msdd_hierarchy();
         H->h.opt = opt;
         H->h.spec = *spectral;
@@ -362,5 +381,114 @@ msdd_status msdd_band_solve(const msdd_band_batch* bb, int nrhs, double* X, void
 }
 
 void msdd_band_destroy(msdd_band_batch* bb) { delete bb; }
+
+// ---- learned warm start
+msdd_status msdd_fine_layout(const msdd_mesh* mesh, const msdd_decomp* decomp, int* out, int cap, int* count) {
+    return guarded([&]() -> msdd_status {
+        if (!mesh_ok(mesh) || !decomp_parts_ok(mesh, decomp)) return fail(MSDD_ERR_INVALID_ARG, "invalid mesh or decomposition");
+        msdd::Geom g;
+        std::vector<msdd::ProbBox> boxes = warm_boxes(mesh, decomp, g);
+        const int P = (int)boxes.size();
+        if (count) *count = P;
+        if (!out) return MSDD_OK;
+        if (cap < 4 * P) return fail(MSDD_ERR_INVALID_ARG, "layout buffer smaller than 4 * subdomains");
+        long long off = 0;
+        for (int i = 0; i < P; ++i) {
+            int nx[3];
+            for (int d = 0; d < 3; ++d) nx[d] = d < mesh->dim ? boxes[i].nhi[d] - boxes[i].nlo[d] + 1 : 1;
+            if (off > 0x7fffffffLL) return fail(MSDD_ERR_INVALID_ARG, "more than 2^31 rows");
+            out[4 * i] = nx[0]; out[4 * i + 1] = nx[1]; out[4 * i + 2] = nx[2]; out[4 * i + 3] = (int)off;
+            off += (long long)nx[0] * nx[1] * nx[2];
+        }
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_nn_patches(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp, float* X,
+                            void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!mesh_ok(mesh) || !decomp_parts_ok(mesh, decomp) || !X || !coeff || !coeff->data)
+            return fail(MSDD_ERR_INVALID_ARG, "invalid arguments");
+        if (mesh->dim != 2 || coeff->kind != 0)
+            return fail(MSDD_ERR_UNSUPPORTED, "the warm-start network takes 2D scalar coefficients");
+        msdd::Geom g;
+        std::vector<msdd::ProbBox> boxes = warm_boxes(mesh, decomp, g);
+        g.coeff_kind = 0;
+        g.coeff = coeff->data;
+        cudaStream_t st = (cudaStream_t)stream;
+        msdd::DevBuf<msdd::ProbBox> d_boxes;
+        d_boxes.upload(boxes, st);
+        msdd::nn_patches(g, d_boxes.p, (int)boxes.size(), X, st);
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        return MSDD_OK;
+    });
+}
+
+size_t msdd_nn_workspace_bytes(int batch) {
+    return batch < 1 ? 0 : msdd::nn_workspace_floats(batch) * sizeof(float);
+}
+
+msdd_status msdd_nn_forward(const float* params, int batch, const float* X, float* out, void* work, void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!params || batch < 1 || !X || !out || !work) return fail(MSDD_ERR_INVALID_ARG, "invalid arguments");
+        msdd::nn_forward(params, batch, X, out, (float*)work, (cudaStream_t)stream);
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_nn_loss_grad(const float* params, int batch, const float* X, const float* T, const int* m,
+                              double* loss, float* grad, void* work, void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!params || batch < 1 || !X || !T || !m || !loss || !grad || !work)
+            return fail(MSDD_ERR_INVALID_ARG, "invalid arguments");
+        msdd::nn_loss_grad(params, batch, X, T, m, loss, grad, (float*)work, (cudaStream_t)stream);
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_nn_adam(float* params, const float* grad, float* m1, float* m2, int t, float lr, void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!params || !grad || !m1 || !m2 || t < 1 || !(lr > 0.f)) return fail(MSDD_ERR_INVALID_ARG, "invalid arguments");
+        msdd::nn_adam(params, grad, m1, m2, t, lr, (cudaStream_t)stream);
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_nn_start_vectors(const msdd_mesh* mesh, const msdd_decomp* decomp, const float* Y, double* out,
+                                  void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!mesh_ok(mesh) || !decomp_parts_ok(mesh, decomp) || !Y || !out)
+            return fail(MSDD_ERR_INVALID_ARG, "invalid arguments");
+        if (mesh->dim != 2) return fail(MSDD_ERR_UNSUPPORTED, "the warm-start network is 2D");
+        msdd::Geom g;
+        std::vector<msdd::ProbBox> boxes = warm_boxes(mesh, decomp, g);
+        std::vector<long long> off(boxes.size());
+        long long o = 0;
+        for (size_t i = 0; i < boxes.size(); ++i) {
+            off[i] = o;
+            o += (long long)(boxes[i].nhi[0] - boxes[i].nlo[0] + 1) * (boxes[i].nhi[1] - boxes[i].nlo[1] + 1);
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        msdd::DevBuf<msdd::ProbBox> d_boxes;
+        msdd::DevBuf<long long> d_off;
+        d_boxes.upload(boxes, st);
+        d_off.upload(off, st);
+        msdd::nn_start_vectors(d_boxes.p, d_off.p, (int)boxes.size(), 2, Y, out, st);
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_nn_targets(const msdd_hierarchy* h, float* T, int* m, void* stream) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !T || !m) return fail(MSDD_ERR_INVALID_ARG, "invalid arguments");
+        const msdd::Hierarchy& H = h->h;
+        if (H.g.dim != 2) return fail(MSDD_ERR_UNSUPPORTED, "the warm-start network is 2D");
+        cudaStream_t st = (cudaStream_t)stream;
+        msdd::nn_targets(H.d_fboxes.p, H.fge.K.d_roff.p, H.fge.m.p, H.Pf, H.g.dim, H.fge.X.p, H.fge.ldx, T, m, st);
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        return MSDD_OK;
+    });
+}
 
 }  // extern "C"

@@ -899,6 +899,19 @@ __global__ void k_dense_pencil(const double* __restrict__ A, const long long* __
     }
 }
 
+__global__ void k_load_start(double* __restrict__ X, const double* __restrict__ Wst, int wc,
+                             const long long* __restrict__ woff, const int* __restrict__ n_,
+                             const long long* __restrict__ roff_, const int* __restrict__ p_, int ldx) {
+    const int i = blockIdx.y;
+    const int n = n_[i], c1 = min(wc, p_[i]);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * c1;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / c1;
+        const int c = (int)(e % c1);
+        X[(roff_[i] + r) * ldx + c] = Wst[(woff[i] + r) * wc + c];
+    }
+}
+
 }  // namespace
 
 void GevpBatch::alloc(cudaStream_t s) {
@@ -920,6 +933,13 @@ void GevpBatch::alloc(cudaStream_t s) {
     rank.alloc(P);
     iters.alloc(P);
     n_active.alloc(1);
+}
+
+void eig_load_start(GevpBatch& g, const double* Wst, int wc, const long long* d_woff, cudaStream_t s) {
+    if (g.P == 0 || !Wst || wc <= 0) return;
+    dim3 grid(32, g.P);
+    k_load_start<<<grid, 256, 0, s>>>(g.X.p, Wst, wc, d_woff, g.K.d_n.p, g.K.d_roff.p, g.d_p.p, g.ldx);
+    MSDD_LAUNCH_CHECK();
 }
 
 void eig_init(GevpBatch& g, unsigned long long seed, cudaStream_t s) {

@@ -50,6 +50,9 @@ struct EigParams {
 // Fill X with counter-based random numbers (rows < n_i, columns < p_i) and
 // zero the rest; reset per-problem state.
 void eig_init(GevpBatch& g, unsigned long long seed, cudaStream_t s);
+// X[:, c] <- Wst rows (woff[i] + r), columns c < min(wc, p_i), for rows r < n_i
+// (caller-provided start vectors; the remaining columns keep eig_init's).
+void eig_load_start(GevpBatch& g, const double* Wst, int wc, const long long* d_woff, cudaStream_t s);
 // W = BX - (AX + sigma BX) diag(mu) (first == true: W = BX).
 void eig_form_rhs(GevpBatch& g, double sigma, bool first, cudaStream_t s);
 // Y = X diag(mu) + W (first == true: Y = W).

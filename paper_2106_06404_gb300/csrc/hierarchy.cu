@@ -99,9 +99,11 @@ void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long
 // are the algorithmic amounts of one operator application per problem.
 template <class Apply, class Solve, class BApply32>
 void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply32 bapply32, int fp32_iters,
-             cudaStream_t st, Prof& prof, const std::string& tag, double apply_bytes, double apply_flops) {
+             cudaStream_t st, Prof& prof, const std::string& tag, double apply_bytes, double apply_flops,
+             const double* start = nullptr, int start_cols = 0, const long long* d_start_off = nullptr) {
     if (g.P == 0) return;
     eig_init(g, ep.seed, st);
+    eig_load_start(g, start, start_cols, d_start_off, st);
     // FP32 start phase: block inverse iteration Y = K~^{-1} B X with Euclidean
     // CholQR, all in FP32 arithmetic; the FP64 phase below starts from its
     // subspace and alone decides convergence.
@@ -202,6 +204,63 @@ Hierarchy::~Hierarchy() {
     }
 }
 
+Geom make_geom(const msdd_mesh& mesh, const msdd_coeff& coeff) {
+    Geom g{};
+    g.dim = mesh.dim;
+    for (int d = 0; d < 3; ++d) g.n[d] = d < mesh.dim ? mesh.n[d] : 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < mesh.dim) {
+            g.ulo[d] = (mesh.dirichlet_faces >> (2 * d)) & 1 ? 1 : 0;
+            g.uhi[d] = (mesh.dirichlet_faces >> (2 * d + 1)) & 1 ? g.n[d] - 1 : g.n[d];
+        } else {
+            g.ulo[d] = g.uhi[d] = 0;
+        }
+        g.ushape[d] = g.uhi[d] - g.ulo[d] + 1;
+    }
+    g.coeff_kind = coeff.kind;
+    g.ncomp = coeff.kind == 0 ? 1 : (mesh.dim == 2 ? 3 : 6);
+    g.coeff = coeff.data;
+    return g;
+}
+
+std::vector<ProbBox> make_fine_boxes(const Geom& g, const msdd_decomp& dec) {
+    const int dim = g.dim;
+    std::vector<int> s[3], e[3];
+    for (int d = 0; d < 3; ++d) {
+        int P = d < dim ? dec.parts[d] : 1;
+        split_axis(g.n[d], P, s[d], e[d]);
+    }
+    int P0 = dec.parts[0], P1 = dim >= 2 ? dec.parts[1] : 1, P2 = dim == 3 ? dec.parts[2] : 1;
+    std::vector<ProbBox> boxes(P0 * P1 * P2);
+    for (int pz = 0; pz < P2; ++pz)
+        for (int py = 0; py < P1; ++py)
+            for (int px = 0; px < P0; ++px) {
+                int j = px + P0 * (py + P1 * pz);
+                int pi[3] = {px, py, pz};
+                ProbBox& b = boxes[j];
+                for (int d = 0; d < 3; ++d) {
+                    if (d >= dim) {
+                        b.elo[d] = 0; b.ehi[d] = 1;
+                        b.nlo[d] = b.nhi[d] = b.dlo[d] = b.dhi[d] = 0;
+                        continue;
+                    }
+                    int lo = std::max(0, s[d][pi[d]] - dec.overlap);
+                    int hi = std::min(g.n[d], e[d][pi[d]] + dec.overlap);
+                    b.elo[d] = lo;
+                    b.ehi[d] = hi;
+                    b.nlo[d] = std::max(lo, g.ulo[d]);
+                    b.nhi[d] = std::min(hi, g.uhi[d]);
+                    int dlo = lo == 0 ? 0 : lo + 1;
+                    int dhi = hi == g.n[d] ? g.n[d] : hi - 1;
+                    b.dlo[d] = std::max(dlo, g.ulo[d]);
+                    b.dhi[d] = std::min(dhi, g.uhi[d]);
+                }
+                if (host_box_size(b.dlo, b.dhi, dim) <= 0 || host_box_size(b.nlo, b.nhi, dim) <= 0)
+                    throw MsddError(MSDD_ERR_INVALID_ARG, "subdomain " + std::to_string(j) + " has no interior unknowns");
+            }
+    return boxes;
+}
+
 size_t Hierarchy::device_bytes() const {
     size_t b = 0;
     b += fdir.bytes() + fge.K.bytes() + cdir.bytes() + mdir.bytes() + mge.K.bytes();
@@ -228,20 +287,7 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     levels = dec.levels;
     L = levels - 1;
     prof.on = opt.profile != 0;
-    g.dim = mesh.dim;
-    for (int d = 0; d < 3; ++d) g.n[d] = d < mesh.dim ? mesh.n[d] : 1;
-    for (int d = 0; d < 3; ++d) {
-        if (d < mesh.dim) {
-            g.ulo[d] = (mesh.dirichlet_faces >> (2 * d)) & 1 ? 1 : 0;
-            g.uhi[d] = (mesh.dirichlet_faces >> (2 * d + 1)) & 1 ? g.n[d] - 1 : g.n[d];
-        } else {
-            g.ulo[d] = g.uhi[d] = 0;
-        }
-        g.ushape[d] = g.uhi[d] - g.ulo[d] + 1;
-    }
-    g.coeff_kind = coeff.kind;
-    g.ncomp = coeff.kind == 0 ? 1 : (mesh.dim == 2 ? 3 : 6);
-    g.coeff = coeff.data;
+    g = make_geom(mesh, coeff);
     nun = (long long)g.ushape[0] * g.ushape[1] * g.ushape[2];
     upload_reference(g);
 
@@ -284,40 +330,9 @@ void Hierarchy::export_prof() {
 void Hierarchy::build_fine() {
     auto t0 = Clock::now();
     const int dim = g.dim;
-    std::vector<int> s[3], e[3];
-    for (int d = 0; d < 3; ++d) {
-        int P = d < dim ? dec.parts[d] : 1;
-        split_axis(g.n[d], P, s[d], e[d]);
-    }
     int P0 = dec.parts[0], P1 = dim >= 2 ? dec.parts[1] : 1, P2 = dim == 3 ? dec.parts[2] : 1;
     Pf = P0 * P1 * P2;
-    fboxes.resize(Pf);
-    for (int pz = 0; pz < P2; ++pz)
-        for (int py = 0; py < P1; ++py)
-            for (int px = 0; px < P0; ++px) {
-                int j = px + P0 * (py + P1 * pz);
-                int pi[3] = {px, py, pz};
-                ProbBox& b = fboxes[j];
-                for (int d = 0; d < 3; ++d) {
-                    if (d >= dim) {
-                        b.elo[d] = 0; b.ehi[d] = 1;
-                        b.nlo[d] = b.nhi[d] = b.dlo[d] = b.dhi[d] = 0;
-                        continue;
-                    }
-                    int lo = std::max(0, s[d][pi[d]] - dec.overlap);
-                    int hi = std::min(g.n[d], e[d][pi[d]] + dec.overlap);
-                    b.elo[d] = lo;
-                    b.ehi[d] = hi;
-                    b.nlo[d] = std::max(lo, g.ulo[d]);
-                    b.nhi[d] = std::min(hi, g.uhi[d]);
-                    int dlo = lo == 0 ? 0 : lo + 1;
-                    int dhi = hi == g.n[d] ? g.n[d] : hi - 1;
-                    b.dlo[d] = std::max(dlo, g.ulo[d]);
-                    b.dhi[d] = std::min(dhi, g.uhi[d]);
-                }
-                if (host_box_size(b.dlo, b.dhi, dim) <= 0 || host_box_size(b.nlo, b.nhi, dim) <= 0)
-                    throw MsddError(MSDD_ERR_INVALID_ARG, "subdomain " + std::to_string(j) + " has no interior unknowns");
-            }
+    fboxes = make_fine_boxes(g, dec);
     d_fboxes = upload_vec(fboxes, st);
     // combine maps: per axis and node coordinate, the blocks whose Dirichlet range holds it
     cmaps.parts[0] = P0; cmaps.parts[1] = P1; cmaps.parts[2] = P2;
@@ -420,6 +435,13 @@ void Hierarchy::build_fine() {
     ep.maxit = opt.eig_maxit;
     ep.seed = opt.seed;
     build_local_stencil(g, d_fboxes.p, d_count.p, fge.K, fst, st);
+    DevBuf<long long> d_woff;              // row offsets of the caller's start vectors
+    if (opt.warm_start) {
+        std::vector<long long> woff(Pf);
+        long long o = 0;
+        for (int j = 0; j < Pf; ++j) { woff[j] = o; o += nN[j]; }
+        d_woff = upload_vec(woff, st);
+    }
     const ProbBox* bx = d_fboxes.p;
     const LocalStencil* ls = &fst;
     GevpBatch* fg = &fge;
@@ -434,7 +456,8 @@ void Hierarchy::build_fine() {
             [=](int pmax) { tile_solve(fg->K, fg->W.p, fg->ldx, pmax, fg->done.p, stream); },
             [=](const double* X, double* W) { apply_local_b32(*ls, bx, dim, fg->K, X, W, fg->ldx, block_p, stream); },
             opt.precision == 1 ? opt.fp32_start_iters : 0,
-            st, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9));
+            st, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9),
+            opt.warm_start, opt.warm_start ? opt.warm_cols : 0, d_woff.p);
     fm = fge.m.download(st);
     {
         std::vector<int> it = fge.iters.download(st), dn = fge.done.download(st);
@@ -449,6 +472,7 @@ void Hierarchy::build_fine() {
         }
         stats.eig_iters_max[L] = mx;
         stats.eig_iters_min[L] = mn;
+        for (int j = 0; j < Pf; ++j) stats.eig_iters_total[L] += it[j];
         stats.eig_unconverged[L] = unc;
         stats.m_min[L] = mmin;
         stats.m_max[L] = mmax;
@@ -744,18 +768,24 @@ void Hierarchy::build_coarse() {
         std::vector<int> bw(Pm);
         for (int i = 0; i < Pm; ++i) bw[i] = std::max(0, ngen[i] - 1);
         mge.K.layout(ngen, bw, 0, st);
+    }
+    // null-pivot threshold of the generating systems: negative = automatic
+    // (1e-10 in 2D, 1e-6 in 3D, whose generating systems carry more
+    // near-dependent neighbour generators; a 2D level whose eigensolves do
+    // not converge is factored and solved again with 1e-6, below)
+    const bool reg_auto = opt.reg_tol < 0.0;
+    double reg_tol = reg_auto ? (g.dim == 3 ? 1e-6 : 1e-10) : opt.reg_tol;
+    auto factor_K = [&](double rt) {
         tile_from_dense(mge.K, K_m.p, d_aoff.p, d_ngen.p, st);
-        // null-pivot threshold of the generating systems: negative = automatic
-        // (3D generating systems carry more near-dependent neighbour generators)
-        const double reg_tol = opt.reg_tol >= 0.0 ? opt.reg_tol : (g.dim == 3 ? 1e-6 : 1e-10);
-        tile_factor(mge.K, reg_tol, st);
+        tile_factor(mge.K, rt, st);
         stats.null_pivots[1] = sum_nreg(mge.K, st);
         // K^+ explicitly (overwrites K_m): every later solve is a batched GEMM
         dense_inverse(mge.K, K_m.p, aoff, ngen, st);
-    }
+    };
+    factor_K(reg_tol);
     stats.phase_ms[4] += ms_since(t0);
     t0 = Clock::now();
-    const int block_p = opt.block_p > 0 ? opt.block_p : std::min(spec.nev_max + 8, PMAX);
+    int block_p = opt.block_p > 0 ? opt.block_p : std::min(spec.nev_max + 8, PMAX);
     mge.ldx = PMAX;
     mge.knorm = true;
     mge.p.resize(Pm);
@@ -795,34 +825,65 @@ void Hierarchy::build_coarse() {
     const GemmItem* dki = d_kitems.p;
     const double* Kinv = K_m.p;
     double* Wtp = Wt.p;
-    run_eig(mge, ep,
-            [=](const double* X, double* AX, double* BX, const int* skip) {
-                apply_dense_pencil(Ab, dao, dng, dno, mg->K, X, AX, BX, mg->ldx, block_p, skip, PmL, ngen_max, stream);
-            },
-            [=](int) {
-                gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, mg->W.p, 0.0, Wtp, ngen_max, pmax_m, stream);
-                MSDD_CUDA(cudaMemcpyAsync(mg->W.p, Wtp, mg->W.n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-            },
-            [=](const double*, double*) {}, 0,
-            st, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
-    mm = mge.m.download(st);
-    {
-        std::vector<int> it = mge.iters.download(st), dn = mge.done.download(st);
-        int mx = 0, mn = 1 << 30, unc = 0, mmin = 1 << 30, mmax = 0;
-        for (int i = 0; i < Pm; ++i) {
-            mx = std::max(mx, it[i]);
-            mn = std::min(mn, it[i]);
-            unc += dn[i] == 2 ? 1 : 0;
-            stats.eig_at_floor[1] += dn[i] == 3 ? 1 : 0;
-            mmin = std::min(mmin, mm[i]);
-            mmax = std::max(mmax, mm[i]);
+    auto eig_pass = [&]() {
+        stats.eig_at_floor[1] = 0;
+        stats.eig_iters_total[1] = 0;
+        run_eig(mge, ep,
+                [=](const double* X, double* AX, double* BX, const int* skip) {
+                    apply_dense_pencil(Ab, dao, dng, dno, mg->K, X, AX, BX, mg->ldx, block_p, skip, PmL, ngen_max, stream);
+                },
+                [=](int) {
+                    gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, mg->W.p, 0.0, Wtp, ngen_max, pmax_m, stream);
+                    MSDD_CUDA(cudaMemcpyAsync(mg->W.p, Wtp, mg->W.n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+                },
+                [=](const double*, double*) {}, 0,
+                st, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
+        mm = mge.m.download(st);
+        {
+            std::vector<int> it = mge.iters.download(st), dn = mge.done.download(st);
+            int mx = 0, mn = 1 << 30, unc = 0, mmin = 1 << 30, mmax = 0;
+            for (int i = 0; i < Pm; ++i) {
+                mx = std::max(mx, it[i]);
+                mn = std::min(mn, it[i]);
+                unc += dn[i] == 2 ? 1 : 0;
+                stats.eig_at_floor[1] += dn[i] == 3 ? 1 : 0;
+                mmin = std::min(mmin, mm[i]);
+                mmax = std::max(mmax, mm[i]);
+            }
+            stats.eig_iters_max[1] = mx;
+            stats.eig_iters_min[1] = mn;
+            for (int i = 0; i < Pm; ++i) stats.eig_iters_total[1] += it[i];
+            stats.eig_unconverged[1] = unc;
+            stats.m_min[1] = mmin;
+            stats.m_max[1] = mmax;
+            stats.subdomains[1] = Pm;
         }
-        stats.eig_iters_max[1] = mx;
-        stats.eig_iters_min[1] = mn;
-        stats.eig_unconverged[1] = unc;
-        stats.m_min[1] = mmin;
-        stats.m_max[1] = mmax;
-        stats.subdomains[1] = Pm;
+    };
+    eig_pass();
+    // automatic options: problems that did not converge are solved again (all
+    // of the level) with the larger null-pivot threshold and the widest block
+    // (near-dependent generators; clusters of tiny eigenvalues that a block of
+    // nev + 8 separates slowly from the rest of the spectrum)
+    const bool block_auto = opt.block_p == 0;
+    if (stats.eig_unconverged[1] > 0 && ((reg_auto && reg_tol < 1e-6) || (block_auto && block_p < PMAX))) {
+        if (reg_auto && reg_tol < 1e-6) {
+            reg_tol = 1e-6;
+            dense_shift(Abar_m.p, K_m.p, d_aoff.p, d_ngen.p, d_nown.p, opt.sigma, Pm, ngen_max, st);
+            factor_K(reg_tol);
+        }
+        if (block_auto) {
+            block_p = PMAX;
+            pmax_m = 0;
+            for (int i = 0; i < Pm; ++i) {
+                mge.p[i] = std::min(block_p, nown[i]);
+                pmax_m = std::max(pmax_m, mge.p[i]);
+                kitems[i].n = mge.p[i];
+            }
+            d_kitems = upload_vec(kitems, st);
+            dki = d_kitems.p;
+            mge.alloc(st);
+        }
+        eig_pass();
     }
     stats.phase_ms[5] = ms_since(t0);
 

@@ -71,6 +71,12 @@ struct Prof {
     }
 };
 
+// Geometry of the mesh (coefficient pointer from coeff) and the fine
+// subdomain boxes of a decomposition (Section 2.2 box partition with
+// overlap); throws MsddError for a subdomain without interior unknowns.
+Geom make_geom(const msdd_mesh& mesh, const msdd_coeff& coeff);
+std::vector<ProbBox> make_fine_boxes(const Geom& g, const msdd_decomp& dec);
+
 struct Hierarchy {
     Prof prof;
     // ---- problem

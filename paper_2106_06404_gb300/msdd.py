@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("block_p", ctypes.c_int), ("eig_maxit", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("eig_tol", ctypes.c_double), ("reg_tol", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("profile", ctypes.c_int),
-                ("fp32_start_iters", ctypes.c_int)]
+                ("fp32_start_iters", ctypes.c_int), ("warm_start", ctypes.c_void_p), ("warm_cols", ctypes.c_int)]
 
 
 class KernelProf(ctypes.Structure):
@@ -65,7 +65,8 @@ class Stats(ctypes.Structure):
                 ("setup_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
                 ("pcg_iterations", ctypes.c_int), ("pcg_rel_residual", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("nprof", ctypes.c_int), ("prof", KernelProf * 12)]
+                ("nprof", ctypes.c_int), ("prof", KernelProf * 12),
+                ("eig_iters_total", ctypes.c_longlong * MAX_LEVELS)]
 
 
 EXPORTED = [
@@ -73,7 +74,14 @@ EXPORTED = [
     "msdd_apply_preconditioner", "msdd_apply_operator", "msdd_assemble_rhs", "msdd_get_stats",
     "msdd_get_eigenvalues", "msdd_get_eigen_residuals", "msdd_get_fine_basis", "msdd_destroy", "msdd_last_error",
     "msdd_band_factor", "msdd_band_solve", "msdd_band_destroy", "msdd_band_solve_noalloc", "msdd_kernel_launches",
+    "msdd_fine_layout", "msdd_nn_patches", "msdd_nn_workspace_bytes", "msdd_nn_forward", "msdd_nn_loss_grad",
+    "msdd_nn_adam", "msdd_nn_start_vectors", "msdd_nn_targets",
 ]
+
+# learned warm start (include/msdd.h, MSDD_NN_*)
+NN_PATCH, NN_HIDDEN, NN_GRID, NN_NVEC = 24, 48, 13, 12
+NN_IN, NN_OUT = NN_PATCH * NN_PATCH, NN_NVEC * NN_GRID * NN_GRID
+NN_NPARAM = NN_HIDDEN * NN_IN + NN_HIDDEN + NN_HIDDEN * NN_HIDDEN + NN_HIDDEN + NN_OUT * NN_HIDDEN + NN_OUT
 
 _lib = None
 
@@ -112,9 +120,18 @@ def load(path=LIB_PATH):
     lib.msdd_band_destroy.restype = None
     lib.msdd_kernel_launches.argtypes = []
     lib.msdd_kernel_launches.restype = ctypes.c_longlong
+    lib.msdd_fine_layout.argtypes = [P(Mesh), P(Decomp), ip, ctypes.c_int, ip]
+    lib.msdd_nn_patches.argtypes = [P(Mesh), P(Coeff), P(Decomp), vp, vp]
+    lib.msdd_nn_workspace_bytes.argtypes = [ctypes.c_int]
+    lib.msdd_nn_workspace_bytes.restype = ctypes.c_size_t
+    lib.msdd_nn_forward.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
+    lib.msdd_nn_loss_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+    lib.msdd_nn_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, vp]
+    lib.msdd_nn_start_vectors.argtypes = [P(Mesh), P(Decomp), vp, vp, vp]
+    lib.msdd_nn_targets.argtypes = [vp, vp, vp, vp]
     for name in EXPORTED:
         if name in ("msdd_last_error", "msdd_destroy", "msdd_band_destroy", "msdd_num_unknowns",
-                    "msdd_kernel_launches"):
+                    "msdd_kernel_launches", "msdd_nn_workspace_bytes"):
             continue
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -179,7 +196,7 @@ class Hierarchy:
 
     def __init__(self, n, coeff, parts, overlap, levels, group, nev_max, eta, dirichlet_faces=0b1,
                  precision=0, block_p=0, eig_maxit=200, sigma=1e-2, eig_tol=1e-6, reg_tol=-1.0, seed=12345,
-                 allow_eig_unconverged=False, profile=False, fp32_start_iters=None):
+                 allow_eig_unconverged=False, profile=False, fp32_start_iters=None, warm_start=None):
         torch = _torch()
         lib = load()
         self._lib = lib
@@ -205,6 +222,11 @@ class Hierarchy:
         o.profile = 1 if profile else 0
         if fp32_start_iters is not None:
             o.fp32_start_iters = int(fp32_start_iters)
+        if warm_start is not None:
+            # start vectors of the fine subspace iteration: rows as fine_layout(), float64 CUDA
+            warm_start = warm_start.to(device="cuda", dtype=torch.float64).contiguous()
+            o.warm_start = warm_start.data_ptr()
+            o.warm_cols = int(warm_start.shape[1])
         h = ctypes.c_void_p()
         st = lib.msdd_setup(ctypes.byref(self.mesh), ctypes.byref(c), ctypes.byref(d), ctypes.byref(s),
                             ctypes.byref(o), ctypes.byref(h))
@@ -264,6 +286,7 @@ class Hierarchy:
             "n": s.n, "levels": lv, "precision": s.precision,
             "subdomains": list(s.subdomains[:lv]), "level_dim": list(s.level_dim[:lv]),
             "eig_iters_max": list(s.eig_iters_max[:lv]), "eig_iters_min": list(s.eig_iters_min[:lv]),
+            "eig_iters_total": list(s.eig_iters_total[:lv]),
             "eig_unconverged": list(s.eig_unconverged[:lv]), "eig_at_floor": list(s.eig_at_floor[:lv]),
             "null_pivots": list(s.null_pivots[:lv]),
             "m_min": list(s.m_min[:lv]), "m_max": list(s.m_max[:lv]),
@@ -288,6 +311,17 @@ class Hierarchy:
         _check(self._lib.msdd_get_eigen_residuals(self._h, int(level), int(subdomain), out, 32, ctypes.byref(conv)))
         theta, _ = self.eigenvalues(level, subdomain)
         return np.array(out[:len(theta)]), bool(conv.value)
+
+    def nn_targets(self):
+        """Training targets of the warm-start network from this hierarchy's fine
+        eigenvectors: (T float32 (P, NVEC, GRID^2), m int32 (P,)) on the GPU."""
+        torch = _torch()
+        P = self.stats()["subdomains"][-1]
+        T = torch.empty((P, NN_NVEC, NN_GRID * NN_GRID), dtype=torch.float32, device="cuda")
+        m = torch.empty(P, dtype=torch.int32, device="cuda")
+        _check(self._lib.msdd_nn_targets(self._h, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                                         _stream()))
+        return T, m
 
     def fine_basis(self, subdomain, m_max=32):
         buf = np.zeros(self.n * m_max)
@@ -336,3 +370,108 @@ class BandBatch:
             self.close()
         except Exception:
             pass
+
+
+def _decomp(parts, overlap):
+    d = Decomp()
+    for k in range(3):
+        d.parts[k] = int(parts[k]) if k < len(parts) else 1
+        d.group[k] = 1
+    d.overlap = int(overlap)
+    d.levels = 2
+    return d
+
+
+def fine_layout(n, parts, overlap, dirichlet_faces=0b1):
+    """(P, 4) int array: Neumann-box node counts (nx, ny, nz) and row offset of each fine subdomain."""
+    lib = load()
+    mesh, d = make_mesh(n, dirichlet_faces), _decomp(parts, overlap)
+    cnt = ctypes.c_int()
+    _check(lib.msdd_fine_layout(ctypes.byref(mesh), ctypes.byref(d), None, 0, ctypes.byref(cnt)))
+    out = np.zeros(4 * cnt.value, dtype=np.int32)
+    _check(lib.msdd_fine_layout(ctypes.byref(mesh), ctypes.byref(d), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                out.size, ctypes.byref(cnt)))
+    return out.reshape(-1, 4)
+
+
+def nn_patches(n, kappa, parts, overlap, dirichlet_faces=0b1):
+    """Network inputs (P, NN_IN) float32 CUDA of all fine subdomains (2D scalar kappa, CUDA float64)."""
+    torch = _torch()
+    lib = load()
+    mesh, d = make_mesh(n, dirichlet_faces), _decomp(parts, overlap)
+    kappa = kappa.to(device="cuda", dtype=torch.float64).contiguous()
+    c = Coeff()
+    c.kind = 0
+    c.data = kappa.data_ptr()
+    P = fine_layout(n, parts, overlap, dirichlet_faces).shape[0]
+    X = torch.empty((P, NN_IN), dtype=torch.float32, device="cuda")
+    _check(lib.msdd_nn_patches(ctypes.byref(mesh), ctypes.byref(c), ctypes.byref(d), ctypes.c_void_p(X.data_ptr()),
+                               _stream()))
+    return X
+
+
+def nn_start_vectors(n, parts, overlap, Y, dirichlet_faces=0b1):
+    """Grid vectors Y (P, NN_OUT) -> start vectors (rows of fine_layout, NN_NVEC) float64 CUDA."""
+    torch = _torch()
+    lib = load()
+    mesh, d = make_mesh(n, dirichlet_faces), _decomp(parts, overlap)
+    lay = fine_layout(n, parts, overlap, dirichlet_faces)
+    rows = int(lay[-1, 3] + lay[-1, 0] * lay[-1, 1] * lay[-1, 2])
+    Y = Y.to(device="cuda", dtype=torch.float32).contiguous()
+    out = torch.empty((rows, NN_NVEC), dtype=torch.float64, device="cuda")
+    _check(lib.msdd_nn_start_vectors(ctypes.byref(mesh), ctypes.byref(d), ctypes.c_void_p(Y.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), _stream()))
+    return out
+
+
+class WarmStartNet:
+    """Parameters (FP32 master copy) and Adam state of the warm-start network;
+    forward, loss/gradient and Adam steps run in the library's kernels."""
+
+    def __init__(self, params):
+        torch = _torch()
+        self._lib = load()
+        self.params = params.to(device="cuda", dtype=torch.float32).contiguous().clone()
+        assert self.params.numel() == NN_NPARAM
+        self.m1 = torch.zeros_like(self.params)
+        self.m2 = torch.zeros_like(self.params)
+        self.t = 0
+        self._work = None
+
+    def _workspace(self, batch):
+        torch = _torch()
+        nbytes = self._lib.msdd_nn_workspace_bytes(int(batch))
+        if self._work is None or self._work.numel() * 4 < nbytes:
+            self._work = torch.empty((nbytes + 3) // 4, dtype=torch.float32, device="cuda")
+        return self._work
+
+    def forward(self, X):
+        torch = _torch()
+        X = X.to(device="cuda", dtype=torch.float32).contiguous()
+        out = torch.empty((X.shape[0], NN_OUT), dtype=torch.float32, device="cuda")
+        w = self._workspace(X.shape[0])
+        _check(self._lib.msdd_nn_forward(ctypes.c_void_p(self.params.data_ptr()), int(X.shape[0]),
+                                         ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(w.data_ptr()), _stream()))
+        return out
+
+    def loss_grad(self, X, T, m):
+        """Batch loss (float64 0-d CUDA tensor) and gradient (NN_NPARAM float32)."""
+        torch = _torch()
+        X = X.to(device="cuda", dtype=torch.float32).contiguous()
+        T = T.to(device="cuda", dtype=torch.float32).contiguous()
+        m = m.to(device="cuda", dtype=torch.int32).contiguous()
+        loss = torch.empty((), dtype=torch.float64, device="cuda")
+        grad = torch.empty_like(self.params)
+        w = self._workspace(X.shape[0])
+        _check(self._lib.msdd_nn_loss_grad(ctypes.c_void_p(self.params.data_ptr()), int(X.shape[0]),
+                                           ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                           ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                           ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(w.data_ptr()), _stream()))
+        return loss, grad
+
+    def adam_step(self, grad, lr):
+        self.t += 1
+        _check(self._lib.msdd_nn_adam(ctypes.c_void_p(self.params.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                      ctypes.c_void_p(self.m1.data_ptr()), ctypes.c_void_p(self.m2.data_ptr()),
+                                      self.t, ctypes.c_float(lr), _stream()))
