@@ -133,64 +133,102 @@ __global__ void __launch_bounds__(TPB) k_form_y_knorm(double* __restrict__ Y, co
 }
 
 // H = Y^T AY, M = Y^T BY (symmetric, FP64), one CTA per problem.
-__global__ void __launch_bounds__(TPB) k_gram(const double* __restrict__ Y, const double* __restrict__ AY,
-                                              const double* __restrict__ BY, double* __restrict__ H,
-                                              double* __restrict__ M, const int* __restrict__ n_,
-                                              const long long* __restrict__ roff_, const int* __restrict__ p_,
-                                              int ldx, const int* __restrict__ done) {
-    __shared__ double sY[ROWBLK][LD], sA[ROWBLK][LD], sB[ROWBLK][LD];
-    const int i = blockIdx.x;
+// H = Y^T AY, M = Y^T BY as partial sums over `gsplit` row ranges of each
+// problem (grid: problems x splits); each thread owns 2 x 2 blocks (bi <= bj)
+// of the upper block triangle, read as double2 from shared row chunks.
+constexpr int GR_T = 64, GR_ROWS = 32, GR_LD = 34;
+__global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ Y, const double* __restrict__ AY,
+                                                     const double* __restrict__ BY, double* __restrict__ Hp,
+                                                     double* __restrict__ Mp, const int* __restrict__ n_,
+                                                     const long long* __restrict__ roff_, const int* __restrict__ p_,
+                                                     int ldx, const int* __restrict__ done, int gsplit) {
+    __shared__ __align__(16) double sY[GR_ROWS][GR_LD], sA[GR_ROWS][GR_LD], sB[GR_ROWS][GR_LD];
+    const int i = blockIdx.x, sp = blockIdx.y, t = threadIdx.x;
     if (done[i]) return;
-    const int n = n_[i], p = p_[i];
+    const int n = n_[i], p = p_[i], q = p + (p & 1), nb = q / 2;
     const long long roff = roff_[i];
-    const int npair = p * (p + 1) / 2;
-    int pa[3], pb[3];
-    double h[3] = {0, 0, 0}, m[3] = {0, 0, 0};
-    for (int q = 0; q < 3; ++q) {
-        int e = threadIdx.x + q * TPB;
-        pa[q] = -1;
-        if (e < npair) {
-            // e -> (a, b) with a <= b
+    const int rows_per = (n + gsplit - 1) / gsplit;
+    const int r_lo = sp * rows_per, r_hi = min(n, r_lo + rows_per);
+    const int nblk = nb * (nb + 1) / 2;
+    constexpr int KMAX = (PMAX / 2 * (PMAX / 2 + 1) / 2 + GR_T - 1) / GR_T;
+    int ba[KMAX], bb[KMAX];
+    double h[KMAX][4], m[KMAX][4];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int e = t + k * GR_T;
+        ba[k] = -1;
+        bb[k] = 0;
+        if (e < nblk) {
             int a = 0, rem = e;
-            while (rem >= p - a) { rem -= p - a; ++a; }
-            pa[q] = a;
-            pb[q] = a + rem;
+            while (rem >= nb - a) { rem -= nb - a; ++a; }
+            ba[k] = a;
+            bb[k] = a + rem;
         }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { h[k][c] = 0.0; m[k][c] = 0.0; }
     }
-    for (int r0 = 0; r0 < n; r0 += ROWBLK) {
+    for (int r0 = r_lo; r0 < r_hi; r0 += GR_ROWS) {
         __syncthreads();
-        for (int e = threadIdx.x; e < ROWBLK * p; e += TPB) {
-            int rr = e / p, c = e % p;
-            int r = r0 + rr;
-            long long idx = (roff + r) * ldx + c;
-            bool ok = r < n;
+        for (int e = t; e < GR_ROWS * q; e += GR_T) {
+            const int rr = e / q, c = e % q, r = r0 + rr;
+            const bool ok = r < r_hi && c < p;
+            const long long idx = (roff + r) * ldx + c;
             sY[rr][c] = ok ? Y[idx] : 0.0;
             sA[rr][c] = ok ? AY[idx] : 0.0;
             sB[rr][c] = ok ? BY[idx] : 0.0;
         }
         __syncthreads();
-        for (int q = 0; q < 3; ++q) {
-            if (pa[q] < 0) continue;
-            int a = pa[q], b = pb[q];
-            double hs = 0.0, ms = 0.0;
-#pragma unroll 8
-            for (int rr = 0; rr < ROWBLK; ++rr) {
-                hs += sY[rr][a] * sA[rr][b];
-                ms += sY[rr][a] * sB[rr][b];
+        const int nr = min(GR_ROWS, r_hi - r0);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (ba[k] < 0) continue;
+            const int a0 = 2 * ba[k], b0 = 2 * bb[k];
+            for (int rr = 0; rr < nr; ++rr) {
+                const double2 y = *reinterpret_cast<const double2*>(&sY[rr][a0]);
+                const double2 av = *reinterpret_cast<const double2*>(&sA[rr][b0]);
+                const double2 bv = *reinterpret_cast<const double2*>(&sB[rr][b0]);
+                h[k][0] += y.x * av.x; h[k][1] += y.x * av.y; h[k][2] += y.y * av.x; h[k][3] += y.y * av.y;
+                m[k][0] += y.x * bv.x; m[k][1] += y.x * bv.y; m[k][2] += y.y * bv.x; m[k][3] += y.y * bv.y;
             }
-            h[q] += hs;
-            m[q] += ms;
         }
     }
-    for (int q = 0; q < 3; ++q) {
-        if (pa[q] < 0) continue;
-        int a = pa[q], b = pb[q];
-        // symmetrise: average the two triangles' contributions is not needed, the
-        // products Y^T AY are symmetric in exact arithmetic; keep (a,b) from a<=b.
-        H[(long long)i * PMAX * PMAX + a * PMAX + b] = h[q];
-        H[(long long)i * PMAX * PMAX + b * PMAX + a] = h[q];
-        M[(long long)i * PMAX * PMAX + a * PMAX + b] = m[q];
-        M[(long long)i * PMAX * PMAX + b * PMAX + a] = m[q];
+    double* Hs = Hp + ((long long)i * gsplit + sp) * PMAX * PMAX;
+    double* Ms = Mp + ((long long)i * gsplit + sp) * PMAX * PMAX;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (ba[k] < 0) continue;
+        const int a0 = 2 * ba[k], b0 = 2 * bb[k];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int a = a0 + (c >> 1), b = b0 + (c & 1);
+            if (a >= p || b >= p) continue;
+            Hs[a * PMAX + b] = h[k][c];
+            Ms[a * PMAX + b] = m[k][c];
+            if (a0 != b0) {                                 // mirror off-diagonal blocks
+                Hs[b * PMAX + a] = h[k][c];
+                Ms[b * PMAX + a] = m[k][c];
+            }
+        }
+    }
+}
+
+// H, M = sums of the split partials (fixed order)
+__global__ void k_gram_sum(const double* __restrict__ Hp, const double* __restrict__ Mp, double* __restrict__ H,
+                           double* __restrict__ M, const int* __restrict__ p_, const int* __restrict__ done,
+                           int gsplit) {
+    const int i = blockIdx.x;
+    if (done[i]) return;
+    const int p = p_[i];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int a = e / p, b = e % p;
+        double hs = 0.0, ms = 0.0;
+        for (int s = 0; s < gsplit; ++s) {
+            const long long o = ((long long)i * gsplit + s) * PMAX * PMAX + a * PMAX + b;
+            hs += Hp[o];
+            ms += Mp[o];
+        }
+        H[(long long)i * PMAX * PMAX + a * PMAX + b] = hs;
+        M[(long long)i * PMAX * PMAX + a * PMAX + b] = ms;
     }
 }
 
@@ -921,6 +959,11 @@ void GevpBatch::alloc(cudaStream_t s) {
     for (DevBuf<double>* b : {&X, &AX, &BX, &Y, &AY, &BY, &W}) { b->alloc(rows * ldx); b->zero(s); }
     H.alloc((size_t)P * PMAX * PMAX);
     M.alloc((size_t)P * PMAX * PMAX);
+    // row splits: about 1024 CTAs in total, at least 64 rows per split
+    gsplit = (int)std::max<long long>(1, std::min<long long>(ceil_div(1024, std::max(P, 1)),
+                                                                 ceil_div((long long)K.max_K * NB, 64)));
+    Hp.alloc((size_t)P * gsplit * PMAX * PMAX);
+    Mp.alloc((size_t)P * gsplit * PMAX * PMAX);
     C.alloc((size_t)P * PMAX * PMAX);
     theta.alloc((size_t)P * PMAX);
     res.alloc((size_t)P * PMAX);
@@ -989,7 +1032,10 @@ void eig_cholqr32(GevpBatch& g, cudaStream_t s) {
 }
 
 void eig_gram(GevpBatch& g, cudaStream_t s) {
-    k_gram<<<g.P, TPB, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.H.p, g.M.p, g.K.d_n.p, g.K.d_roff.p, g.d_p.p, g.ldx, g.done.p);
+    k_gram_split<<<dim3(g.P, g.gsplit), GR_T, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.Hp.p, g.Mp.p, g.K.d_n.p, g.K.d_roff.p,
+                                                     g.d_p.p, g.ldx, g.done.p, g.gsplit);
+    MSDD_LAUNCH_CHECK();
+    k_gram_sum<<<g.P, 256, 0, s>>>(g.Hp.p, g.Mp.p, g.H.p, g.M.p, g.d_p.p, g.done.p, g.gsplit);
     MSDD_LAUNCH_CHECK();
 }
 

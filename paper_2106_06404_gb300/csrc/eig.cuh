@@ -28,6 +28,8 @@ struct GevpBatch {
     TileBatch K;                      // factor of Abar + sigma B (rows = problem size)
     DevBuf<double> X, AX, BX, Y, AY, BY, W;        // (total_rows x ldx)
     DevBuf<double> H, M, C, theta, res;            // per problem PMAX^2 / PMAX
+    int gsplit = 1;                                // row splits of the Gram products
+    DevBuf<double> Hp, Mp;                         // per (problem, split) PMAX^2 partial Grams
     DevBuf<double> partial;                        // per (problem, row block) sums
     DevBuf<int> done, m, rank, iters;   // done: 0 running, 1 converged, 2 maxit, 3 at noise floor
     DevBuf<double> best;                 // best worst-selected residual so far

