@@ -37,30 +37,46 @@ long long& kernel_launch_counter();
         MSDD_CUDA(cudaGetLastError());      \
     } while (0)
 
-// Owning device buffer (cudaMalloc / cudaFree), move-only.
+// Device buffer (cudaMalloc / cudaFree), move-only; borrow() makes a
+// non-owning view of another buffer's memory (never freed by the view).
 template <typename T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
+    bool owned = true;
     DevBuf() = default;
     explicit DevBuf(size_t count) { alloc(count); }
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), owned(o.owned) { o.p = nullptr; o.n = 0; o.owned = true; }
     DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; owned = o.owned;
+            o.p = nullptr; o.n = 0; o.owned = true;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
+    static DevBuf borrow(T* q, size_t count) {
+        DevBuf v;
+        v.p = q;
+        v.n = count;
+        v.owned = false;
+        return v;
+    }
+    // view of elements [off, off + count) of this buffer
+    DevBuf view(size_t off, size_t count) const { return borrow(p ? p + off : nullptr, count); }
     void alloc(size_t count) {
         release();
         n = count;
         if (count) MSDD_CUDA(cudaMalloc(&p, count * sizeof(T)));
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p && owned) cudaFree(p);
         p = nullptr;
         n = 0;
+        owned = true;
     }
     void upload(const std::vector<T>& h, cudaStream_t s) {
         alloc(h.size());

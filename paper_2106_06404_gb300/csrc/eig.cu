@@ -975,7 +975,34 @@ void GevpBatch::alloc(cudaStream_t s) {
     m.alloc(P);
     rank.alloc(P);
     iters.alloc(P);
-    n_active.alloc(1);
+    n_active.alloc(2);
+}
+
+GevpBatch GevpBatch::slice(int p0, int np, int group) const {
+    GevpBatch v;
+    v.P = np;
+    v.ldx = ldx;
+    v.p.assign(p.begin() + p0, p.begin() + p0 + np);
+    v.d_p = d_p.view(p0, np);
+    v.K = K.slice(p0, np);
+    for (auto pr : {std::make_pair(&v.X, &X), std::make_pair(&v.AX, &AX), std::make_pair(&v.BX, &BX),
+                    std::make_pair(&v.Y, &Y), std::make_pair(&v.AY, &AY), std::make_pair(&v.BY, &BY),
+                    std::make_pair(&v.W, &W)})
+        *pr.first = pr.second->view(0, pr.second->n);
+    const size_t q2 = (size_t)PMAX * PMAX;
+    v.H = H.view(p0 * q2, np * q2); v.M = M.view(p0 * q2, np * q2); v.C = C.view(p0 * q2, np * q2);
+    v.theta = theta.view((size_t)p0 * PMAX, (size_t)np * PMAX);
+    v.res = res.view((size_t)p0 * PMAX, (size_t)np * PMAX);
+    v.gsplit = gsplit;
+    v.Hp = Hp.view(p0 * gsplit * q2, np * gsplit * q2);
+    v.Mp = Mp.view(p0 * gsplit * q2, np * gsplit * q2);
+    v.nblk_max = nblk_max;
+    v.partial = partial.view((size_t)p0 * nblk_max * 2 * PMAX, (size_t)np * nblk_max * 2 * PMAX);
+    v.done = done.view(p0, np); v.m = m.view(p0, np); v.rank = rank.view(p0, np); v.iters = iters.view(p0, np);
+    v.best = best.view(p0, np); v.best_it = best_it.view(p0, np);
+    v.n_active = n_active.view(group, 1);
+    v.knorm = knorm;
+    return v;
 }
 
 void eig_load_start(GevpBatch& g, const double* Wst, int wc, const long long* d_woff, cudaStream_t s) {

@@ -38,6 +38,10 @@ struct GevpBatch {
     int nblk_max = 0;
     bool knorm = false;           // residual measured in the K^+-norm (coarse levels)
     void alloc(cudaStream_t s);
+    // Non-owning view of problems [p0, p0 + np) with its own active counter
+    // (group < 2): per-problem arrays offset, block vectors shared (they are
+    // addressed by absolute row offsets).
+    GevpBatch slice(int p0, int np, int group) const;
 };
 
 struct EigParams {

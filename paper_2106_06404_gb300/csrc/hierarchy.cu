@@ -94,91 +94,166 @@ void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long
     MSDD_CUDA(cudaStreamSynchronize(st));
 }
 
-// Subspace iteration driver; `apply(X, AX, BX, skip)` applies Abar and B.
-// `tag` names the kernel families for profiling; `apply_bytes`/`apply_flops`
-// are the algorithmic amounts of one operator application per problem.
+// Subspace iteration driver.  apply(v, p0, X, AX, BX, skip, s) applies Abar
+// and B to the problems of batch view v (first problem p0 of the whole
+// batch), solve(v, ncols, s) applies K^{-1} to v.W, bapply32(v, p0, X, W, s)
+// is the FP32 B apply.  `tag` names the kernel families for profiling;
+// `apply_bytes`/`apply_flops` are the algorithmic amounts of one operator
+// application per problem.
+//
+// With groups = 2 the problems are split into two halves on two streams
+// whose iterations are offset by about one band solve: the latency-bound
+// kernels of one half (band solve, Rayleigh-Ritz) then run beside the
+// FP64-bound kernels of the other (operators, Gram products, updates).
+// Convergence is read back every `batch` iterations; a half that converged
+// inside a batch only launches kernels that skip its (done) problems.
 template <class Apply, class Solve, class BApply32>
 void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply32 bapply32, int fp32_iters,
-             cudaStream_t st, Prof& prof, const std::string& tag, double apply_bytes, double apply_flops,
-             const double* start = nullptr, int start_cols = 0, const long long* d_start_off = nullptr) {
+             cudaStream_t st, cudaStream_t st_b, Prof& prof, const std::string& tag, double apply_bytes,
+             double apply_flops, const double* start = nullptr, int start_cols = 0,
+             const long long* d_start_off = nullptr, int groups = 1) {
     if (g.P == 0) return;
     eig_init(g, ep.seed, st);
     eig_load_start(g, start, start_cols, d_start_off, st);
+    const int G = (groups == 2 && g.P >= 2 && st_b) ? 2 : 1;
+    const int batch = G == 2 ? 4 : 1;
+    std::vector<GevpBatch> gv;
+    std::vector<int> gp0;
+    std::vector<cudaStream_t> gs;
+    if (G == 1) {
+        gv.push_back(g.slice(0, g.P, 0));
+        gp0 = {0};
+        gs = {st};
+    } else {
+        const int h = g.P / 2;
+        gv.push_back(g.slice(0, h, 0));
+        gv.push_back(g.slice(h, g.P - h, 1));
+        gp0 = {0, h};
+        gs = {st, st_b};
+    }
+    cudaEvent_t ev_start, ev_off, ev_end;
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_off, cudaEventDisableTiming));
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_end, cudaEventDisableTiming));
+    MSDD_CUDA(cudaEventRecord(ev_start, st));
+    for (int k = 1; k < G; ++k) MSDD_CUDA(cudaStreamWaitEvent(gs[k], ev_start, 0));
+    int* h_act = nullptr;
+    MSDD_CUDA(cudaHostAlloc(&h_act, 2 * sizeof(int), cudaHostAllocDefault));
+    struct Amounts { int pm = 0; double sb0 = 0, sf0 = 0, solve_b = 0, solve_f = 0, vec_n = 0; };
+    std::vector<Amounts> am(G);
+    for (int k = 0; k < G; ++k) {
+        const GevpBatch& v = gv[k];
+        const double fsz = v.K.prec ? 4.0 : 8.0;
+        for (int i = 0; i < v.P; ++i) {
+            const double n = v.K.n[i], b = v.K.b[i], p = v.p[i];
+            am[k].pm = std::max(am[k].pm, v.p[i]);
+            am[k].sb0 += 2.0 * n * (b + 1) * fsz + 4.0 * n * p * 8.0;
+            am[k].sf0 += 4.0 * n * b * p;
+            am[k].vec_n += n * p;
+        }
+        am[k].solve_b = am[k].sb0;
+        am[k].solve_f = am[k].sf0;
+    }
     // FP32 start phase: block inverse iteration Y = K~^{-1} B X with Euclidean
     // CholQR, all in FP32 arithmetic; the FP64 phase below starts from its
     // subspace and alone decides convergence.
-    int pm0 = 0;
-    for (int v : g.p) pm0 = std::max(pm0, v);
-    double sb0 = 0, sf0 = 0;
-    for (int i = 0; i < g.P; ++i) {
-        double n = g.K.n[i], b = g.K.b[i], p = g.p[i];
-        sb0 += 2.0 * n * (b + 1) * (g.K.prec ? 4.0 : 8.0) + 4.0 * n * p * 8.0;
-        sf0 += 4.0 * n * b * p;
+    for (int it = 0; it < fp32_iters; ++it)
+        for (int k = 0; k < G; ++k) {
+            GevpBatch& v = gv[k];
+            prof.begin(tag + "_fp32_start_other", gs[k]);
+            bapply32(v, gp0[k], v.X.p, v.W.p, gs[k]);
+            prof.end(gs[k], 0.0, 0.0);
+            prof.begin(tag + "_solve", gs[k]);
+            solve(v, am[k].pm, gs[k]);
+            prof.end(gs[k], am[k].sb0, am[k].sf0);
+            if (G == 2 && k == 0 && it == 0) {
+                MSDD_CUDA(cudaEventRecord(ev_off, gs[0]));        // the second half starts one solve later
+                MSDD_CUDA(cudaStreamWaitEvent(gs[1], ev_off, 0));
+            }
+            prof.begin(tag + "_fp32_start_other", gs[k]);
+            eig_cholqr32(v, gs[k]);
+            prof.end(gs[k], 0.0, 0.0);
+        }
+    std::vector<int> active(G), iter(G, 0);
+    for (int k = 0; k < G; ++k) {
+        active[k] = gv[k].P;
+        apply(gv[k], gp0[k], gv[k].X.p, gv[k].AX.p, gv[k].BX.p, (const int*)nullptr, gs[k]);
     }
-    for (int it = 0; it < fp32_iters; ++it) {
-        prof.begin(tag + "_fp32_start_other", st);
-        bapply32(g.X.p, g.W.p);
-        prof.end(st, 0.0, 0.0);
-        prof.begin(tag + "_solve", st);
-        solve(pm0);
-        prof.end(st, sb0, sf0);
-        prof.begin(tag + "_fp32_start_other", st);
-        eig_cholqr32(g, st);
-        prof.end(st, 0.0, 0.0);
-    }
-    int pmax = 0;
-    for (int v : g.p) pmax = std::max(pmax, v);
-    // algorithmic amounts per problem: band solve (two sweeps) and the
-    // block-vector kernels
-    const double fsz = g.K.prec ? 4.0 : 8.0;
-    double solve_b = 0, solve_f = 0, vec_n = 0;
-    for (int i = 0; i < g.P; ++i) {
-        double n = g.K.n[i], b = g.K.b[i], p = g.p[i];
-        solve_b += 2.0 * n * (b + 1) * fsz + 4.0 * n * p * 8.0;
-        solve_f += 4.0 * n * b * p;
-        vec_n += n * p;
-    }
-    const double pavg = (double)pmax;
-    apply(g.X.p, g.AX.p, g.BX.p, (const int*)nullptr);
-    int active = g.P;
-    for (int it = 0; it < ep.maxit; ++it) {
-        bool first = it == 0;
-        const double fr = (double)active / g.P;
-        eig_form_rhs(g, ep.sigma, first, st);
-        prof.begin(tag + "_solve", st);
-        solve(pmax);
-        prof.end(st, solve_b * fr, solve_f * fr);
-        if (g.knorm && !first) {
+    // one iteration of half k on its stream; returns whether it ran a convergence test
+    auto iteration = [&](int k, int it, bool offset) -> bool {
+        GevpBatch& v = gv[k];
+        cudaStream_t s = gs[k];
+        const bool first = it == 0;
+        const double fr = (double)active[k] / v.P;
+        eig_form_rhs(v, ep.sigma, first, s);
+        prof.begin(tag + "_solve", s);
+        solve(v, am[k].pm, s);
+        prof.end(s, am[k].solve_b * fr, am[k].solve_f * fr);
+        if (offset) {
+            MSDD_CUDA(cudaEventRecord(ev_off, s));
+            MSDD_CUDA(cudaStreamWaitEvent(gs[1], ev_off, 0));
+        }
+        if (v.knorm && !first) {
             // test the current Ritz pairs before updating them
-            eig_form_y_knorm(g, ep.sigma, st);
-            MSDD_CUDA(cudaMemsetAsync(g.n_active.p, 0, sizeof(int), st));
-            eig_check_knorm(g, ep, it, st);
+            eig_form_y_knorm(v, ep.sigma, s);
+            MSDD_CUDA(cudaMemsetAsync(v.n_active.p, 0, sizeof(int), s));
+            eig_check_knorm(v, ep, it, s);
         } else {
-            eig_form_y(g, ep.sigma, first, st);
+            eig_form_y(v, ep.sigma, first, s);
         }
-        prof.begin(tag + "_apply", st);
-        apply(g.Y.p, g.AY.p, g.BY.p, (const int*)g.done.p);
-        prof.end(st, apply_bytes * active, apply_flops * active);
-        prof.begin(tag + "_gram", st);
-        eig_gram(g, st);
-        prof.end(st, 3.0 * vec_n * 8.0 * fr, 2.0 * vec_n * (pavg + 1) * fr);
-        prof.begin(tag + "_rayleigh_ritz", st);
-        eig_rayleigh_ritz(g, st);
-        prof.end(st, 0.0, 0.0);
-        prof.begin(tag + "_update", st);
-        eig_update(g, st);
-        prof.end(st, 6.0 * vec_n * 8.0 * fr, 6.0 * vec_n * pavg * fr);
-        if (g.knorm) {
-            if (first) continue;
+        prof.begin(tag + "_apply", s);
+        apply(v, gp0[k], v.Y.p, v.AY.p, v.BY.p, (const int*)v.done.p, s);
+        prof.end(s, apply_bytes * active[k], apply_flops * active[k]);
+        prof.begin(tag + "_gram", s);
+        eig_gram(v, s);
+        prof.end(s, 3.0 * am[k].vec_n * 8.0 * fr, 2.0 * am[k].vec_n * (am[k].pm + 1) * fr);
+        prof.begin(tag + "_rayleigh_ritz", s);
+        eig_rayleigh_ritz(v, s);
+        prof.end(s, 0.0, 0.0);
+        prof.begin(tag + "_update", s);
+        eig_update(v, s);
+        prof.end(s, 6.0 * am[k].vec_n * 8.0 * fr, 6.0 * am[k].vec_n * am[k].pm * fr);
+        if (v.knorm) {
+            if (first) return false;
         } else {
-            MSDD_CUDA(cudaMemsetAsync(g.n_active.p, 0, sizeof(int), st));
-            eig_check(g, ep, it, st);
+            MSDD_CUDA(cudaMemsetAsync(v.n_active.p, 0, sizeof(int), s));
+            eig_check(v, ep, it, s);
         }
-        MSDD_CUDA(cudaMemcpyAsync(&active, g.n_active.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        MSDD_CUDA(cudaStreamSynchronize(st));
-        if (active == 0) break;
+        MSDD_CUDA(cudaMemcpyAsync(&h_act[k], v.n_active.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        return true;
+    };
+    for (;;) {
+        bool any = false;
+        std::vector<bool> checked(G, false);
+        for (int b = 0; b < batch; ++b)
+            for (int k = 0; k < G; ++k) {
+                if (active[k] == 0 || iter[k] >= ep.maxit) continue;
+                const bool offset = G == 2 && k == 0 && b == 0 && active[1] > 0 && iter[1] < ep.maxit;
+                if (iteration(k, iter[k], offset)) checked[k] = true;
+                ++iter[k];
+                any = true;
+            }
+        if (!any) break;
+        for (int k = 0; k < G; ++k) {
+            MSDD_CUDA(cudaStreamSynchronize(gs[k]));
+            if (checked[k]) active[k] = h_act[k];
+        }
+        bool more = false;
+        for (int k = 0; k < G; ++k) more = more || (active[k] > 0 && iter[k] < ep.maxit);
+        if (!more) break;
     }
-    if (g.knorm && active > 0) {
+    for (int k = 1; k < G; ++k) {
+        MSDD_CUDA(cudaEventRecord(ev_end, gs[k]));
+        MSDD_CUDA(cudaStreamWaitEvent(st, ev_end, 0));
+    }
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    cudaFreeHost(h_act);
+    cudaEventDestroy(ev_start);
+    cudaEventDestroy(ev_off);
+    cudaEventDestroy(ev_end);
+    int left = 0;
+    for (int k = 0; k < G; ++k) left += active[k];
+    if (g.knorm && left > 0) {
         // eig_maxit reached: the last updated pairs are kept and marked unconverged
         std::vector<int> dn = g.done.download(st);
         for (int& v : dn)
@@ -450,14 +525,16 @@ void Hierarchy::build_fine() {
     for (int j = 0; j < Pf; ++j) nav += nN[j];
     nav /= Pf;
     run_eig(fge, ep,
-            [=](const double* X, double* AX, double* BX, const int* skip) {
-                apply_local(*ls, bx, dim, fg->K, X, AX, BX, fg->ldx, block_p, skip, stream);
+            [=](GevpBatch& v, int p0, const double* X, double* AX, double* BX, const int* skip, cudaStream_t s) {
+                apply_local(*ls, bx + p0, dim, v.K, X, AX, BX, v.ldx, block_p, skip, s);
             },
-            [=](int pmax) { tile_solve(fg->K, fg->W.p, fg->ldx, pmax, fg->done.p, stream); },
-            [=](const double* X, double* W) { apply_local_b32(*ls, bx, dim, fg->K, X, W, fg->ldx, block_p, stream); },
+            [=](GevpBatch& v, int pmax, cudaStream_t s) { tile_solve(v.K, v.W.p, v.ldx, pmax, v.done.p, s); },
+            [=](GevpBatch& v, int p0, const double* X, double* W, cudaStream_t s) {
+                apply_local_b32(*ls, bx + p0, dim, v.K, X, W, v.ldx, block_p, s);
+            },
             opt.precision == 1 ? opt.fp32_start_iters : 0,
-            st, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9),
-            opt.warm_start, opt.warm_start ? opt.warm_cols : 0, d_woff.p);
+            st, st2, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9),
+            opt.warm_start, opt.warm_start ? opt.warm_cols : 0, d_woff.p, Pf >= 64 ? 2 : 1);
     fm = fge.m.download(st);
     {
         std::vector<int> it = fge.iters.download(st), dn = fge.done.download(st);
@@ -829,15 +906,16 @@ void Hierarchy::build_coarse() {
         stats.eig_at_floor[1] = 0;
         stats.eig_iters_total[1] = 0;
         run_eig(mge, ep,
-                [=](const double* X, double* AX, double* BX, const int* skip) {
-                    apply_dense_pencil(Ab, dao, dng, dno, mg->K, X, AX, BX, mg->ldx, block_p, skip, PmL, ngen_max, stream);
+                [=](GevpBatch& v, int p0, const double* X, double* AX, double* BX, const int* skip, cudaStream_t s) {
+                    apply_dense_pencil(Ab, dao + p0, dng + p0, dno + p0, v.K, X, AX, BX, v.ldx, block_p, skip, v.P,
+                                       ngen_max, s);
                 },
-                [=](int) {
-                    gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, mg->W.p, 0.0, Wtp, ngen_max, pmax_m, stream);
-                    MSDD_CUDA(cudaMemcpyAsync(mg->W.p, Wtp, mg->W.n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+                [=](GevpBatch& v, int, cudaStream_t s) {
+                    gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, v.W.p, 0.0, Wtp, ngen_max, pmax_m, s);
+                    MSDD_CUDA(cudaMemcpyAsync(v.W.p, Wtp, v.W.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
                 },
-                [=](const double*, double*) {}, 0,
-                st, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
+                [=](GevpBatch&, int, const double*, double*, cudaStream_t) {}, 0,
+                st, nullptr, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
         mm = mge.m.download(st);
         {
             std::vector<int> it = mge.iters.download(st), dn = mge.done.download(st);

@@ -3,7 +3,9 @@
 #include "tile_ldlt.cuh"
 
 #include <cuda.h>
+#include <cstring>
 #include <mutex>
+#include <type_traits>
 
 namespace msdd {
 
@@ -1054,6 +1056,27 @@ __global__ void k_tile_from_dense(T* __restrict__ tiles, const int* __restrict__
 }
 
 }  // namespace
+
+TileBatch TileBatch::slice(int p0, int np) const {
+    TileBatch v;
+    v.P = np;
+    v.prec = prec;
+    auto sub = [&](const auto& vec) { return std::decay_t<decltype(vec)>(vec.begin() + p0, vec.begin() + p0 + np); };
+    v.n = sub(n); v.kb = sub(kb); v.K = sub(K); v.b = sub(b); v.toff = sub(toff); v.roff = sub(roff);
+    v.total_tile_elems = total_tile_elems;
+    v.total_rows = total_rows;
+    v.max_K = 0;
+    for (int k : v.K) v.max_K = std::max(v.max_K, k);
+    v.d_n = d_n.view(p0, np); v.d_kb = d_kb.view(p0, np); v.d_K = d_K.view(p0, np); v.d_b = d_b.view(p0, np);
+    v.d_status = d_status.view(p0, np); v.d_nreg = d_nreg.view(p0, np);
+    v.d_toff = d_toff.view(p0, np); v.d_roff = d_roff.view(p0, np);
+    v.tiles_d = tiles_d.view(0, tiles_d.n); v.dinv_d = dinv_d.view(0, dinv_d.n);
+    v.tiles_f = tiles_f.view(0, tiles_f.n); v.dinv_f = dinv_f.view(0, dinv_f.n);
+    tile_tensor_map(*this);                     // build the shared descriptor once, then copy it
+    memcpy(v.tmap_tiles, tmap_tiles, sizeof(tmap_tiles));
+    v.tmap_base = tmap_base;
+    return v;
+}
 
 void TileBatch::layout(const std::vector<int>& n_, const std::vector<int>& b_, int precision, cudaStream_t s) {
     P = (int)n_.size();

@@ -36,6 +36,8 @@ struct TileBatch {
 
     // Layout from per-problem sizes and half-bandwidths.
     void layout(const std::vector<int>& n_, const std::vector<int>& b_, int precision, cudaStream_t s);
+    // Non-owning view of problems [p0, p0 + np) (same tiles, rows and offsets).
+    TileBatch slice(int p0, int np) const;
     void* tiles() const { return prec ? (void*)tiles_f.p : (void*)tiles_d.p; }
     size_t bytes() const {
         return (size_t)total_tile_elems * (prec ? 4 : 8) + (size_t)total_rows * (prec ? 4 : 8);
