@@ -731,8 +731,9 @@ __global__ void __launch_bounds__(8 * CG) k_tile_solve_band(
 }
 
 // ---- the FP32 band solve with TMA tile loads
-// Same steps and thread mapping as k_tile_solve_band<float, 1, 16> (128
-// threads, 16 right-hand sides per CTA); the tiles of a step and D^{-1} are
+// Same steps as k_tile_solve_band<float, 1, 16> (16 right-hand sides per
+// CTA; NT = 128, 256 or 512 threads hold 4, 2 or 1 rows of a tile row each,
+// so more threads shorten each step's dependent chain); the tiles of a step and D^{-1} are
 // fetched by one thread with cp.async.bulk(.tensor) into 128-byte-swizzled
 // shared tiles (16-byte chunk g of row r at g ^ (r & 7)), completion tracked
 // by one mbarrier per stage.  Every mbarrier wait is bounded: on timeout the
@@ -781,19 +782,36 @@ __device__ __forceinline__ void tma_load4(const float* tile, int r, int g, float
     const float4 x = *reinterpret_cast<const float4*>(tile + r * NB + ((g ^ (r & 7)) << 2));
     v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
 }
+// N = 1, 2 or 4 consecutive entries of row r from column c (c a multiple of N)
+template <int N>
+__device__ __forceinline__ void tma_loadn(const float* tile, int r, int c, float (&v)[N]) {
+    const float* q = tile + r * NB + (((c >> 2) ^ (r & 7)) << 2) + (c & 3);
+    if constexpr (N == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(q);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if constexpr (N == 2) {
+        const float2 x = *reinterpret_cast<const float2*>(q);
+        v[0] = x.x; v[1] = x.y;
+    } else {
+        v[0] = *q;
+    }
+}
 
-constexpr int BT_NT = 128, BT_CG = 16, BT_ZLD = 16, BT_NST = 3;
+constexpr int BT_NT = 256, BT_CG = 16, BT_ZLD = 16, BT_NST = 3;
 constexpr size_t band_tma_smem_bytes() {
     return 1024 + sizeof(float) * ((size_t)BT_NST * BAND_SLOTS * NB2) + sizeof(double) * (size_t)BT_NST * NB * BT_ZLD +
            sizeof(float) * ((size_t)BT_NST * NB + (size_t)(BAND_SLOTS + 1) * NB * BT_ZLD) + 8 * BT_NST;
 }
 
-__global__ void __launch_bounds__(BT_NT) k_tile_solve_band_tma(
+// NT threads: a row group of BT_CG threads holds the BT_CG columns of RPT rows.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_tile_solve_band_tma(
     const __grid_constant__ CUtensorMap tmt, const float* __restrict__ dinv, const int* __restrict__ kb_,
     const int* __restrict__ K_, const long long* __restrict__ toff_, const long long* __restrict__ roff_,
     double* __restrict__ Xall, int ldx, int ncols_all, const int* __restrict__ skip, const int* __restrict__ gdone)
 {
-    constexpr int NST = BT_NST, ZLD = BT_ZLD, NT = BT_NT;
+    constexpr int NST = BT_NST, ZLD = BT_ZLD, RPT = NB * BT_CG / NT;
+    static_assert(RPT == 1 || RPT == 2 || RPT == 4, "4, 2 or 1 rows per thread");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     float* St = reinterpret_cast<float*>(base);                               // [NST][SLOTS][32*32]
@@ -813,8 +831,9 @@ __global__ void __launch_bounds__(BT_NT) k_tile_solve_band_tma(
     const long long toff = toff_[i], roff = roff_[i];
     const int t = threadIdx.x;
     const int rg = t / BT_CG, c0 = t % BT_CG, warp = t >> 5;
-    const int r0 = 4 * rg;
-    const int wrow_lo = 8 * warp, wgrp_hi = 2 * warp + 1;   // rows 8 warp .. 8 warp + 7
+    const int r0 = RPT * rg;
+    constexpr int WROWS = RPT * 32 / BT_CG;                  // rows of one warp
+    const int wrow_lo = WROWS * warp, wgrp_hi = (WROWS * warp + WROWS - 1) >> 2;
     if (t == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
@@ -869,37 +888,39 @@ __global__ void __launch_bounds__(BT_NT) k_tile_solve_band_tma(
         cp_async_wait_n<0>();
         __syncthreads();
     };
-    auto finish = [&](float (&acc)[4], int R, const float* Tt, bool fwd) {
+    auto finish = [&](float (&acc)[RPT], int R, const float* Tt, bool fwd) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) Acc[(r0 + a) * ZLD + c0] = acc[a];
+        for (int a = 0; a < RPT; ++a) Acc[(r0 + a) * ZLD + c0] = acc[a];
         __syncthreads();
-        float out[4] = {0.f, 0.f, 0.f, 0.f};
+        float out[RPT];
+#pragma unroll
+        for (int a = 0; a < RPT; ++a) out[a] = 0.f;
         if (fwd) {
 #pragma unroll 4
             for (int g = 0; g <= wgrp_hi; ++g) {
-                float l[4][4];
+                float l[RPT][4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) tma_load4(Tt, r0 + a, g, l[a]);
+                for (int a = 0; a < RPT; ++a) tma_load4(Tt, r0 + a, g, l[a]);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const float zv = Acc[(4 * g + kk) * ZLD + c0];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) out[a] += l[a][kk] * zv;
+                    for (int a = 0; a < RPT; ++a) out[a] += l[a][kk] * zv;
                 }
             }
         } else {
 #pragma unroll 4
             for (int k = wrow_lo; k < NB; ++k) {
-                float l[4];
-                tma_load4(Tt, k, rg, l);
+                float l[RPT];
+                tma_loadn<RPT>(Tt, k, r0, l);
                 const float zv = Acc[k * ZLD + c0];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) out[a] += l[a] * zv;
+                for (int a = 0; a < RPT; ++a) out[a] += l[a] * zv;
             }
         }
         float* Zw = Zr + (size_t)(R % BAND_SLOTS) * NB * ZLD;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < RPT; ++a) {
             Zw[(r0 + a) * ZLD + c0] = out[a];
             if (c0 < ncols) X[(roff + (long long)R * NB + r0 + a) * ldx + c0] = f32_to_f64(out[a]);
         }
@@ -911,24 +932,24 @@ __global__ void __launch_bounds__(BT_NT) k_tile_solve_band_tma(
         const int st = R % NST;
         if (!wait_stage(st)) { abort_cta(); return; }
         issue((R + NST - 1) % NST, R + NST - 1, true);
-        float acc[4];
+        float acc[RPT];
         const double* xs = Sx + (size_t)st * NB * ZLD;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a] = c0 < ncols ? f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
+        for (int a = 0; a < RPT; ++a) acc[a] = c0 < ncols ? f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
         for (int d = 1; d <= kb; ++d) {
             if (R - d < 0) break;
             const float* L = stile(st, d);
             const float* Z = Zr + (size_t)((R - d) % BAND_SLOTS) * NB * ZLD;
 #pragma unroll
             for (int g = 0; g < NB / 4; ++g) {
-                float l[4][4];
+                float l[RPT][4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) tma_load4(L, r0 + a, g, l[a]);
+                for (int a = 0; a < RPT; ++a) tma_load4(L, r0 + a, g, l[a]);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const float zv = Z[(4 * g + kk) * ZLD + c0];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) acc[a] -= l[a][kk] * zv;
+                    for (int a = 0; a < RPT; ++a) acc[a] -= l[a][kk] * zv;
                 }
             }
         }
@@ -942,22 +963,22 @@ __global__ void __launch_bounds__(BT_NT) k_tile_solve_band_tma(
         const int st = it % NST;
         if (!wait_stage(st)) { abort_cta(); return; }
         issue((it + NST - 1) % NST, R - (NST - 1), false);
-        float acc[4];
+        float acc[RPT];
         const double* xs = Sx + (size_t)st * NB * ZLD;
         const float* dv = Sd + st * NB;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a] = c0 < ncols ? dv[r0 + a] * f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
+        for (int a = 0; a < RPT; ++a) acc[a] = c0 < ncols ? dv[r0 + a] * f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
         for (int d = 1; d <= kb; ++d) {
             if (R + d >= K) break;
             const float* L = stile(st, d);
             const float* Z = Zr + (size_t)((R + d) % BAND_SLOTS) * NB * ZLD;
 #pragma unroll 8
             for (int k = 0; k < NB; ++k) {
-                float l[4];
-                tma_load4(L, k, rg, l);
+                float l[RPT];
+                tma_loadn<RPT>(L, k, r0, l);
                 const float zv = Z[k * ZLD + c0];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) acc[a] -= l[a] * zv;
+                for (int a = 0; a < RPT; ++a) acc[a] -= l[a] * zv;
             }
         }
         finish(acc, R, stile(st, 0), false);
@@ -1212,8 +1233,8 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
         const CUtensorMap* tm = tile_tensor_map(tb);
         if (tm) {
             const size_t b = band_tma_smem_bytes();
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_band_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-            k_tile_solve_band_tma<<<dim3(tb.P, (ncols + BT_ZLD - 1) / BT_ZLD), BT_NT, b, s>>>(
+            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_band_tma<BT_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            k_tile_solve_band_tma<BT_NT><<<dim3(tb.P, (ncols + BT_ZLD - 1) / BT_ZLD), BT_NT, b, s>>>(
                 *tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
             MSDD_LAUNCH_CHECK();
         } else if (tb.prec) {
