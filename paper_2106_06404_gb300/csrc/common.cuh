@@ -15,6 +15,11 @@ constexpr int NB = 32;
 constexpr int NB2 = NB * NB;
 // Maximum block size of the subspace iteration (columns of X, Y).
 constexpr int PMAX = 32;
+// rows per block of the eigensolver's residual partial sums: entry
+// ((i * nblk_max + blk) * 2 + {0, 1}) * PMAX + c holds, for rows
+// [32 blk, 32 blk + 32) of problem i and column c, sum |AX - theta BX|^2 and
+// sum |BX|^2
+constexpr int EIG_ROWBLK = 32;
 
 struct CudaError : std::runtime_error {
     explicit CudaError(const std::string& s) : std::runtime_error(s) {}

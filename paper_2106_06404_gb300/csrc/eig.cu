@@ -9,7 +9,7 @@ namespace {
 
 constexpr int TPB = 256;
 constexpr int LD = PMAX + 1;
-constexpr int ROWBLK = 32;
+constexpr int ROWBLK = EIG_ROWBLK;
 
 __global__ void k_init(double* __restrict__ X, const int* __restrict__ n_, const int* __restrict__ K_,
                        const long long* __restrict__ roff_, const int* __restrict__ p_, int ldx,
@@ -615,6 +615,8 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
 
 // X = Y C, AX = AY C, BX = BY C on a block of 32 rows; residual partial sums.
 // Outputs (row, column < p) are spread over the threads, at most 4 each.
+// FULL = false: X = Y C only (AX, BX, partial untouched).
+template <bool FULL>
 __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, const double* __restrict__ AY,
                                                 const double* __restrict__ BY, double* __restrict__ X,
                                                 double* __restrict__ AX, double* __restrict__ BX,
@@ -639,10 +641,25 @@ __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, co
         bool ok = r < n;
         long long idx = (roff + r) * ldx + c;
         sY[rr][c] = ok ? Y[idx] : 0.0;
-        sA[rr][c] = ok ? AY[idx] : 0.0;
-        sB[rr][c] = ok ? BY[idx] : 0.0;
+        if (FULL) {
+            sA[rr][c] = ok ? AY[idx] : 0.0;
+            sB[rr][c] = ok ? BY[idx] : 0.0;
+        }
     }
     __syncthreads();
+    if (!FULL) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = t + k * TPB;
+            if (e >= ROWBLK * p) break;
+            int rr = e / p, c = e % p;
+            double x = 0.0;
+            for (int j = 0; j < p; ++j) x += sY[rr][j] * sC[j][c];
+            int r = r0 + rr;
+            if (r < rows) X[(roff + r) * ldx + c] = x;
+        }
+        return;
+    }
     double vnum[4] = {0, 0, 0, 0}, vden[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -1073,8 +1090,16 @@ void eig_rayleigh_ritz(GevpBatch& g, cudaStream_t s) {
 
 void eig_update(GevpBatch& g, cudaStream_t s) {
     dim3 grid(g.nblk_max, g.P);
-    k_update<<<grid, TPB, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.X.p, g.AX.p, g.BX.p, g.C.p, g.theta.p, g.K.d_n.p,
-                                  g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx, g.partial.p, g.nblk_max, g.done.p);
+    k_update<true><<<grid, TPB, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.X.p, g.AX.p, g.BX.p, g.C.p, g.theta.p, g.K.d_n.p,
+                                        g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx, g.partial.p, g.nblk_max, g.done.p);
+    MSDD_LAUNCH_CHECK();
+}
+
+void eig_update_x(GevpBatch& g, cudaStream_t s) {
+    dim3 grid(g.nblk_max, g.P);
+    k_update<false><<<grid, TPB, 0, s>>>(g.Y.p, nullptr, nullptr, g.X.p, nullptr, nullptr, g.C.p, g.theta.p,
+                                         g.K.d_n.p, g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx, nullptr, g.nblk_max,
+                                         g.done.p);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -76,6 +76,9 @@ void eig_gram(GevpBatch& g, cudaStream_t s);
 void eig_rayleigh_ritz(GevpBatch& g, cudaStream_t s);
 // X = Y C, AX = AY C, BX = BY C, residual partial sums.
 void eig_update(GevpBatch& g, cudaStream_t s);
+// X = Y C only: with a cheap operator (stored stencils) AX and BX are applied
+// afresh, together with the next right-hand side (apply_local_rhs).
+void eig_update_x(GevpBatch& g, cudaStream_t s);
 // Residuals, selection count m = min(nev_max, #{theta < eta}), convergence flags.
 void eig_check(GevpBatch& g, const EigParams& ep, int it, cudaStream_t s);
 

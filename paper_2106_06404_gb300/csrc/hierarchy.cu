@@ -107,10 +107,15 @@ void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long
 // FP64-bound kernels of the other (operators, Gram products, updates).
 // Convergence is read back every `batch` iterations; a half that converged
 // inside a batch only launches kernels that skip its (done) problems.
-template <class Apply, class Solve, class BApply32>
-void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply32 bapply32, int fp32_iters,
-             cudaStream_t st, cudaStream_t st_b, Prof& prof, const std::string& tag, double apply_bytes,
-             double apply_flops, const double* start = nullptr, int start_cols = 0,
+//
+// With `fused` (operators cheaper than the p x p update: stored stencils),
+// the update forms X = Y C only and apply_rhs(v, p0, s) applies Abar and B
+// to the new X, writing the next right-hand side W and the residual partial
+// sums; AX and BX are then not kept.
+template <class Apply, class Solve, class BApply32, class ApplyRhs>
+void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply32 bapply32, ApplyRhs apply_rhs,
+             bool fused, int fp32_iters, cudaStream_t st, cudaStream_t st_b, Prof& prof, const std::string& tag,
+             double apply_bytes, double apply_flops, const double* start = nullptr, int start_cols = 0,
              const long long* d_start_off = nullptr, int groups = 1) {
     if (g.P == 0) return;
     eig_init(g, ep.seed, st);
@@ -185,7 +190,7 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
         cudaStream_t s = gs[k];
         const bool first = it == 0;
         const double fr = (double)active[k] / v.P;
-        eig_form_rhs(v, ep.sigma, first, s);
+        if (!fused || first) eig_form_rhs(v, ep.sigma, first, s);
         prof.begin(tag + "_solve", s);
         solve(v, am[k].pm, s);
         prof.end(s, am[k].solve_b * fr, am[k].solve_f * fr);
@@ -210,9 +215,18 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
         prof.begin(tag + "_rayleigh_ritz", s);
         eig_rayleigh_ritz(v, s);
         prof.end(s, 0.0, 0.0);
-        prof.begin(tag + "_update", s);
-        eig_update(v, s);
-        prof.end(s, 6.0 * am[k].vec_n * 8.0 * fr, 6.0 * am[k].vec_n * am[k].pm * fr);
+        if (fused) {
+            prof.begin(tag + "_update", s);
+            eig_update_x(v, s);
+            prof.end(s, 2.0 * am[k].vec_n * 8.0 * fr, 2.0 * am[k].vec_n * am[k].pm * fr);
+            prof.begin(tag + "_apply", s);
+            apply_rhs(v, gp0[k], s);
+            prof.end(s, (apply_bytes + 8.0 * am[k].vec_n / std::max(1, v.P)) * active[k], apply_flops * active[k]);
+        } else {
+            prof.begin(tag + "_update", s);
+            eig_update(v, s);
+            prof.end(s, 6.0 * am[k].vec_n * 8.0 * fr, 6.0 * am[k].vec_n * am[k].pm * fr);
+        }
         if (v.knorm) {
             if (first) return false;
         } else {
@@ -532,7 +546,11 @@ void Hierarchy::build_fine() {
             [=](GevpBatch& v, int p0, const double* X, double* W, cudaStream_t s) {
                 apply_local_b32(*ls, bx + p0, dim, v.K, X, W, v.ldx, block_p, s);
             },
-            opt.precision == 1 ? opt.fp32_start_iters : 0,
+            [=](GevpBatch& v, int p0, cudaStream_t s) {
+                apply_local_rhs(*ls, bx + p0, dim, v.K, v.X.p, v.W.p, v.ldx, v.d_p.p, v.theta.p, ep.sigma,
+                                v.partial.p, v.nblk_max, v.done.p, s);
+            },
+            true, opt.precision == 1 ? opt.fp32_start_iters : 0,
             st, st2, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9),
             opt.warm_start, opt.warm_start ? opt.warm_cols : 0, d_woff.p, Pf >= 64 ? 2 : 1);
     fm = fge.m.download(st);
@@ -914,7 +932,8 @@ void Hierarchy::build_coarse() {
                     gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, v.W.p, 0.0, Wtp, ngen_max, pmax_m, s);
                     MSDD_CUDA(cudaMemcpyAsync(v.W.p, Wtp, v.W.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
                 },
-                [=](GevpBatch&, int, const double*, double*, cudaStream_t) {}, 0,
+                [=](GevpBatch&, int, const double*, double*, cudaStream_t) {},
+                [=](GevpBatch&, int, cudaStream_t) {}, false, 0,
                 st, nullptr, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
         mm = mge.m.download(st);
         {

@@ -351,6 +351,81 @@ __global__ void __launch_bounds__(128) k_apply_local(const ProbBox* __restrict__
     }
 }
 
+// AX = Abar X and BX = B X from the stored stencils, consumed at once:
+// W = BX - (AX + sigma BX) diag(mu), mu_c = 1 / (theta_c + sigma) (the next
+// right-hand side of the residual-correction subspace iteration; zero on
+// padding rows) and, per 32-row block and column, the residual sums
+// |AX - theta BX|^2 and |BX|^2 (EIG_ROWBLK layout).  Grid: (row blocks,
+// problems); 128 threads = 32 rows x 4 groups of 4 columns.
+__global__ void __launch_bounds__(128) k_apply_rhs(const ProbBox* __restrict__ boxes, int dim,
+                                                   const long long* __restrict__ roff_, const int* __restrict__ K_,
+                                                   const double* __restrict__ A, const double* __restrict__ B,
+                                                   const double* __restrict__ X, double* __restrict__ W, int ldx,
+                                                   const int* __restrict__ p_, const double* __restrict__ theta,
+                                                   double sigma, double* __restrict__ partial, int nblk_max,
+                                                   const int* __restrict__ done) {
+    static_assert(EIG_ROWBLK == NB, "row blocks are tile rows");
+    __shared__ double sn[EIG_ROWBLK][PMAX + 1], sd[EIG_ROWBLK][PMAX + 1], sth[PMAX], smu[PMAX];
+    const int i = blockIdx.y, blk = blockIdx.x;
+    if (done[i]) return;
+    const ProbBox pb = boxes[i];
+    const int n = box_size(pb.nlo, pb.nhi, dim);
+    const int rows = K_[i] * NB;
+    const int r0 = blk * EIG_ROWBLK;
+    if (r0 >= rows) return;   // rows is a multiple of NB = EIG_ROWBLK: every row of the block exists
+    const int p = p_[i];
+    const int w0 = pb.nhi[0] - pb.nlo[0] + 1, w1 = dim >= 2 ? pb.nhi[1] - pb.nlo[1] + 1 : 1;
+    const int noff = dim == 3 ? 27 : 9;
+    const long long roff = roff_[i];
+    const int t = threadIdx.x, rr = t >> 2, cg = (t & 3) * 4;
+    const int r = r0 + rr;
+    if (t < p) {
+        const double th = theta[i * PMAX + t];
+        sth[t] = th;
+        smu[t] = 1.0 / (th + sigma);
+    }
+    __syncthreads();
+    for (int cb = cg; cb < p; cb += 16) {
+        double ax[4] = {0.0, 0.0, 0.0, 0.0}, bx[4] = {0.0, 0.0, 0.0, 0.0};
+        if (r < n) {
+            const double* ar = A + (roff + r) * noff;
+            const double* br = B + (roff + r) * noff;
+            for (int oi = 0; oi < noff; ++oi) {
+                const double a = ar[oi], b = br[oi];
+                if (a == 0.0 && b == 0.0) continue;
+                const double* xr = X + (roff + r + nbr_offset(oi, w0, w1, dim)) * ldx + cb;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (cb + c < p) {
+                        const double v = xr[c];
+                        ax[c] += a * v;
+                        bx[c] += b * v;
+                    }
+            }
+        }
+        double* wr = W + (roff + r) * ldx + cb;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (cb + c < p) {
+                wr[c] = r < n ? bx[c] - (ax[c] + sigma * bx[c]) * smu[cb + c] : 0.0;
+                const double rv = ax[c] - sth[cb + c] * bx[c];
+                sn[rr][cb + c] = rv * rv;
+                sd[rr][cb + c] = bx[c] * bx[c];
+            }
+    }
+    __syncthreads();
+    if (t < PMAX) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; t < p && k < EIG_ROWBLK; ++k) {
+            a += sn[k][t];
+            b += sd[k][t];
+        }
+        double* dst = partial + ((long long)i * nblk_max + blk) * 2 * PMAX;
+        dst[t] = a;
+        dst[PMAX + t] = b;
+    }
+}
+
 // FP32 arithmetic, conversions on the integer pipe; padding rows zeroed.
 __global__ void __launch_bounds__(128) k_apply_local_b32(const ProbBox* __restrict__ boxes, int dim,
                                                          const long long* __restrict__ roff_, const int* __restrict__ K_,
@@ -560,6 +635,16 @@ void apply_local(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const 
     if (layout.P == 0) return;
     dim3 grid(64, layout.P);
     k_apply_local<<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, ls.a.p, ls.b.p, X, AX, BX, ldx, ncols, skip);
+    MSDD_LAUNCH_CHECK();
+}
+
+void apply_local_rhs(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout,
+                     const double* X, double* W, int ldx, const int* d_p, const double* theta, double sigma,
+                     double* partial, int nblk_max, const int* done, cudaStream_t s) {
+    if (layout.P == 0) return;
+    dim3 grid(nblk_max, layout.P);
+    k_apply_rhs<<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, layout.d_K.p, ls.a.p, ls.b.p, X, W, ldx, d_p,
+                                     theta, sigma, partial, nblk_max, done);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -110,6 +110,13 @@ void build_local_stencil(const Geom& g, const ProbBox* d_boxes, const int* d_cou
 // AX = Abar X, BX = X Abar X from the stored stencils (same contract as apply_neumann).
 void apply_local(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout, const double* X,
                  double* AX, double* BX, int ldx, int ncols, const int* skip, cudaStream_t s);
+// W = BX - (AX + sigma BX) diag(1 / (theta + sigma)) with AX, BX from the
+// stored stencils (zero on padding rows, columns < p_i), and the residual
+// partial sums of X (layout of EIG_ROWBLK) for the problems with done == 0;
+// theta is PMAX per problem, partial (P * nblk_max * 2 PMAX).
+void apply_local_rhs(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout,
+                     const double* X, double* W, int ldx, const int* d_p, const double* theta, double sigma,
+                     double* partial, int nblk_max, const int* done, cudaStream_t s);
 // W = X Abar X X in FP32 arithmetic from b32 (same contract as apply_b32).
 void apply_local_b32(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout,
                      const double* X, double* W, int ldx, int ncols, cudaStream_t s);
