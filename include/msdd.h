@@ -136,9 +136,11 @@ typedef struct msdd_stats {
     int null_pivots[MSDD_MAX_LEVELS];         /* regularised pivots (Section 4.2) */
     int m_min[MSDD_MAX_LEVELS], m_max[MSDD_MAX_LEVELS];
     double setup_ms;                          /* wall time of msdd_setup */
-    double phase_ms[8];                       /* 0 decomposition, 1 Dirichlet factor, 2 shifted
-                                                 Neumann factor, 3 fine eigensolve, 4 coarse
-                                                 Galerkin, 5 coarse eigensolve, 6 coarse factors */
+    double phase_ms[8];                       /* 0 decomposition, 1 Dirichlet factor (host time to
+                                                 enqueue it: it runs on a side stream beside
+                                                 phases 2-5), 2 shifted Neumann factor, 3 fine
+                                                 eigensolve, 4 coarse Galerkin, 5 coarse
+                                                 eigensolve, 6 coarse factors */
     int pcg_iterations;                       /* of the last solve */
     double pcg_rel_residual;                  /* recursive residual / ||b|| */
     double solve_ms;

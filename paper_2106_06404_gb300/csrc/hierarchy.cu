@@ -285,6 +285,11 @@ Hierarchy::~Hierarchy() {
         cudaStreamSynchronize(st2);
         cudaStreamDestroy(st2);
     }
+    if (st3) {
+        cudaStreamSynchronize(st3);
+        cudaStreamDestroy(st3);
+    }
+    if (ev_dir) cudaEventDestroy(ev_dir);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (own_stream && st) {
@@ -371,6 +376,8 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
         own_stream = true;
     }
     MSDD_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    MSDD_CUDA(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_dir, cudaEventDisableTiming));
     MSDD_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
     MSDD_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     levels = dec.levels;
@@ -387,6 +394,9 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
 
     build_fine();
     build_coarse();
+    // the fine Dirichlet factors ran on st3 beside the eigensolves
+    MSDD_CUDA(cudaStreamWaitEvent(st, ev_dir, 0));
+    check_status(fdir, st, "fine Dirichlet factorisation");
 
     // CG buffers and the stored global stencil
     x.alloc(nun); r.alloc(nun); p.alloc(nun); q.alloc(nun); z.alloc(nun);
@@ -460,7 +470,10 @@ void Hierarchy::build_fine() {
     MSDD_CUDA(cudaStreamSynchronize(st));
     stats.phase_ms[0] = ms_since(t0);
 
-    // ---- Dirichlet factors
+    // ---- Dirichlet factors: only the preconditioner needs them, so they are
+    // assembled and factored on the side stream st3, beside the Neumann
+    // factors and the fine eigensolves (ev_dir marks completion; their status
+    // is checked at the end of the set-up)
     t0 = Clock::now();
     std::vector<int> nD(Pf), bD(Pf), nN(Pf), bN(Pf);
     for (int j = 0; j < Pf; ++j) {
@@ -471,19 +484,20 @@ void Hierarchy::build_fine() {
     }
     const int prec = opt.precision ? 1 : 0;
     fdir.layout(nD, bD, prec, st);
-    tile_zero(fdir, st);
-    assemble_local_tiles(g, d_fboxes.p, d_count.p, fdir, 0, 0.0, st);
+    MSDD_CUDA(cudaStreamSynchronize(st));            // layout tables uploaded
+    tile_zero(fdir, st3);
+    assemble_local_tiles(g, d_fboxes.p, d_count.p, fdir, 0, 0.0, st3);
     {
         double fb = 0, ff = 0, sz = prec ? 4.0 : 8.0;
         for (int j = 0; j < Pf; ++j) {
             fb += 2.0 * nD[j] * (bD[j] + 1.0) * sz;
             ff += (double)nD[j] * bD[j] * bD[j];
         }
-        prof.begin("fine_factor", st);
-        tile_factor(fdir, 0.0, st);
-        prof.end(st, fb, ff);
+        prof.begin("fine_factor", st3);
+        tile_factor(fdir, 0.0, st3);
+        prof.end(st3, fb, ff);
     }
-    check_status(fdir, st, "fine Dirichlet factorisation");
+    MSDD_CUDA(cudaEventRecord(ev_dir, st3));
     frhs.alloc(fdir.total_rows);
     frhs.zero(st);
     MSDD_CUDA(cudaStreamSynchronize(st));

@@ -87,7 +87,8 @@ struct Hierarchy {
     cudaStream_t st = nullptr;
     bool own_stream = false;           // created when the caller passes no stream
     cudaStream_t st2 = nullptr;        // coarse chain of the preconditioner
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t st3 = nullptr;        // set-up side stream: fine Dirichlet factors
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dir = nullptr;
     int levels = 0, L = 0;
     long long nun = 0;
     msdd_stats stats{};

@@ -357,6 +357,10 @@ __global__ void __launch_bounds__(128) k_apply_local(const ProbBox* __restrict__
 // padding rows) and, per 32-row block and column, the residual sums
 // |AX - theta BX|^2 and |BX|^2 (EIG_ROWBLK layout).  Grid: (row blocks,
 // problems); 128 threads = 32 rows x 4 groups of 4 columns.
+// Since BX - (AX + sigma BX) mu = -(AX - theta BX) mu, W is one product of
+// the residual R = AX - theta BX.  The squares are summed in FP32 (from
+// integer-pipe conversions): they only feed the relative residual test, and
+// the FP64 pipe is the bound of this kernel.
 __global__ void __launch_bounds__(128) k_apply_rhs(const ProbBox* __restrict__ boxes, int dim,
                                                    const long long* __restrict__ roff_, const int* __restrict__ K_,
                                                    const double* __restrict__ A, const double* __restrict__ B,
@@ -365,7 +369,8 @@ __global__ void __launch_bounds__(128) k_apply_rhs(const ProbBox* __restrict__ b
                                                    double sigma, double* __restrict__ partial, int nblk_max,
                                                    const int* __restrict__ done) {
     static_assert(EIG_ROWBLK == NB, "row blocks are tile rows");
-    __shared__ double sn[EIG_ROWBLK][PMAX + 1], sd[EIG_ROWBLK][PMAX + 1], sth[PMAX], smu[PMAX];
+    __shared__ float sn[EIG_ROWBLK][PMAX + 1], sd[EIG_ROWBLK][PMAX + 1];
+    __shared__ double sth[PMAX], smu[PMAX];
     const int i = blockIdx.y, blk = blockIdx.x;
     if (done[i]) return;
     const ProbBox pb = boxes[i];
@@ -407,22 +412,23 @@ __global__ void __launch_bounds__(128) k_apply_rhs(const ProbBox* __restrict__ b
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             if (cb + c < p) {
-                wr[c] = r < n ? bx[c] - (ax[c] + sigma * bx[c]) * smu[cb + c] : 0.0;
                 const double rv = ax[c] - sth[cb + c] * bx[c];
-                sn[rr][cb + c] = rv * rv;
-                sd[rr][cb + c] = bx[c] * bx[c];
+                wr[c] = r < n ? -rv * smu[cb + c] : 0.0;
+                const float rf = f64_to_f32(rv), bf = f64_to_f32(bx[c]);
+                sn[rr][cb + c] = rf * rf;
+                sd[rr][cb + c] = bf * bf;
             }
     }
     __syncthreads();
     if (t < PMAX) {
-        double a = 0.0, b = 0.0;
+        float a = 0.f, b = 0.f;
         for (int k = 0; t < p && k < EIG_ROWBLK; ++k) {
             a += sn[k][t];
             b += sd[k][t];
         }
         double* dst = partial + ((long long)i * nblk_max + blk) * 2 * PMAX;
-        dst[t] = a;
-        dst[PMAX + t] = b;
+        dst[t] = f32_to_f64(a);
+        dst[PMAX + t] = f32_to_f64(b);
     }
 }
 
