@@ -319,7 +319,7 @@ __device__ __forceinline__ void rot_params(double app, double aqq, double apq, d
 template <typename T>
 __device__ void block_jacobi(T (*S)[LD], T (*V)[LD], int q, T rel_tol, T floor_rel, int max_sweeps) {
     __shared__ T sc[2][PMAX / 2], ss[2][PMAX / 2];
-    __shared__ int sa[2][PMAX / 2], sb[2][PMAX / 2];
+    __shared__ int sa[2][PMAX / 2], sb[2][PMAX / 2], sr[2][PMAX / 2];
     __shared__ double s_scale;
     const int t = threadIdx.x, h = q / 2;
     for (int e = t; e < q * q; e += TPB) V[e / q][e % q] = (e / q == e % q) ? T(1) : T(0);
@@ -343,6 +343,7 @@ __device__ void block_jacobi(T (*S)[LD], T (*V)[LD], int q, T rel_tol, T floor_r
         }
         if (!__syncthreads_or(active)) break;
         for (int step = 0; step < q - 1; ++step, par ^= 1) {
+            int rot = 0;
             if (t < h) {
                 // circle method: position 0 fixed, the others rotate
                 int pos1 = t, pos2 = q - 1 - t;
@@ -350,19 +351,18 @@ __device__ void block_jacobi(T (*S)[LD], T (*V)[LD], int q, T rel_tol, T floor_r
                 int b = 1 + (pos2 - 1 + step) % (q - 1);
                 if (a > b) { int tmp = a; a = b; b = tmp; }
                 T c = T(1), s = T(0);
-                if (pair_active<T>(S[a][a], S[b][b], S[a][b], rel_tol, floor_abs)) rot_params(S[a][a], S[b][b], S[a][b], c, s);
-                sa[par][t] = a; sb[par][t] = b; sc[par][t] = c; ss[par][t] = s;
+                rot = pair_active<T>(S[a][a], S[b][b], S[a][b], rel_tol, floor_abs) ? 1 : 0;
+                if (rot) rot_params(S[a][a], S[b][b], S[a][b], c, s);
+                sa[par][t] = a; sb[par][t] = b; sc[par][t] = c; ss[par][t] = s; sr[par][t] = rot;
             }
-            __syncthreads();
-            bool any = false;
-            for (int j = 0; j < h; ++j) any |= ss[par][j] != T(0);
-            if (!any) continue;
+            // (integer flags: FP64 comparisons would occupy the narrow FP64 pipe)
+            if (!__syncthreads_or(rot)) continue;
             const int nblk = h * h;
             for (int e = t; e < nblk + q * h; e += TPB) {
                 if (e < nblk) {
                     const int j = e / h, jj = e % h;
+                    if (!(sr[par][j] | sr[par][jj])) continue;
                     const T sj = ss[par][j], sjj = ss[par][jj];
-                    if (sj == T(0) && sjj == T(0)) continue;
                     const T cj = sc[par][j], cjj = sc[par][jj];
                     const int x1 = sa[par][j], x2 = sb[par][j], y1 = sa[par][jj], y2 = sb[par][jj];
                     const T b11 = S[x1][y1], b12 = S[x1][y2], b21 = S[x2][y1], b22 = S[x2][y2];
@@ -374,8 +374,8 @@ __device__ void block_jacobi(T (*S)[LD], T (*V)[LD], int q, T rel_tol, T floor_r
                     S[x1][y1] = n11; S[x1][y2] = n12; S[x2][y1] = n21; S[x2][y2] = n22;
                 } else {
                     const int e2 = e - nblk, k = e2 / h, jj = e2 % h;
+                    if (!sr[par][jj]) continue;
                     const T sjj = ss[par][jj];
-                    if (sjj == T(0)) continue;
                     const T cjj = sc[par][jj];
                     const int y1 = sa[par][jj], y2 = sb[par][jj];
                     const T u = V[k][y1], v = V[k][y2];
@@ -460,6 +460,179 @@ __device__ void mixed_jacobi(double (*S)[LD], double (*V)[LD], double (*W)[LD], 
     __syncthreads();
 }
 
+
+// D = op(E) op(F) for q x q FP32 blocks in shared memory (q even).
+__device__ __forceinline__ void smem_gemm_f(float (*D)[LD], const float (*E)[LD], const float (*F)[LD], int q,
+                                            bool tE, bool tF) {
+    for (int e = threadIdx.x; e < q * q; e += TPB) {
+        const int a = e / q, b = e % q;
+        float v0 = 0.f, v1 = 0.f;
+        for (int j = 0; j < q; j += 2) {
+            const float e0 = tE ? E[j][a] : E[a][j], e1 = tE ? E[j + 1][a] : E[a][j + 1];
+            const float f0 = tF ? F[b][j] : F[j][b], f1 = tF ? F[b][j + 1] : F[j + 1][b];
+            v0 = fmaf(e0, f0, v0);
+            v1 = fmaf(e1, f1, v1);
+        }
+        D[a][b] = v0 + v1;
+    }
+}
+
+// Rayleigh-Ritz for a well-conditioned scaled pencil (Hs, Ms), FP32 first:
+//   1. FP32 Cholesky Ms = L L^T and U = L^{-1} (warp 0), G = U Hs U^T and its
+//      FP32 Jacobi eigenvectors V; Z = U^T V (so Z^T Ms Z ~ I, Z^T Hs Z ~
+//      diagonal to FP32 accuracy);
+//   2. FP64: Z <- Z P with P = I - E/2 + 3 E^2/8, E = Z^T Ms Z - I (the
+//      second-order inverse square root of I + E: the error drops from |E|
+//      to O(|E|^3)), repeated while |E| > 2e-6 (at most 3 times);
+//   3. FP64 Jacobi on A = Z^T Hs Z (nearly diagonal), Z <- Z Q.
+// Every serial chain runs in FP32 and the FP64 work is seven or so q x q
+// products plus the finishing Jacobi steps.  Returns false (nothing of L and
+// T changed but a unit dummy pivot) when an FP32 pivot is below 1e-3 or
+// |E| > 0.05: the caller then takes the FP64 Cholesky path.  On success S
+// holds theta on its diagonal and T the coefficients C' (rows scaled by D
+// later).  L = Ms, T = Hs on entry (zero padded to q); S, V, U scratch.
+__device__ bool rr_fast(double (*S)[LD], double (*V)[LD], double (*L)[LD], double (*T)[LD], double (*U)[LD], int p,
+                        int q) {
+    __shared__ float linv32[PMAX];
+    __shared__ int s_fail32, s_emax;
+    const int t = threadIdx.x;
+    float (*L32)[LD] = reinterpret_cast<float (*)[LD]>(&U[0][0]);
+    float (*U32)[LD] = L32 + PMAX;
+    float (*T32)[LD] = reinterpret_cast<float (*)[LD]>(&S[0][0]);
+    float (*G32)[LD] = T32 + PMAX;
+    float (*V32)[LD] = reinterpret_cast<float (*)[LD]>(&V[0][0]);
+    float (*W32)[LD] = V32 + PMAX;
+    if (t == 0 && q > p) L[p][p] = 1.0;                 // odd p: a unit dummy pivot
+    __syncthreads();
+    for (int e = t; e < q * q; e += TPB) {
+        const int a = e / q, b = e % q;
+        L32[a][b] = f64_to_f32(L[a][b]);
+        T32[a][b] = f64_to_f32(T[a][b]);
+    }
+    __syncthreads();
+    if (t < 32) {
+        const int lane = t;
+        int fail = 0;
+        for (int k = 0; k < q; ++k) {
+            const float d = L32[k][k];
+            float r = 0.f, lkk = 0.f;
+            if (d > 1e-3f) {
+                r = rsqrtf(d);
+                r = r * fmaf(-0.5f * d * r, r, 1.5f);
+                lkk = d * r;
+            } else {
+                fail = 1;
+            }
+            __syncwarp();
+            if (lane == k) { L32[k][k] = lkk; linv32[k] = r; }
+            if (lane > k && lane < q) L32[lane][k] *= r;
+            __syncwarp();
+            if (lane > k && lane < q)
+                for (int b = k + 1; b <= lane; ++b) L32[lane][b] = fmaf(-L32[lane][k], L32[b][k], L32[lane][b]);
+            __syncwarp();
+        }
+        if (lane < q) {
+            const int c = lane;
+            for (int r = 0; r < q; ++r) {
+                float v = 0.f;
+                if (r >= c) {
+                    float a0 = (r == c) ? 1.f : 0.f, a1 = 0.f;
+                    int j = c;
+                    for (; j + 1 < r; j += 2) {
+                        a0 = fmaf(-L32[r][j], U32[j][c], a0);
+                        a1 = fmaf(-L32[r][j + 1], U32[j + 1][c], a1);
+                    }
+                    if (j < r) a0 = fmaf(-L32[r][j], U32[j][c], a0);
+                    v = (a0 + a1) * linv32[r];
+                }
+                U32[r][c] = v;
+            }
+        }
+        if (lane == 0) { s_fail32 = fail; s_emax = 0; }
+    }
+    __syncthreads();
+    if (s_fail32) return false;
+    smem_gemm_f(W32, U32, T32, q, false, false);        // W = U Hs
+    __syncthreads();
+    smem_gemm_f(G32, W32, U32, q, false, true);         // G = W U^T
+    __syncthreads();
+    for (int e = t; e < q * q; e += TPB) {
+        const int a = e / q, b = e % q;
+        if (a < b) {
+            const float v = 0.5f * (G32[a][b] + G32[b][a]);
+            G32[a][b] = v;
+            G32[b][a] = v;
+        }
+    }
+    __syncthreads();
+    block_jacobi<float>(G32, V32, q, 1e-6f, 1e-9f, 12);
+    __syncthreads();
+    smem_gemm_f(L32, U32, V32, q, true, false);         // Z = U^T V (FP32), into the L32 slot
+    __syncthreads();
+    for (int e = t; e < q * q; e += TPB) S[e / q][e % q] = f32_to_f64(L32[e / q][e % q]);
+    __syncthreads();
+    // FP64 Ms-orthonormalisation of Z
+    bool ok = false;
+    for (int round = 0; round < 3; ++round) {
+        smem_gemm(V, L, S, q, false);                    // W = Ms Z
+        __syncthreads();
+        smem_gemm(U, S, V, q, true);                     // Z^T W
+        __syncthreads();
+        float em = 0.f;
+        for (int e = t; e < q * q; e += TPB) {
+            const int a = e / q, b = e % q;
+            double v = U[a][b];
+            if (a == b) {
+                v -= 1.0;
+                U[a][b] = v;
+            }
+            const float av = fabsf(f64_to_f32(v));
+            em = av != av ? 1e30f : fmaxf(em, av);        // NaN sends the problem to the FP64 path
+        }
+        for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+        if ((t & 31) == 0) atomicMax(&s_emax, __float_as_int(em));     // non-negative: int order = float order
+        __syncthreads();
+        const float emax = __int_as_float(s_emax);
+        if (!(emax <= 0.05f)) return false;
+        if (emax == 0.f) { ok = true; break; }
+        smem_gemm(V, U, U, q, false);                    // E^2
+        __syncthreads();
+        for (int e = t; e < q * q; e += TPB) {
+            const int a = e / q, b = e % q;
+            V[a][b] = fma(0.375, V[a][b], fma(-0.5, U[a][b], a == b ? 1.0 : 0.0));
+        }
+        __syncthreads();
+        smem_gemm(U, S, V, q, false);                    // Z P
+        __syncthreads();
+        for (int e = t; e < q * q; e += TPB) S[e / q][e % q] = U[e / q][e % q];
+        if (t == 0) s_emax = 0;
+        __syncthreads();
+        if (emax <= 2e-6f) { ok = true; break; }
+    }
+    if (!ok) return false;
+    // A = Z^T Hs Z, then the FP64 Jacobi finish
+    smem_gemm(V, T, S, q, false);                        // W = Hs Z
+    __syncthreads();
+    smem_gemm(U, S, V, q, true);                         // A = Z^T W
+    __syncthreads();
+    for (int e = t; e < q * q; e += TPB) {
+        const int a = e / q, b = e % q;
+        if (a < b) {
+            const double v = 0.5 * (U[a][b] + U[b][a]);
+            U[a][b] = v;
+            U[b][a] = v;
+        }
+    }
+    __syncthreads();
+    block_jacobi<double>(U, V, q, 1e-10, 1e-15, 8);
+    __syncthreads();
+    smem_gemm(T, S, V, q, false);                        // C' = Z Q
+    __syncthreads();
+    for (int e = t; e < q * q; e += TPB) S[e / q][e % q] = U[e / q][e % q];
+    __syncthreads();
+    return true;
+}
+
 // Rayleigh-Ritz on (H, M): column scaling D = diag(M)^{-1/2}, Cholesky of
 // D M D (Jacobi-based pseudo-inverse square root if it is not numerically
 // positive definite), eigen-decomposition of the reduced standard problem.
@@ -472,7 +645,7 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
     __shared__ double S[PMAX][LD], V[PMAX][LD], L[PMAX][LD], T[PMAX][LD], U[PMAX][LD];
     __shared__ double dsc[PMAX], th[PMAX], linv[PMAX];
     __shared__ int perm[PMAX];
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_zero;
     const int i = blockIdx.x;
     if (done[i]) return;
     const int p = p_[i];
@@ -480,9 +653,12 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
     const int t = threadIdx.x;
     const double* Hi = H + (long long)i * PMAX * PMAX;
     const double* Mi = M + (long long)i * PMAX * PMAX;
+    if (t == 0) s_zero = 0;
+    __syncthreads();
     if (t < PMAX) {
         double mkk = t < p ? Mi[t * PMAX + t] : 0.0;
         dsc[t] = mkk > 0.0 ? rsqrt_nr(mkk) : 0.0;
+        if (t < p && !(mkk > 0.0)) s_zero = 1;
     }
     __syncthreads();
     // scaled M into L, scaled H into T (q x q, dummy rows zero)
@@ -493,6 +669,11 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
         T[a][b] = ok ? dsc[a] * Hi[a * PMAX + b] * dsc[b] : 0.0;
     }
     __syncthreads();
+    int r = 0;
+    if (!s_zero && rr_fast(S, V, L, T, U, p, q)) {
+        r = p;
+        goto sorted_output;
+    }
     // warp 0: Cholesky of L in place (lane a owns row a), then U = L^{-1}
     // (lane c owns column c).  A column with dsc == 0 is dropped (linv = 0);
     // any other pivot <= 1e-13 sends the problem to the pseudo-inverse path.
@@ -536,7 +717,6 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
         if (lane == 0) s_fail = fail;
     }
     __syncthreads();
-    int r = 0;
     if (!s_fail) {
         // G = U T U^T  (S = U T, then V = S U^T)
         smem_gemm(S, U, T, q, false);
@@ -591,6 +771,7 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
         __syncthreads();
         for (int k = 0; k < p; ++k) r += th[k] > 0.0 ? 1 : 0;
     }
+sorted_output:
     // sort eigenvalues ascending; apply D to rows of C
     if (t < p) {
         double v = S[t][t];
