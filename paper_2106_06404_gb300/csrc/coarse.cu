@@ -18,26 +18,38 @@ __global__ void k_block_sum(const SumItem* __restrict__ items, const long long* 
 
 constexpr int GT = 32;
 
+// C tile of 32 rows x 8 NQ columns per CTA (NQ < 4 when the items are
+// narrower than 32 columns: the FP64 pipe bounds this kernel, so padded
+// columns cost as much as real ones).  skip[z] != 0 leaves item z alone.
+template <int NQ>
 __global__ void __launch_bounds__(256) k_gemm_batched(const GemmItem* __restrict__ items, int transA, int transB,
                                                       double alpha, const double* __restrict__ A,
                                                       const double* __restrict__ B, double beta,
-                                                      double* __restrict__ C, const int* __restrict__ gdone) {
-    __shared__ double sA[GT][GT + 1], sB[GT][GT + 1];
+                                                      double* __restrict__ C, const int* __restrict__ gdone,
+                                                      const int* __restrict__ skip) {
+    constexpr int TN = 8 * NQ;
+    __shared__ double sA[GT][GT + 1], sB[GT][TN + 1];
     if (gdone && *gdone) return;
+    if (skip && skip[blockIdx.z]) return;
     const GemmItem it = items[blockIdx.z];
-    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * TN;
     if (row0 >= it.m || col0 >= it.n) return;
     const int t = threadIdx.x;
     const int r = t >> 3, cb = t & 7;
-    double acc[4] = {0, 0, 0, 0};
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int k0 = 0; k0 < it.k; k0 += GT) {
         for (int e = t; e < GT * GT; e += 256) {
-            int a = e / GT, b = e % GT;       // sA[a = row][b = k], sB[a = k][b = col]
+            int a = e / GT, b = e % GT;       // sA[a = row][b = k]
             int gr = row0 + a, gk = k0 + b;
             double va = 0.0;
             if (gr < it.m && gk < it.k)
                 va = transA ? A[it.aoff + (long long)gk * it.lda + gr] : A[it.aoff + (long long)gr * it.lda + gk];
             sA[a][b] = va;
+        }
+        for (int e = t; e < GT * TN; e += 256) {
+            int a = e / TN, b = e % TN;       // sB[a = k][b = col]
             int bk = k0 + a, bc = col0 + b;
             double vb = 0.0;
             if (bk < it.k && bc < it.n)
@@ -49,12 +61,12 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const GemmItem* __restrict
         for (int k = 0; k < GT; ++k) {
             double a = sA[r][k];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += a * sB[k][cb + 8 * q];
+            for (int q = 0; q < NQ; ++q) acc[q] += a * sB[k][cb + 8 * q];
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         int gr = row0 + r, gc = col0 + cb + 8 * q;
         if (gr < it.m && gc < it.n) {
             double* dst = C + it.coff + (long long)gr * it.ldc + gc;
@@ -230,10 +242,16 @@ void block_sum(const SumItem* d_items, int nitems, const long long* d_contrib, c
 
 void gemm_batched(const GemmItem* d_items, int nitems, int transA, int transB, double alpha, const double* A,
                   const double* B, double beta, double* C, int max_m, int max_n, cudaStream_t s,
-                  const int* gdone) {
+                  const int* gdone, const int* skip) {
     if (nitems == 0 || max_m == 0 || max_n == 0) return;
-    dim3 grid(ceil_div(max_n, GT), ceil_div(max_m, GT), nitems);
-    k_gemm_batched<<<grid, 256, 0, s>>>(d_items, transA, transB, alpha, A, B, beta, C, gdone);
+    const int nq = max_n >= 32 ? 4 : (max_n + 7) / 8;
+    dim3 grid(ceil_div(max_n, 8 * nq), ceil_div(max_m, GT), nitems);
+    switch (nq) {
+        case 1: k_gemm_batched<1><<<grid, 256, 0, s>>>(d_items, transA, transB, alpha, A, B, beta, C, gdone, skip); break;
+        case 2: k_gemm_batched<2><<<grid, 256, 0, s>>>(d_items, transA, transB, alpha, A, B, beta, C, gdone, skip); break;
+        case 3: k_gemm_batched<3><<<grid, 256, 0, s>>>(d_items, transA, transB, alpha, A, B, beta, C, gdone, skip); break;
+        default: k_gemm_batched<4><<<grid, 256, 0, s>>>(d_items, transA, transB, alpha, A, B, beta, C, gdone, skip); break;
+    }
     MSDD_LAUNCH_CHECK();
 }
 

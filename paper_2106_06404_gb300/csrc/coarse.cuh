@@ -18,7 +18,8 @@ struct SumItem {
 void block_sum(const SumItem* d_items, int nitems, const long long* d_contrib, const double* G, double* dst,
                cudaStream_t s);
 
-// Batched C_b = alpha * op(A_b) op(B_b) + beta * C_b, FP64.
+// Batched C_b = alpha * op(A_b) op(B_b) + beta * C_b, FP64.  Nothing is done
+// when *gdone != 0; item b is left alone when skip[b] != 0.
 struct GemmItem {
     long long aoff, boff, coff;
     int m, n, k;
@@ -26,7 +27,7 @@ struct GemmItem {
 };
 void gemm_batched(const GemmItem* d_items, int nitems, int transA, int transB, double alpha, const double* A,
                   const double* B, double beta, double* C, int max_m, int max_n, cudaStream_t s,
-                  const int* gdone = nullptr);
+                  const int* gdone = nullptr, const int* skip = nullptr);
 
 // Batched matrix-vector products with the GemmItem geometry (n = 1 implied):
 // y[coff + r * ldc] = alpha * sum_k op(A)[r][k] x[boff + k * ldb] + beta * y[...].

@@ -1094,44 +1094,77 @@ __global__ void __launch_bounds__(TPB) k_update32(const double* __restrict__ W, 
     }
 }
 
-__global__ void k_dense_pencil(const double* __restrict__ A, const long long* __restrict__ aoff,
-                               const int* __restrict__ n_, const int* __restrict__ nown_,
-                               const long long* __restrict__ roff_, const double* __restrict__ X,
-                               double* __restrict__ AX, double* __restrict__ BX, int ldx, int ncols,
-                               const int* __restrict__ skip) {
-    const int i = blockIdx.y;
+// AX = Abar X and BX = X Abar X (X the indicator of the own generators, rows
+// and columns < nown): one tiled product (32 rows x 8 NQ columns of the
+// output per CTA, k-tiles of 32 staged in shared memory) whose k-sum is
+// split at nown: AX = own part + rest, BX = own part on own rows.
+template <int NQ>
+__global__ void __launch_bounds__(256) k_dense_pencil(const double* __restrict__ A, const long long* __restrict__ aoff,
+                                                      const int* __restrict__ n_, const int* __restrict__ nown_,
+                                                      const long long* __restrict__ roff_,
+                                                      const double* __restrict__ X, double* __restrict__ AX,
+                                                      double* __restrict__ BX, int ldx, int ncols,
+                                                      const int* __restrict__ skip) {
+    constexpr int GT = 32, TN = 8 * NQ;
+    __shared__ double sA[GT][GT + 1], sX[GT][TN + 1];
+    const int i = blockIdx.z;
     if (skip && skip[i]) return;
     const int n = n_[i], nown = nown_[i];
-    const int nchunk = (ncols + 7) / 8;
+    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * TN;
+    if (row0 >= n || col0 >= ncols) return;
     const long long roff = roff_[i];
     const double* Ai = A + aoff[i];
-    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n * nchunk;
-         w += (long long)gridDim.x * blockDim.x) {
-        int r = (int)(w / nchunk), c0 = (int)(w % nchunk) * 8;
-        double so[8], sn[8];
+    const int t = threadIdx.x, r = t >> 3, cb = t & 7;
+    double ao[NQ], an[NQ];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) { so[c] = 0.0; sn[c] = 0.0; }
-        const double* arow = Ai + (long long)r * n;
-        for (int j = 0; j < n; ++j) {
-            double a = arow[j];
-            if (a == 0.0) continue;
-            const double* xr = X + (roff + j) * ldx + c0;
-            if (j < nown) {
+    for (int q = 0; q < NQ; ++q) { ao[q] = 0.0; an[q] = 0.0; }
+    for (int k0 = 0; k0 < n; k0 += GT) {
+        for (int e = t; e < GT * GT; e += 256) {
+            const int a = e / GT, b = e % GT, gr = row0 + a, gk = k0 + b;
+            sA[a][b] = (gr < n && gk < n) ? Ai[(long long)gr * n + gk] : 0.0;
+        }
+        for (int e = t; e < GT * TN; e += 256) {
+            const int a = e / TN, b = e % TN, gk = k0 + a, gc = col0 + b;
+            sX[a][b] = (gk < n && gc < ncols) ? X[(roff + gk) * ldx + gc] : 0.0;
+        }
+        __syncthreads();
+        if (k0 + GT <= nown) {
+#pragma unroll 8
+            for (int k = 0; k < GT; ++k) {
+                const double a = sA[r][k];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) if (c0 + c < ncols) so[c] += a * xr[c];
-            } else {
+                for (int q = 0; q < NQ; ++q) ao[q] += a * sX[k][cb + 8 * q];
+            }
+        } else if (k0 >= nown) {
+#pragma unroll 8
+            for (int k = 0; k < GT; ++k) {
+                const double a = sA[r][k];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) if (c0 + c < ncols) sn[c] += a * xr[c];
+                for (int q = 0; q < NQ; ++q) an[q] += a * sX[k][cb + 8 * q];
+            }
+        } else {
+            for (int k = 0; k < GT; ++k) {
+                const double a = sA[r][k];
+                if (k0 + k < nown) {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) ao[q] += a * sX[k][cb + 8 * q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) an[q] += a * sX[k][cb + 8 * q];
+                }
             }
         }
-        double* ar = AX + (roff + r) * ldx + c0;
-        double* br = BX + (roff + r) * ldx + c0;
+        __syncthreads();
+    }
+    const int gr = row0 + r;
+    if (gr >= n) return;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (c0 + c < ncols) {
-                ar[c] = so[c] + sn[c];
-                br[c] = r < nown ? so[c] : 0.0;
-            }
+    for (int q = 0; q < NQ; ++q) {
+        const int gc = col0 + cb + 8 * q;
+        if (gc < ncols) {
+            AX[(roff + gr) * ldx + gc] = ao[q] + an[q];
+            BX[(roff + gr) * ldx + gc] = gr < nown ? ao[q] : 0.0;
+        }
     }
 }
 
@@ -1294,9 +1327,15 @@ void eig_check(GevpBatch& g, const EigParams& ep, int it, cudaStream_t s) {
 void apply_dense_pencil(const double* Abar, const long long* d_aoff, const int* d_n, const int* d_nown,
                         const TileBatch& layout, const double* X, double* AX, double* BX, int ldx, int ncols,
                         const int* skip, int P, int nmax, cudaStream_t s) {
-    if (P == 0) return;
-    dim3 grid(std::max(1u, ceil_div((long long)nmax * ((ncols + 7) / 8), 128)), P);
-    k_dense_pencil<<<grid, 128, 0, s>>>(Abar, d_aoff, d_n, d_nown, layout.d_roff.p, X, AX, BX, ldx, ncols, skip);
+    if (P == 0 || nmax == 0 || ncols == 0) return;
+    const int nq = ncols >= 32 ? 4 : (ncols + 7) / 8;
+    dim3 grid(ceil_div(ncols, 8 * nq), ceil_div(nmax, 32), P);
+    switch (nq) {
+        case 1: k_dense_pencil<1><<<grid, 256, 0, s>>>(Abar, d_aoff, d_n, d_nown, layout.d_roff.p, X, AX, BX, ldx, ncols, skip); break;
+        case 2: k_dense_pencil<2><<<grid, 256, 0, s>>>(Abar, d_aoff, d_n, d_nown, layout.d_roff.p, X, AX, BX, ldx, ncols, skip); break;
+        case 3: k_dense_pencil<3><<<grid, 256, 0, s>>>(Abar, d_aoff, d_n, d_nown, layout.d_roff.p, X, AX, BX, ldx, ncols, skip); break;
+        default: k_dense_pencil<4><<<grid, 256, 0, s>>>(Abar, d_aoff, d_n, d_nown, layout.d_roff.p, X, AX, BX, ldx, ncols, skip); break;
+    }
     MSDD_LAUNCH_CHECK();
 }
 

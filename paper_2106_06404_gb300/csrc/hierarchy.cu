@@ -96,7 +96,7 @@ void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long
 
 // Subspace iteration driver.  apply(v, p0, X, AX, BX, skip, s) applies Abar
 // and B to the problems of batch view v (first problem p0 of the whole
-// batch), solve(v, ncols, s) applies K^{-1} to v.W, bapply32(v, p0, X, W, s)
+// batch), solve(v, p0, ncols, s) applies K^{-1} to v.W, bapply32(v, p0, X, W, s)
 // is the FP32 B apply.  `tag` names the kernel families for profiling;
 // `apply_bytes`/`apply_flops` are the algorithmic amounts of one operator
 // application per problem.
@@ -105,8 +105,9 @@ void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long
 // whose iterations are offset by about one band solve: the latency-bound
 // kernels of one half (band solve, Rayleigh-Ritz) then run beside the
 // FP64-bound kernels of the other (operators, Gram products, updates).
-// Convergence is read back every `batch` iterations; a half that converged
-// inside a batch only launches kernels that skip its (done) problems.
+// Convergence is read back every `batch` = 4 iterations (a host round trip
+// per iteration would drain the stream); a group that converged inside a
+// batch only launches kernels that skip its (done) problems.
 //
 // With `fused` (operators cheaper than the p x p update: stored stencils),
 // the update forms X = Y C only and apply_rhs(v, p0, s) applies Abar and B
@@ -121,7 +122,7 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
     eig_init(g, ep.seed, st);
     eig_load_start(g, start, start_cols, d_start_off, st);
     const int G = (groups == 2 && g.P >= 2 && st_b) ? 2 : 1;
-    const int batch = G == 2 ? 4 : 1;
+    const int batch = 4;
     std::vector<GevpBatch> gv;
     std::vector<int> gp0;
     std::vector<cudaStream_t> gs;
@@ -169,7 +170,7 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
             bapply32(v, gp0[k], v.X.p, v.W.p, gs[k]);
             prof.end(gs[k], 0.0, 0.0);
             prof.begin(tag + "_solve", gs[k]);
-            solve(v, am[k].pm, gs[k]);
+            solve(v, gp0[k], am[k].pm, gs[k]);
             prof.end(gs[k], am[k].sb0, am[k].sf0);
             if (G == 2 && k == 0 && it == 0) {
                 MSDD_CUDA(cudaEventRecord(ev_off, gs[0]));        // the second half starts one solve later
@@ -192,7 +193,7 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
         const double fr = (double)active[k] / v.P;
         if (!fused || first) eig_form_rhs(v, ep.sigma, first, s);
         prof.begin(tag + "_solve", s);
-        solve(v, am[k].pm, s);
+        solve(v, gp0[k], am[k].pm, s);
         prof.end(s, am[k].solve_b * fr, am[k].solve_f * fr);
         if (offset) {
             MSDD_CUDA(cudaEventRecord(ev_off, s));
@@ -547,8 +548,6 @@ void Hierarchy::build_fine() {
     }
     const ProbBox* bx = d_fboxes.p;
     const LocalStencil* ls = &fst;
-    GevpBatch* fg = &fge;
-    cudaStream_t stream = st;
     double nav = 0;
     for (int j = 0; j < Pf; ++j) nav += nN[j];
     nav /= Pf;
@@ -556,7 +555,7 @@ void Hierarchy::build_fine() {
             [=](GevpBatch& v, int p0, const double* X, double* AX, double* BX, const int* skip, cudaStream_t s) {
                 apply_local(*ls, bx + p0, dim, v.K, X, AX, BX, v.ldx, block_p, skip, s);
             },
-            [=](GevpBatch& v, int pmax, cudaStream_t s) { tile_solve(v.K, v.W.p, v.ldx, pmax, v.done.p, s); },
+            [=](GevpBatch& v, int, int pmax, cudaStream_t s) { tile_solve(v.K, v.W.p, v.ldx, pmax, v.done.p, s); },
             [=](GevpBatch& v, int p0, const double* X, double* W, cudaStream_t s) {
                 apply_local_b32(*ls, bx + p0, dim, v.K, X, W, v.ldx, block_p, s);
             },
@@ -911,9 +910,6 @@ void Hierarchy::build_coarse() {
     const long long* dao = d_aoff.p;
     const int* dng = d_ngen.p;
     const int* dno = d_nown.p;
-    GevpBatch* mg = &mge;
-    int PmL = Pm;
-    cudaStream_t stream = st;
     std::vector<GemmItem> kitems(Pm);
     int pmax_m = 0;
     for (int i = 0; i < Pm; ++i) {
@@ -931,6 +927,9 @@ void Hierarchy::build_coarse() {
     }
     DevBuf<GemmItem> d_kitems = upload_vec(kitems, st);
     DevBuf<double> Wt(mge.W.n);
+    std::vector<long long> mrow(Pm + 1);            // first W element of each problem, and the end
+    for (int i = 0; i < Pm; ++i) mrow[i] = mge.K.roff[i] * mge.ldx;
+    mrow[Pm] = (long long)mge.K.total_rows * mge.ldx;
     const GemmItem* dki = d_kitems.p;
     const double* Kinv = K_m.p;
     double* Wtp = Wt.p;
@@ -942,9 +941,12 @@ void Hierarchy::build_coarse() {
                     apply_dense_pencil(Ab, dao + p0, dng + p0, dno + p0, v.K, X, AX, BX, v.ldx, block_p, skip, v.P,
                                        ngen_max, s);
                 },
-                [=](GevpBatch& v, int, cudaStream_t s) {
-                    gemm_batched(dki, PmL, 0, 0, 1.0, Kinv, v.W.p, 0.0, Wtp, ngen_max, pmax_m, s);
-                    MSDD_CUDA(cudaMemcpyAsync(v.W.p, Wtp, v.W.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                [=](GevpBatch& v, int p0, int, cudaStream_t s) {
+                    gemm_batched(dki + p0, v.P, 0, 0, 1.0, Kinv, v.W.p, 0.0, Wtp, ngen_max, pmax_m, s, nullptr,
+                                 v.done.p);
+                    const long long e0 = mrow[p0], e1 = mrow[p0 + v.P];
+                    MSDD_CUDA(cudaMemcpyAsync(v.W.p + e0, Wtp + e0, (e1 - e0) * sizeof(double),
+                                              cudaMemcpyDeviceToDevice, s));
                 },
                 [=](GevpBatch&, int, const double*, double*, cudaStream_t) {},
                 [=](GevpBatch&, int, cudaStream_t) {}, false, 0,
