@@ -971,13 +971,17 @@ __global__ void k_check_knorm(const double* __restrict__ partial, const double* 
 
 // ---- FP32 start phase: Euclidean CholQR of the block W (W = Q R, X <- Q).
 // G = W^T W with FP32 products, one CTA per problem.
-__global__ void __launch_bounds__(TPB) k_gram32(const double* __restrict__ W, double* __restrict__ G,
+// Partial Grams over `gsplit` row ranges of each problem (grid: problems x
+// splits), written to Gp[(i gsplit + s) PMAX^2]; k_cholqr sums them.
+__global__ void __launch_bounds__(TPB) k_gram32(const double* __restrict__ W, double* __restrict__ Gp,
                                                 const int* __restrict__ n_, const long long* __restrict__ roff_,
-                                                const int* __restrict__ p_, int ldx) {
+                                                const int* __restrict__ p_, int ldx, int gsplit) {
     __shared__ float sW[ROWBLK][LD];
-    const int i = blockIdx.x;
+    const int i = blockIdx.x, sp = blockIdx.y;
     const int n = n_[i], p = p_[i];
     const long long roff = roff_[i];
+    const int rows_per = (n + gsplit - 1) / gsplit;
+    const int r_lo = sp * rows_per, r_hi = min(n, r_lo + rows_per);
     const int npair = p * (p + 1) / 2;
     int pa[3], pb[3];
     float acc[3] = {0.f, 0.f, 0.f};
@@ -991,12 +995,12 @@ __global__ void __launch_bounds__(TPB) k_gram32(const double* __restrict__ W, do
             pb[q] = a + rem;
         }
     }
-    for (int r0 = 0; r0 < n; r0 += ROWBLK) {
+    for (int r0 = r_lo; r0 < r_hi; r0 += ROWBLK) {
         __syncthreads();
         for (int e = threadIdx.x; e < ROWBLK * p; e += TPB) {
             int rr = e / p, c = e % p;
             int r = r0 + rr;
-            sW[rr][c] = r < n ? (float)W[(roff + r) * ldx + c] : 0.f;
+            sW[rr][c] = r < r_hi ? f64_to_f32(W[(roff + r) * ldx + c]) : 0.f;
         }
         __syncthreads();
         for (int q = 0; q < 3; ++q) {
@@ -1007,10 +1011,11 @@ __global__ void __launch_bounds__(TPB) k_gram32(const double* __restrict__ W, do
             acc[q] += s;
         }
     }
+    double* G = Gp + ((long long)i * gsplit + sp) * PMAX * PMAX;
     for (int q = 0; q < 3; ++q) {
         if (pa[q] < 0) continue;
-        G[(long long)i * PMAX * PMAX + pa[q] * PMAX + pb[q]] = acc[q];
-        G[(long long)i * PMAX * PMAX + pb[q] * PMAX + pa[q]] = acc[q];
+        G[pa[q] * PMAX + pb[q]] = f32_to_f64(acc[q]);
+        G[pb[q] * PMAX + pa[q]] = f32_to_f64(acc[q]);
     }
 }
 
@@ -1018,21 +1023,30 @@ __global__ void __launch_bounds__(TPB) k_gram32(const double* __restrict__ W, do
 // warp per problem).  A column whose pivot falls below 1e-10 of its scaled
 // diagonal is dependent on the previous ones: it is reset to its scaled self
 // (R row e_k) so that the basis stays finite; the FP64 phase removes it.
-__global__ void k_cholqr(const double* __restrict__ G, double* __restrict__ C, const int* __restrict__ p_) {
+__global__ void k_cholqr(const double* __restrict__ Gp, int gsplit, double* __restrict__ C,
+                         const int* __restrict__ p_) {
     __shared__ double R[PMAX][LD], Ri[PMAX][LD], d[PMAX], d_inv[PMAX];
     const int i = blockIdx.x;
     const int p = p_[i];
     const int t = threadIdx.x;
-    const double* Gi = G + (long long)i * PMAX * PMAX;
+    const double* Gi = Gp + (long long)i * gsplit * PMAX * PMAX;
+    for (int e = t; e < PMAX * PMAX; e += 32) {       // G = sum of the row-range partials
+        int a = e / PMAX, b = e % PMAX;
+        double g = 0.0;
+        if (a < p && b < p)
+            for (int sp = 0; sp < gsplit; ++sp) g += Gi[(long long)sp * PMAX * PMAX + e];
+        R[a][b] = g;
+        Ri[a][b] = 0.0;
+    }
+    __syncwarp();
     if (t < PMAX) {
-        double g = t < p ? Gi[t * PMAX + t] : 0.0;
+        double g = t < p ? R[t][t] : 0.0;
         d[t] = g > 0.0 ? rsqrt_nr(g) : 0.0;
     }
     __syncwarp();
     for (int e = t; e < PMAX * PMAX; e += 32) {
         int a = e / PMAX, b = e % PMAX;
-        R[a][b] = (a < p && b < p) ? d[a] * Gi[a * PMAX + b] * d[b] : 0.0;
-        Ri[a][b] = 0.0;
+        R[a][b] = (a < p && b < p) ? d[a] * R[a][b] * d[b] : 0.0;
     }
     __syncwarp();
     // upper Cholesky in place: R <- U with D G D = U^T U
@@ -1078,11 +1092,11 @@ __global__ void __launch_bounds__(TPB) k_update32(const double* __restrict__ W, 
     if (r0 >= rows) return;
     const long long roff = roff_[i];
     const int t = threadIdx.x;
-    for (int e = t; e < p * p; e += TPB) sC[e / p][e % p] = (float)C[(long long)i * PMAX * PMAX + (e / p) * PMAX + e % p];
+    for (int e = t; e < p * p; e += TPB) sC[e / p][e % p] = f64_to_f32(C[(long long)i * PMAX * PMAX + (e / p) * PMAX + e % p]);
     for (int e = t; e < ROWBLK * p; e += TPB) {
         int rr = e / p, c = e % p;
         int r = r0 + rr;
-        sW[rr][c] = r < n ? (float)W[(roff + r) * ldx + c] : 0.f;
+        sW[rr][c] = r < n ? f64_to_f32(W[(roff + r) * ldx + c]) : 0.f;
     }
     __syncthreads();
     for (int e = t; e < ROWBLK * p; e += TPB) {
@@ -1090,7 +1104,7 @@ __global__ void __launch_bounds__(TPB) k_update32(const double* __restrict__ W, 
         if (r0 + rr >= rows) continue;
         float x = 0.f;
         for (int j = 0; j < p; ++j) x += sW[rr][j] * sC[j][c];
-        X[(roff + r0 + rr) * ldx + c] = (double)x;
+        X[(roff + r0 + rr) * ldx + c] = f32_to_f64(x);
     }
 }
 
@@ -1280,9 +1294,9 @@ void eig_check_knorm(GevpBatch& g, const EigParams& ep, int it, cudaStream_t s) 
 }
 
 void eig_cholqr32(GevpBatch& g, cudaStream_t s) {
-    k_gram32<<<g.P, TPB, 0, s>>>(g.W.p, g.H.p, g.K.d_n.p, g.K.d_roff.p, g.d_p.p, g.ldx);
+    k_gram32<<<dim3(g.P, g.gsplit), TPB, 0, s>>>(g.W.p, g.Hp.p, g.K.d_n.p, g.K.d_roff.p, g.d_p.p, g.ldx, g.gsplit);
     MSDD_LAUNCH_CHECK();
-    k_cholqr<<<g.P, 32, 0, s>>>(g.H.p, g.C.p, g.d_p.p);
+    k_cholqr<<<g.P, 32, 0, s>>>(g.Hp.p, g.gsplit, g.C.p, g.d_p.p);
     MSDD_LAUNCH_CHECK();
     dim3 grid(g.nblk_max, g.P);
     k_update32<<<grid, TPB, 0, s>>>(g.W.p, g.X.p, g.C.p, g.K.d_n.p, g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx);
