@@ -43,10 +43,13 @@ __global__ void k_form_rhs(double* __restrict__ W, const double* __restrict__ AX
                            const double* __restrict__ theta, const int* __restrict__ n_, const int* __restrict__ K_,
                            const long long* __restrict__ roff_, const int* __restrict__ p_, int ldx, double sigma,
                            int first, const int* __restrict__ done) {
+    __shared__ double smu[PMAX];                       // 1 / (theta + sigma): one division per column
     const int i = blockIdx.y;
     if (done[i]) return;
     const int n = n_[i], p = p_[i];
     const long long rows = (long long)K_[i] * NB;
+    if (threadIdx.x < p) smu[threadIdx.x] = first ? 0.0 : 1.0 / (theta[i * PMAX + threadIdx.x] + sigma);
+    __syncthreads();
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * ldx;
          e += (long long)gridDim.x * blockDim.x) {
         int r = (int)(e / ldx), c = (int)(e % ldx);
@@ -54,12 +57,7 @@ __global__ void k_form_rhs(double* __restrict__ W, const double* __restrict__ AX
         double v = 0.0;
         if (r < n && c < p) {
             double bx = BX[idx];
-            if (first) {
-                v = bx;
-            } else {
-                double mu = 1.0 / (theta[i * PMAX + c] + sigma);
-                v = bx - (AX[idx] + sigma * bx) * mu;
-            }
+            v = first ? bx : bx - (AX[idx] + sigma * bx) * smu[c];
         }
         W[idx] = v;
     }
@@ -69,19 +67,19 @@ __global__ void k_form_y(double* __restrict__ Y, const double* __restrict__ X, c
                          const double* __restrict__ theta, const int* __restrict__ n_, const int* __restrict__ K_,
                          const long long* __restrict__ roff_, const int* __restrict__ p_, int ldx, double sigma,
                          int first, const int* __restrict__ done) {
+    __shared__ double smu[PMAX];                       // 1 / (theta + sigma): one division per column
     const int i = blockIdx.y;
     if (done[i]) return;
     const int n = n_[i], p = p_[i];
     const long long rows = (long long)K_[i] * NB;
+    if (threadIdx.x < p) smu[threadIdx.x] = first ? 0.0 : 1.0 / (theta[i * PMAX + threadIdx.x] + sigma);
+    __syncthreads();
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * ldx;
          e += (long long)gridDim.x * blockDim.x) {
         int r = (int)(e / ldx), c = (int)(e % ldx);
         long long idx = (roff_[i] + r) * ldx + c;
         double v = 0.0;
-        if (r < n && c < p) {
-            v = W[idx];
-            if (!first) v += X[idx] / (theta[i * PMAX + c] + sigma);
-        }
+        if (r < n && c < p) v = first ? W[idx] : fma(X[idx], smu[c], W[idx]);
         Y[idx] = v;
     }
 }
@@ -96,13 +94,15 @@ __global__ void __launch_bounds__(TPB) k_form_y_knorm(double* __restrict__ Y, co
                                                       const long long* __restrict__ roff_, const int* __restrict__ p_,
                                                       int ldx, double sigma, double* __restrict__ partial,
                                                       int nblk_max, const int* __restrict__ done) {
-    __shared__ double red[ROWBLK][LD];
+    __shared__ double red[ROWBLK][LD], smu[PMAX];
     const int i = blockIdx.y, blk = blockIdx.x;
     if (done[i]) return;
     const int n = n_[i], p = p_[i];
     const long long rows = (long long)K_[i] * NB;
     const int r0 = blk * ROWBLK;
     if (r0 >= rows) return;
+    if (threadIdx.x < p) smu[threadIdx.x] = 1.0 / (theta[i * PMAX + threadIdx.x] + sigma);
+    __syncthreads();
     const long long roff = roff_[i];
     const int t = threadIdx.x;
     const int rr = t >> 3, cb = t & 7;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(TPB) k_form_y_knorm(double* __restrict__ Y, co
         if (r < rows && c < ldx) {
             long long idx = (roff + r) * ldx + c;
             if (r < n && c < p) {
-                double mu = 1.0 / (theta[i * PMAX + c] + sigma);
+                const double mu = smu[c];
                 double w = W[idx];
                 double bx = BX[idx];
                 double R = bx - (AX[idx] + sigma * bx) * mu;
