@@ -285,6 +285,172 @@ __device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_
 // rows contiguously across the warp, partial sums of the 4 warps are combined
 // in shared memory.  For band matrices (kb <= KBP) the tiles of step R+1 are
 // loaded into registers while step R computes.
+// ------------------------------------------------------------------ factor, FP32, half-bandwidth <= 2 tiles
+// The steps and the arithmetic of k_tile_factor<float> (same expressions in
+// the same order), arranged for latency: the tiles of the last three tile
+// rows (L, T and the pivots) stay in shared memory, so nothing the CTA
+// produced is read back from global memory; the original tiles of row R + 1
+// are copied with cp.async while row R is factored; the diagonal tiles are
+// factored and inverted by one warp holding a row per lane in registers
+// (shuffles instead of block barriers).
+constexpr int FB_T = 256, FB_LD = NB + 1, FB_ROWS = 3;
+constexpr size_t factor_band32_smem() {
+    return sizeof(float) * ((size_t)2 * FB_ROWS * NB2 + (size_t)FB_ROWS * FB_ROWS * NB * FB_LD + (size_t)NB * FB_LD +
+                            (size_t)2 * FB_ROWS * NB + NB) + 16;
+}
+
+__global__ void __launch_bounds__(FB_T) k_tile_factor_band32(
+    float* __restrict__ tiles, float* __restrict__ dinv, const int* __restrict__ n_, const int* __restrict__ kb_,
+    const int* __restrict__ K_, const long long* __restrict__ toff_, const long long* __restrict__ roff_,
+    int* __restrict__ status, int* __restrict__ nreg, double reg_tol)
+{
+    extern __shared__ __align__(16) float fb_sm[];
+    float* stg = fb_sm;                                                          // [2][3][32*32] original tiles
+    float (*cache)[NB][FB_LD] = reinterpret_cast<float (*)[NB][FB_LD]>(stg + 2 * FB_ROWS * NB2);  // [row%3 * 3 + d]
+    float (*Wsm)[FB_LD] = reinterpret_cast<float (*)[FB_LD]>(&cache[FB_ROWS * FB_ROWS][0][0]);
+    float* cpiv = &Wsm[NB][0];                                                   // [3][32] D = 1 / D^{-1}
+    float* cdinv = cpiv + FB_ROWS * NB;                                          // [3][32] D^{-1}
+    float* od = cdinv + FB_ROWS * NB;                                            // original diagonal
+    __shared__ int s_status, s_nreg;
+
+    const int i = blockIdx.x;
+    const int n = n_[i], kb = kb_[i], K = K_[i];
+    const long long toff = toff_[i], roff = roff_[i];
+    const int t = threadIdx.x;
+    const int r = t >> 3, c0 = t & 7;
+    if (t == 0) { s_status = 0; s_nreg = 0; }
+    auto issue_row = [&](int R) {
+        if (R < K) {
+            const int Cmin = R - kb > 0 ? R - kb : 0;
+            for (int C = Cmin; C <= R; ++C) {
+                const float* src = tiles + tile_index(toff, kb, R, C);
+                float* dst = stg + ((R & 1) * FB_ROWS + (R - C)) * NB2;
+                for (int ch = t; ch < NB2 / 4; ch += FB_T) cp_async16(dst + ch * 4, src + ch * 4);
+            }
+        }
+        cp_async_commit();
+    };
+    issue_row(0);
+    for (int R = 0; R < K; ++R) {
+        issue_row(R + 1);
+        cp_async_wait_n<1>();                       // row R landed (row R + 1 may be in flight)
+        __syncthreads();
+        const int Cmin = R - kb > 0 ? R - kb : 0;
+        const int rs = R % FB_ROWS;
+        for (int C = Cmin; C <= R; ++C) {
+            __syncthreads();                        // the previous step's cache and Wsm accesses are done
+            const float* A = stg + ((R & 1) * FB_ROWS + (R - C)) * NB2;
+            if (C == R && t < NB) od[t] = A[t * NB + t];
+            float acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = A[r * NB + c0 + 8 * q];
+            // W -= sum_J L_RJ D_J L_CJ^T
+            for (int J = Cmin; J < C; ++J) {
+                const float (*LR)[FB_LD] = cache[rs * FB_ROWS + (R - J)];
+                const float (*LC)[FB_LD] = cache[(C % FB_ROWS) * FB_ROWS + (C - J)];
+                const float* Dj = cpiv + (J % FB_ROWS) * NB;
+#pragma unroll 8
+                for (int k = 0; k < NB; ++k) {
+                    const float a = LR[r][k] * Dj[k];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] -= a * LC[c0 + 8 * q][k];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Wsm[r][c0 + 8 * q] = acc[q];
+            __syncthreads();
+            if (C < R) {
+                // L_RC = W T_C^T D_C^{-1}
+                const float (*TC)[FB_LD] = cache[(C % FB_ROWS) * FB_ROWS];
+                const float* dC = cdinv + (C % FB_ROWS) * NB;
+                float out[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+                for (int k = 0; k < NB; ++k) {
+                    const float w = Wsm[r][k];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) out[q] += w * TC[c0 + 8 * q][k];
+                }
+                float* dst = tiles + tile_index(toff, kb, R, C);
+                float (*Lc)[FB_LD] = cache[rs * FB_ROWS + (R - C)];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float v = out[q] * dC[c0 + 8 * q];
+                    Lc[r][c0 + 8 * q] = v;
+                    dst[r * NB + c0 + 8 * q] = v;
+                }
+            } else if (t < 32) {
+                // dense LDL^T of the diagonal tile by warp 0, lane a holding
+                // row a of W in registers (W[b][k] by shuffle from lane b);
+                // then T_R = L_RR^{-1}, lane a building row a of T
+                const int lane = t;
+                const int rows_valid = n - R * NB;
+                float row[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) row[b] = Wsm[lane][b];
+                float dl = 0.f;                     // D^{-1} of this lane's row
+                int nr = 0, st = 0;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const float d = __shfl_sync(0xffffffffu, row[k], k);
+                    float dinv_k;
+                    if (k >= rows_valid) {
+                        dinv_k = 1.f;
+                    } else if (reg_tol > 0.0 && !(d > (float)reg_tol * od[k])) {
+                        dinv_k = 0.f;
+                        ++nr;
+                    } else if (!(d > 0.f)) {
+                        dinv_k = 0.f;
+                        if (st == 0) st = R * NB + k + 1;
+                    } else {
+                        dinv_k = 1.f / d;
+                    }
+                    if (lane == k) dl = dinv_k;
+                    const float pinv = dinv_k;
+                    const float wak = row[k];
+                    // W[a][b] -= W[a][k] W[b][k] / d for k < b <= a
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (b > k) {
+                            const float wbk = __shfl_sync(0xffffffffu, wak, b);
+                            if (lane >= b) row[b] -= wak * wbk * pinv;
+                        }
+                    }
+                    if (lane > k) row[k] = (k >= rows_valid || lane >= rows_valid) ? 0.f : wak * pinv;
+                }
+                float tr[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) tr[b] = (b == lane) ? 1.f : 0.f;
+#pragma unroll
+                for (int k = 0; k < NB - 1; ++k) {
+                    const float lak = row[k];
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (b <= k) {
+                            const float tkb = __shfl_sync(0xffffffffu, tr[b], k);
+                            if (lane > k) tr[b] -= lak * tkb;
+                        }
+                    }
+                }
+                float* dst = tiles + tile_index(toff, kb, R, R);
+                float (*Tc)[FB_LD] = cache[rs * FB_ROWS];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    Tc[lane][b] = tr[b];
+                    dst[lane * NB + b] = tr[b];
+                }
+                cdinv[rs * NB + lane] = dl;
+                cpiv[rs * NB + lane] = dl != 0.f ? 1.f / dl : 0.f;
+                dinv[roff + (long long)R * NB + lane] = dl;
+                if (lane == 0) { s_nreg += nr; if (s_status == 0 && st != 0) s_status = st; }
+            }
+        }
+        __syncthreads();                            // row R complete before its stage is refilled
+    }
+    cp_async_wait_n<0>();
+    __syncthreads();
+    if (t == 0) { status[i] = s_status; nreg[i] = s_nreg; }
+}
+
 constexpr int S1T = 128;
 
 constexpr int S1_STAGES = 4;
@@ -1171,6 +1337,16 @@ void tile_identity(const TileBatch& tb, double* E, int lde, cudaStream_t s) {
 
 void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
     if (tb.P == 0) return;
+    int maxkb = 0;
+    for (int v : tb.kb) maxkb = std::max(maxkb, v);
+    if (tb.prec && maxkb <= 2) {
+        const size_t b = factor_band32_smem();
+        MSDD_CUDA(cudaFuncSetAttribute(k_tile_factor_band32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+        k_tile_factor_band32<<<tb.P, FB_T, b, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,
+                                                  tb.d_toff.p, tb.d_roff.p, tb.d_status.p, tb.d_nreg.p, reg_tol);
+        MSDD_LAUNCH_CHECK();
+        return;
+    }
     if (tb.prec)
         k_tile_factor<float><<<tb.P, TPB, 0, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,
                                                  tb.d_toff.p, tb.d_roff.p, tb.d_status.p, tb.d_nreg.p, reg_tol);
