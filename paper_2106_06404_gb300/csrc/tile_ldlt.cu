@@ -29,6 +29,58 @@ __device__ __forceinline__ void store_tile(T* __restrict__ dst, T (*src)[LDS]) {
 }
 
 // ------------------------------------------------------------------ factor
+// Dense LDL^T of the diagonal tile R held in W (lower triangle; rows >=
+// rows_valid are padding): pivots d with d <= reg_tol * od (the original
+// diagonal) are null pivots (D^{-1} = 0, counted in s_nreg), other
+// non-positive pivots set s_status to the first failing row + 1.  T_R =
+// L_RR^{-1} (unit lower) is built in Sa and stored to Tdst, D^{-1} to ddst.
+template <typename T>
+__device__ void factor_diag_tile(T (*W)[LDS], T (*Sa)[LDS], T* sd, const T* od, T& piv_inv, int rows_valid,
+                                 double reg_tol, int R, int& s_status, int& s_nreg, T* __restrict__ Tdst,
+                                 T* __restrict__ ddst) {
+    const int t = threadIdx.x;
+    for (int k = 0; k < NB; ++k) {
+        if (t == 0) {
+            T d = W[k][k];
+            T dinv_k;
+            if (k >= rows_valid) {
+                dinv_k = T(1);
+            } else if (reg_tol > 0.0 && !(d > T(reg_tol) * od[k])) {
+                dinv_k = T(0);
+                ++s_nreg;
+            } else if (!(d > T(0))) {
+                dinv_k = T(0);
+                if (s_status == 0) s_status = R * NB + k + 1;
+            } else {
+                dinv_k = T(1) / d;
+            }
+            piv_inv = dinv_k;
+            sd[k] = dinv_k;
+        }
+        __syncthreads();
+        const T pinv = piv_inv;
+        // trailing update W[a][b] -= W[a][k] W[b][k] / d for k < b <= a
+        for (int e = t; e < NB2; e += TPB) {
+            int a = e / NB, b = e % NB;
+            if (b > k && a >= b) W[a][b] -= W[a][k] * W[b][k] * pinv;
+        }
+        __syncthreads();
+        if (t > k && t < NB) W[t][k] = (k >= rows_valid || t >= rows_valid) ? T(0) : W[t][k] * pinv;
+        __syncthreads();
+    }
+    for (int e = t; e < NB2; e += TPB) Sa[e / NB][e % NB] = (e / NB == e % NB) ? T(1) : T(0);
+    __syncthreads();
+    for (int k = 0; k < NB - 1; ++k) {
+        for (int e = t; e < NB2; e += TPB) {
+            int a = e / NB, b = e % NB;
+            if (a > k && b <= k) Sa[a][b] -= W[a][k] * Sa[k][b];
+        }
+        __syncthreads();
+    }
+    store_tile(Tdst, Sa);
+    if (t < NB) ddst[t] = sd[t];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_tile_factor(
     T* __restrict__ tiles, T* __restrict__ dinv, const int* __restrict__ n_, const int* __restrict__ kb_,
@@ -98,49 +150,8 @@ __global__ void __launch_bounds__(TPB) k_tile_factor(
 #pragma unroll
                 for (int q = 0; q < 4; ++q) dst[r * NB + c0 + 8 * q] = out[q] * sd[c0 + 8 * q];
             } else {
-                // dense LDL^T of the diagonal tile (lower triangle of W)
-                const int rows_valid = n - R * NB;   // rows >= rows_valid are padding
-                for (int k = 0; k < NB; ++k) {
-                    if (t == 0) {
-                        T d = W[k][k];
-                        T dinv_k;
-                        if (k >= rows_valid) {
-                            dinv_k = T(1);
-                        } else if (reg_tol > 0.0 && !(d > T(reg_tol) * od[k])) {
-                            dinv_k = T(0);
-                            ++s_nreg;
-                        } else if (!(d > T(0))) {
-                            dinv_k = T(0);
-                            if (s_status == 0) s_status = R * NB + k + 1;
-                        } else {
-                            dinv_k = T(1) / d;
-                        }
-                        piv_inv = dinv_k;
-                        sd[k] = dinv_k;
-                    }
-                    __syncthreads();
-                    const T pinv = piv_inv;
-                    // trailing update W[a][b] -= W[a][k] W[b][k] / d for k < b <= a
-                    for (int e = t; e < NB2; e += TPB) {
-                        int a = e / NB, b = e % NB;
-                        if (b > k && a >= b) W[a][b] -= W[a][k] * W[b][k] * pinv;
-                    }
-                    __syncthreads();
-                    if (t > k && t < NB) W[t][k] = (k >= rows_valid || t >= rows_valid) ? T(0) : W[t][k] * pinv;
-                    __syncthreads();
-                }
-                // T_R = L_RR^{-1} (unit lower), built in Sa
-                for (int e = t; e < NB2; e += TPB) Sa[e / NB][e % NB] = (e / NB == e % NB) ? T(1) : T(0);
-                __syncthreads();
-                for (int k = 0; k < NB - 1; ++k) {
-                    for (int e = t; e < NB2; e += TPB) {
-                        int a = e / NB, b = e % NB;
-                        if (a > k && b <= k) Sa[a][b] -= W[a][k] * Sa[k][b];
-                    }
-                    __syncthreads();
-                }
-                store_tile(tiles + tile_index(toff, kb, R, R), Sa);
-                if (t < NB) dinv[roff + (long long)R * NB + t] = sd[t];
+                factor_diag_tile<T>(W, Sa, sd, od, piv_inv, n - R * NB, reg_tol, R, s_status, s_nreg,
+                                    tiles + tile_index(toff, kb, R, R), dinv + roff + (long long)R * NB);
             }
         }
     }
@@ -285,6 +296,126 @@ __device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_
 // rows contiguously across the warp, partial sums of the 4 warps are combined
 // in shared memory.  For band matrices (kb <= KBP) the tiles of step R+1 are
 // loaded into registers while step R computes.
+// ------------------------------------------------------------------ factor, dense, right-looking
+// Dense batches (kb >= K - 1: coarse-level matrices) are factored one tile
+// column k per launch triple, so that many CTAs share each step instead of
+// one CTA per matrix: the diagonal tile (one CTA per problem), the panel
+// L_ik = A_ik T_k^T D_k^{-1} (one CTA per tile), and the trailing update
+// A_ij -= L_ik D_k L_jk^T for k < j <= i (one CTA per tile).  Every tile sees
+// the subtractions of k_tile_factor in the same order and in the same
+// precision, so the factors are the same.  k_save_diag first parks the
+// original diagonal (the null-pivot reference) in dinv and clears the status.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_save_diag(const T* __restrict__ tiles, T* __restrict__ dinv,
+                                                   const int* __restrict__ kb_, const int* __restrict__ K_,
+                                                   const long long* __restrict__ toff_,
+                                                   const long long* __restrict__ roff_, int* __restrict__ status,
+                                                   int* __restrict__ nreg) {
+    const int i = blockIdx.x;
+    const int kb = kb_[i], K = K_[i];
+    const long long toff = toff_[i], roff = roff_[i];
+    for (int e = threadIdx.x; e < K * NB; e += TPB) {
+        const int R = e / NB, r = e % NB;
+        dinv[roff + e] = tiles[tile_index(toff, kb, R, R) + r * NB + r];
+    }
+    if (threadIdx.x == 0) { status[i] = 0; nreg[i] = 0; }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rl_diag(T* __restrict__ tiles, T* __restrict__ dinv,
+                                                 const int* __restrict__ n_, const int* __restrict__ kb_,
+                                                 const int* __restrict__ K_, const long long* __restrict__ toff_,
+                                                 const long long* __restrict__ roff_, int* __restrict__ status,
+                                                 int* __restrict__ nreg, double reg_tol, int k) {
+    __shared__ T W[NB][LDS];
+    __shared__ T Sa[NB][LDS];
+    __shared__ T sd[NB];
+    __shared__ T od[NB];
+    __shared__ T piv_inv;
+    __shared__ int s_status, s_nreg;
+    const int i = blockIdx.x;
+    const int K = K_[i];
+    if (k >= K) return;
+    const int kb = kb_[i], t = threadIdx.x;
+    const long long toff = toff_[i], roff = roff_[i];
+    if (t == 0) { s_status = status[i]; s_nreg = nreg[i]; }
+    load_tile(W, tiles + tile_index(toff, kb, k, k));
+    if (t < NB) od[t] = dinv[roff + (long long)k * NB + t];
+    __syncthreads();
+    factor_diag_tile<T>(W, Sa, sd, od, piv_inv, n_[i] - k * NB, reg_tol, k, s_status, s_nreg,
+                        tiles + tile_index(toff, kb, k, k), dinv + roff + (long long)k * NB);
+    __syncthreads();
+    if (t == 0) { status[i] = s_status; nreg[i] = s_nreg; }
+}
+
+// grid.y: i = k + 1 + blockIdx.y
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rl_panel(T* __restrict__ tiles, const T* __restrict__ dinv,
+                                                  const int* __restrict__ kb_, const int* __restrict__ K_,
+                                                  const long long* __restrict__ toff_,
+                                                  const long long* __restrict__ roff_, int k) {
+    __shared__ T W[NB][LDS];
+    __shared__ T Sb[NB][LDS];
+    __shared__ T sd[NB];
+    const int i = blockIdx.x, R = k + 1 + blockIdx.y;
+    const int K = K_[i];
+    if (R >= K) return;
+    const int kb = kb_[i], t = threadIdx.x, r = t >> 3, c0 = t & 7;
+    const long long toff = toff_[i], roff = roff_[i];
+    T* dst = tiles + tile_index(toff, kb, R, k);
+    load_tile(W, dst);
+    load_tile(Sb, tiles + tile_index(toff, kb, k, k));
+    if (t < NB) sd[t] = dinv[roff + (long long)k * NB + t];
+    __syncthreads();
+    T out[4] = {0, 0, 0, 0};
+#pragma unroll 8
+    for (int kk = 0; kk < NB; ++kk) {
+        T w = W[r][kk];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] += w * Sb[c0 + 8 * q][kk];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[r * NB + c0 + 8 * q] = out[q] * sd[c0 + 8 * q];
+}
+
+// grid.y enumerates the tiles (i, j), k < j <= i < K, row by row
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rl_update(T* __restrict__ tiles, const T* __restrict__ dinv,
+                                                   const int* __restrict__ kb_, const int* __restrict__ K_,
+                                                   const long long* __restrict__ toff_,
+                                                   const long long* __restrict__ roff_, int k) {
+    __shared__ T Sa[NB][LDS];
+    __shared__ T Sb[NB][LDS];
+    __shared__ T sd[NB];
+    const int i = blockIdx.x;
+    const int K = K_[i];
+    int e = blockIdx.y, R = k + 1;
+    while (R < K && e >= R - k) { e -= R - k; ++R; }
+    if (R >= K) return;
+    const int C = k + 1 + e;
+    const int kb = kb_[i], t = threadIdx.x, r = t >> 3, c0 = t & 7;
+    const long long toff = toff_[i], roff = roff_[i];
+    T* dst = tiles + tile_index(toff, kb, R, C);
+    T acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = dst[r * NB + c0 + 8 * q];
+    load_tile(Sa, tiles + tile_index(toff, kb, R, k));
+    load_tile(Sb, tiles + tile_index(toff, kb, C, k));
+    if (t < NB) {
+        T di = dinv[roff + (long long)k * NB + t];
+        sd[t] = di != T(0) ? T(1) / di : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < NB; ++kk) {
+        T a = Sa[r][kk] * sd[kk];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] -= a * Sb[c0 + 8 * q][kk];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[r * NB + c0 + 8 * q] = acc[q];
+}
+
 // ------------------------------------------------------------------ factor, FP32, half-bandwidth <= 2 tiles
 // The steps and the arithmetic of k_tile_factor<float> (same expressions in
 // the same order), arranged for latency: the tiles of the last three tile
@@ -1339,6 +1470,31 @@ void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
     if (tb.P == 0) return;
     int maxkb = 0;
     for (int v : tb.kb) maxkb = std::max(maxkb, v);
+    bool dense = tb.max_K >= 3;
+    for (int i = 0; i < tb.P && dense; ++i) dense = tb.kb[i] >= tb.K[i] - 1;
+    if (dense) {
+        auto run = [&](auto* tl, auto* dv) {
+            using T = std::remove_pointer_t<decltype(tl)>;
+            k_save_diag<T><<<tb.P, TPB, 0, s>>>(tl, dv, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, tb.d_status.p,
+                                               tb.d_nreg.p);
+            MSDD_LAUNCH_CHECK();
+            for (int k = 0; k < tb.max_K; ++k) {
+                k_rl_diag<T><<<tb.P, TPB, 0, s>>>(tl, dv, tb.d_n.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p,
+                                                 tb.d_status.p, tb.d_nreg.p, reg_tol, k);
+                MSDD_LAUNCH_CHECK();
+                const int m = tb.max_K - 1 - k;
+                if (m == 0) break;
+                k_rl_panel<T><<<dim3(tb.P, m), TPB, 0, s>>>(tl, dv, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, k);
+                MSDD_LAUNCH_CHECK();
+                k_rl_update<T><<<dim3(tb.P, m * (m + 1) / 2), TPB, 0, s>>>(tl, dv, tb.d_kb.p, tb.d_K.p, tb.d_toff.p,
+                                                                         tb.d_roff.p, k);
+                MSDD_LAUNCH_CHECK();
+            }
+        };
+        if (tb.prec) run(tb.tiles_f.p, tb.dinv_f.p);
+        else run(tb.tiles_d.p, tb.dinv_d.p);
+        return;
+    }
     if (tb.prec && maxkb <= 2) {
         const size_t b = factor_band32_smem();
         MSDD_CUDA(cudaFuncSetAttribute(k_tile_factor_band32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
