@@ -207,6 +207,20 @@ msdd_status msdd_get_fine_basis(const msdd_hierarchy* h, int subdomain, double* 
 
 void msdd_destroy(msdd_hierarchy* h);
 
+/* ---- device memory -------------------------------------------------------
+ * Device buffers come from a process-wide cache, not from one cudaMalloc and
+ * cudaFree each: a buffer released inside a call (or by msdd_destroy /
+ * msdd_band_destroy) is parked, and at the end of that call the device is
+ * synchronised once and parked blocks become reusable by later allocations
+ * of the same rounded size (512 bytes).  A sequence of set-ups of the same
+ * size thus allocates nothing after the first, and no block is reused while
+ * a kernel launched before its release can still read it.  The cache keeps
+ * its memory until msdd_release_cache, which synchronises the device and
+ * returns every cached block to the driver (an allocation that fails also
+ * releases the cache and retries once).  msdd_cached_bytes: bytes held. */
+msdd_status msdd_release_cache(void);
+long long msdd_cached_bytes(void);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (a replayed CUDA graph counts the kernels it holds).  Not thread-safe. */
 long long msdd_kernel_launches(void);

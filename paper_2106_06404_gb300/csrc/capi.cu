@@ -29,7 +29,7 @@ msdd_status msdd::set_last_error(msdd_status s, const std::string& msg) { return
 namespace {
 
 template <class F>
-msdd_status guarded(F&& f) {
+msdd_status guarded_call(F&& f) {
     try {
         g_last_error.clear();
         return f();
@@ -44,6 +44,15 @@ msdd_status guarded(F&& f) {
     } catch (const std::exception& e) {
         return fail(MSDD_ERR_CUDA, e.what());
     }
+}
+
+// every entry point: blocks released during the call become reusable
+// (device synchronised once, only if the call released any)
+template <class F>
+msdd_status guarded(F&& f) {
+    const msdd_status st = guarded_call(std::forward<F>(f));
+    msdd::dev_cache_collect();
+    return st;
 }
 
 bool mesh_ok(const msdd_mesh* m) {
@@ -299,7 +308,19 @@ msdd_status msdd_get_fine_basis(const msdd_hierarchy* h, int subdomain, double* 
     });
 }
 
-void msdd_destroy(msdd_hierarchy* h) { delete h; }
+void msdd_destroy(msdd_hierarchy* h) {
+    delete h;
+    msdd::dev_cache_collect();
+}
+
+msdd_status msdd_release_cache(void) {
+    return guarded([&]() -> msdd_status {
+        msdd::dev_cache_trim();
+        return MSDD_OK;
+    });
+}
+
+long long msdd_cached_bytes(void) { return (long long)msdd::dev_cache_bytes(); }
 
 long long msdd_kernel_launches(void) { return msdd::kernel_launch_counter(); }
 
@@ -380,7 +401,10 @@ msdd_status msdd_band_solve(const msdd_band_batch* bb, int nrhs, double* X, void
     });
 }
 
-void msdd_band_destroy(msdd_band_batch* bb) { delete bb; }
+void msdd_band_destroy(msdd_band_batch* bb) {
+    delete bb;
+    msdd::dev_cache_collect();
+}
 
 // ---- learned warm start
 msdd_status msdd_fine_layout(const msdd_mesh* mesh, const msdd_decomp* decomp, int* out, int cap, int* count) {

@@ -42,7 +42,18 @@ long long& kernel_launch_counter();
         MSDD_CUDA(cudaGetLastError());      \
     } while (0)
 
-// Device buffer (cudaMalloc / cudaFree), move-only; borrow() makes a
+// Caching device allocator (devcache.cu): dev_cache_release parks a block
+// until the next dev_cache_collect, which synchronises the device once and
+// makes parked blocks reusable by dev_cache_alloc of the same rounded size;
+// dev_cache_trim returns everything to the driver.  The C API collects at
+// the end of every call that released memory.
+void* dev_cache_alloc(size_t bytes);
+void dev_cache_release(void* p, size_t bytes);
+void dev_cache_collect();
+void dev_cache_trim();
+size_t dev_cache_bytes();
+
+// Device buffer (caching allocator above), move-only; borrow() makes a
 // non-owning view of another buffer's memory (never freed by the view).
 template <typename T>
 struct DevBuf {
@@ -74,11 +85,11 @@ struct DevBuf {
     DevBuf view(size_t off, size_t count) const { return borrow(p ? p + off : nullptr, count); }
     void alloc(size_t count) {
         release();
+        if (count) p = static_cast<T*>(dev_cache_alloc(count * sizeof(T)));
         n = count;
-        if (count) MSDD_CUDA(cudaMalloc(&p, count * sizeof(T)));
     }
     void release() {
-        if (p && owned) cudaFree(p);
+        if (p && owned) dev_cache_release(p, n * sizeof(T));
         p = nullptr;
         n = 0;
         owned = true;

@@ -75,7 +75,7 @@ EXPORTED = [
     "msdd_get_eigenvalues", "msdd_get_eigen_residuals", "msdd_get_fine_basis", "msdd_destroy", "msdd_last_error",
     "msdd_band_factor", "msdd_band_solve", "msdd_band_destroy", "msdd_band_solve_noalloc", "msdd_kernel_launches",
     "msdd_fine_layout", "msdd_nn_patches", "msdd_nn_workspace_bytes", "msdd_nn_forward", "msdd_nn_loss_grad",
-    "msdd_nn_adam", "msdd_nn_start_vectors", "msdd_nn_targets",
+    "msdd_nn_adam", "msdd_nn_start_vectors", "msdd_nn_targets", "msdd_release_cache", "msdd_cached_bytes",
 ]
 
 # learned warm start (include/msdd.h, MSDD_NN_*)
@@ -120,6 +120,9 @@ def load(path=LIB_PATH):
     lib.msdd_band_destroy.restype = None
     lib.msdd_kernel_launches.argtypes = []
     lib.msdd_kernel_launches.restype = ctypes.c_longlong
+    lib.msdd_release_cache.argtypes = []
+    lib.msdd_cached_bytes.argtypes = []
+    lib.msdd_cached_bytes.restype = ctypes.c_longlong
     lib.msdd_fine_layout.argtypes = [P(Mesh), P(Decomp), ip, ctypes.c_int, ip]
     lib.msdd_nn_patches.argtypes = [P(Mesh), P(Coeff), P(Decomp), vp, vp]
     lib.msdd_nn_workspace_bytes.argtypes = [ctypes.c_int]
@@ -131,7 +134,7 @@ def load(path=LIB_PATH):
     lib.msdd_nn_targets.argtypes = [vp, vp, vp, vp]
     for name in EXPORTED:
         if name in ("msdd_last_error", "msdd_destroy", "msdd_band_destroy", "msdd_num_unknowns",
-                    "msdd_kernel_launches", "msdd_nn_workspace_bytes"):
+                    "msdd_kernel_launches", "msdd_nn_workspace_bytes", "msdd_cached_bytes"):
             continue
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -180,6 +183,16 @@ def assemble_rhs(n, dirichlet_faces=0b1, f=1.0):
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(load().msdd_kernel_launches())
+
+
+def release_cache():
+    """msdd_release_cache: return the library's cached device blocks to the driver."""
+    _check(load().msdd_release_cache())
+
+
+def cached_bytes():
+    """msdd_cached_bytes: device bytes held by the library's allocation cache."""
+    return int(load().msdd_cached_bytes())
 
 
 def default_options():
