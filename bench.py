@@ -361,7 +361,7 @@ def run_ours(args, rank, world, local_rank):
         "step_seconds": [round(t, 6) for t in t_chosen],
         "setup_ms": round(st_chosen["setup_ms"], 3),
         "solve_ms": round(st_chosen["solve_ms"], 3),
-        "phase_ms": [round(v, 3) for v in st_chosen["phase_ms"][:7]],
+        "phase_ms": [round(v, 3) for v in st_chosen["phase_ms"][:8]],
         "level_dim": st_chosen["level_dim"],
         "eig_iters_max": st_chosen["eig_iters_max"],
         "plain_fp64": None if t_plain is None else {

@@ -140,7 +140,8 @@ typedef struct msdd_stats {
                                                  enqueue it: it runs on a side stream beside
                                                  phases 2-5), 2 shifted Neumann factor, 3 fine
                                                  eigensolve, 4 coarse Galerkin, 5 coarse
-                                                 eigensolve, 6 coarse factors */
+                                                 eigensolve, 6 coarse factors, 7 capture and
+                                                 instantiation of the CG graph (first solve) */
     int pcg_iterations;                       /* of the last solve */
     double pcg_rel_residual;                  /* recursive residual / ||b|| */
     double solve_ms;
@@ -217,7 +218,8 @@ void msdd_destroy(msdd_hierarchy* h);
  * a kernel launched before its release can still read it.  The cache keeps
  * its memory until msdd_release_cache, which synchronises the device and
  * returns every cached block to the driver (an allocation that fails also
- * releases the cache and retries once).  msdd_cached_bytes: bytes held. */
+ * releases the cache and retries once).  A hierarchy's 4 KiB pinned host
+ * scratch follows the same rules.  msdd_cached_bytes: device bytes held. */
 msdd_status msdd_release_cache(void);
 long long msdd_cached_bytes(void);
 

@@ -52,6 +52,9 @@ void dev_cache_release(void* p, size_t bytes);
 void dev_cache_collect();
 void dev_cache_trim();
 size_t dev_cache_bytes();
+// pinned host blocks, same rules (released blocks reusable after a collect)
+void* pinned_cache_alloc(size_t bytes);
+void pinned_cache_release(void* p, size_t bytes);
 
 // Device buffer (caching allocator above), move-only; borrow() makes a
 // non-owning view of another buffer's memory (never freed by the view).

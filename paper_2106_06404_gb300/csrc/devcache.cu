@@ -23,6 +23,9 @@ struct Cache {
     std::map<std::pair<int, size_t>, std::vector<void*>> free_blocks;   // (device, rounded bytes)
     std::vector<std::pair<std::pair<int, size_t>, void*>> pending;
     size_t held = 0;                                                     // bytes in both lists
+    // pinned host blocks: same rules (device -1)
+    std::map<size_t, std::vector<void*>> free_host;
+    std::vector<std::pair<size_t, void*>> pending_host;
 };
 
 Cache& cache() {
@@ -74,16 +77,43 @@ void dev_cache_release(void* p, size_t bytes) {
     c.held += r;
 }
 
+void* pinned_cache_alloc(size_t bytes) {
+    const size_t r = rounded(bytes);
+    Cache& c = cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.free_host.find(r);
+        if (it != c.free_host.end() && !it->second.empty()) {
+            void* p = it->second.back();
+            it->second.pop_back();
+            return p;
+        }
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaHostAlloc(&p, r, cudaHostAllocDefault);
+    if (e != cudaSuccess) throw CudaError(std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
+    return p;
+}
+
+void pinned_cache_release(void* p, size_t bytes) {
+    if (!p) return;
+    Cache& c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.pending_host.push_back({rounded(bytes), p});
+}
+
 void dev_cache_collect() {
     Cache& c = cache();
     {
         std::lock_guard<std::mutex> lk(c.mu);
-        if (c.pending.empty()) return;
+        if (c.pending.empty() && c.pending_host.empty()) return;
     }
     cudaDeviceSynchronize();
     std::lock_guard<std::mutex> lk(c.mu);
     for (auto& e : c.pending) c.free_blocks[e.first].push_back(e.second);
     c.pending.clear();
+    for (auto& e : c.pending_host) c.free_host[e.first].push_back(e.second);
+    c.pending_host.clear();
 }
 
 void dev_cache_trim() {
@@ -96,6 +126,11 @@ void dev_cache_trim() {
         for (void* p : kv.second) cudaFree(p);
     c.free_blocks.clear();
     c.held = 0;
+    for (auto& e : c.pending_host) c.free_host[e.first].push_back(e.second);
+    c.pending_host.clear();
+    for (auto& kv : c.free_host)
+        for (void* p : kv.second) cudaFreeHost(p);
+    c.free_host.clear();
 }
 
 size_t dev_cache_bytes() {

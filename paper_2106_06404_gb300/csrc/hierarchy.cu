@@ -116,8 +116,8 @@ void dense_inverse(const TileBatch& tb, double* out, const std::vector<long long
 template <class Apply, class Solve, class BApply32, class ApplyRhs>
 void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply32 bapply32, ApplyRhs apply_rhs,
              bool fused, int fp32_iters, cudaStream_t st, cudaStream_t st_b, Prof& prof, const std::string& tag,
-             double apply_bytes, double apply_flops, const double* start = nullptr, int start_cols = 0,
-             const long long* d_start_off = nullptr, int groups = 1) {
+             double apply_bytes, double apply_flops, int* h_act, const double* start = nullptr,
+             int start_cols = 0, const long long* d_start_off = nullptr, int groups = 1) {
     if (g.P == 0) return;
     eig_init(g, ep.seed, st);
     eig_load_start(g, start, start_cols, d_start_off, st);
@@ -143,8 +143,6 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
     MSDD_CUDA(cudaEventCreateWithFlags(&ev_end, cudaEventDisableTiming));
     MSDD_CUDA(cudaEventRecord(ev_start, st));
     for (int k = 1; k < G; ++k) MSDD_CUDA(cudaStreamWaitEvent(gs[k], ev_start, 0));
-    int* h_act = nullptr;
-    MSDD_CUDA(cudaHostAlloc(&h_act, 2 * sizeof(int), cudaHostAllocDefault));
     struct Amounts { int pm = 0; double sb0 = 0, sf0 = 0, solve_b = 0, solve_f = 0, vec_n = 0; };
     std::vector<Amounts> am(G);
     for (int k = 0; k < G; ++k) {
@@ -262,7 +260,6 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
         MSDD_CUDA(cudaStreamWaitEvent(st, ev_end, 0));
     }
     MSDD_CUDA(cudaStreamSynchronize(st));
-    cudaFreeHost(h_act);
     cudaEventDestroy(ev_start);
     cudaEventDestroy(ev_off);
     cudaEventDestroy(ev_end);
@@ -291,6 +288,9 @@ Hierarchy::~Hierarchy() {
         cudaStreamDestroy(st3);
     }
     if (ev_dir) cudaEventDestroy(ev_dir);
+    for (cudaEvent_t& e : ev_chunk)
+        if (e) cudaEventDestroy(e);
+    pinned_cache_release(pinned, 4096);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (own_stream && st) {
@@ -379,6 +379,9 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     MSDD_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
     MSDD_CUDA(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
     MSDD_CUDA(cudaEventCreateWithFlags(&ev_dir, cudaEventDisableTiming));
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_chunk[0], cudaEventDisableTiming));
+    MSDD_CUDA(cudaEventCreateWithFlags(&ev_chunk[1], cudaEventDisableTiming));
+    pinned = pinned_cache_alloc(4096);
     MSDD_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
     MSDD_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     levels = dec.levels;
@@ -565,7 +568,7 @@ void Hierarchy::build_fine() {
             },
             true, opt.precision == 1 ? opt.fp32_start_iters : 0,
             st, st2, prof, "fine_gevp", nav * (3.0 * block_p * 8.0 + 8.0), nav * block_p * 2.0 * 2.0 * (dim == 3 ? 27 : 9),
-            opt.warm_start, opt.warm_start ? opt.warm_cols : 0, d_woff.p, Pf >= 64 ? 2 : 1);
+            static_cast<int*>(pinned), opt.warm_start, opt.warm_start ? opt.warm_cols : 0, d_woff.p, Pf >= 64 ? 2 : 1);
     fm = fge.m.download(st);
     {
         std::vector<int> it = fge.iters.download(st), dn = fge.done.download(st);
@@ -950,7 +953,8 @@ void Hierarchy::build_coarse() {
                 },
                 [=](GevpBatch&, int, const double*, double*, cudaStream_t) {},
                 [=](GevpBatch&, int, cudaStream_t) {}, false, 0,
-                st, nullptr, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p);
+                st, nullptr, prof, "coarse_gevp", (double)ngen_max * ngen_max * 8.0, 2.0 * ngen_max * ngen_max * block_p,
+                static_cast<int*>(pinned));
         mm = mge.m.download(st);
         {
             std::vector<int> it = mge.iters.download(st), dn = mge.done.download(st);
@@ -1165,7 +1169,10 @@ void Hierarchy::build_graph() {
 
 int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, double* relres) {
     auto t0 = Clock::now();
-    if (!graph) build_graph();
+    if (!graph) {
+        build_graph();
+        stats.phase_ms[7] = ms_since(t0);
+    }
     pcg_start(b, x.p, r.p, nun, partial.p, nblocks, st);
     pcg_fin_bb(sc.p, partial.p, nblocks, tol, maxit, st);
     apply_prec(r.p, z.p, &sc.p->done);
@@ -1182,22 +1189,37 @@ int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, doubl
         }
         it_flops += 2.0 * (g.dim == 3 ? 27 : 9) * nun + 10.0 * nun;
     }
-    int prev_iters = 0;
-    for (;;) {
+    // graph chunks are launched one ahead of the convergence check, so the
+    // GPU never waits for the host; a chunk launched after convergence finds
+    // the done flag set and its kernels return at once
+    PcgScalars* hsc = reinterpret_cast<PcgScalars*>(static_cast<char*>(pinned) + 1024);
+    auto launch_chunk = [&](int slot) {
         prof.begin("pcg_iterations", st);
         MSDD_CUDA(cudaGraphLaunch(graph, st));
         kernel_launch_counter() += graph_kernels;
         prof.end(st, 0.0, 0.0);
-        MSDD_CUDA(cudaMemcpyAsync(&hs, sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
-        MSDD_CUDA(cudaStreamSynchronize(st));
+        MSDD_CUDA(cudaMemcpyAsync(&hsc[slot], sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+        MSDD_CUDA(cudaEventRecord(ev_chunk[slot], st));
+    };
+    launch_chunk(0);
+    launch_chunk(1);
+    int prev_iters = 0;
+    for (int k = 0;; ++k) {
+        const int slot = k & 1;
+        MSDD_CUDA(cudaEventSynchronize(ev_chunk[slot]));
+        hs = hsc[slot];
         if (prof.on) {
-            int done_it = hs.iters - prev_iters;
-            prof.pend.back().bytes = it_bytes * done_it;
-            prof.pend.back().flops = it_flops * done_it;
+            // the profiled interval of chunk k is the (k+1)-th pending entry
+            Prof::Pending& pe = prof.pend[prof.pend.size() - 2];
+            const int done_it = hs.iters - prev_iters;
+            pe.bytes = it_bytes * done_it;
+            pe.flops = it_flops * done_it;
             prev_iters = hs.iters;
         }
         if (hs.done) break;
+        launch_chunk(slot);
     }
+    MSDD_CUDA(cudaStreamSynchronize(st));
     prof.collect();
     MSDD_CUDA(cudaMemcpyAsync(xout, x.p, nun * sizeof(double), cudaMemcpyDeviceToDevice, st));
     MSDD_CUDA(cudaStreamSynchronize(st));

@@ -89,6 +89,8 @@ struct Hierarchy {
     cudaStream_t st2 = nullptr;        // coarse chain of the preconditioner
     cudaStream_t st3 = nullptr;        // set-up side stream: fine Dirichlet factors
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dir = nullptr;
+    cudaEvent_t ev_chunk[2] = {nullptr, nullptr};   // PCG: completion of the last two graph launches
+    void* pinned = nullptr;            // 4 KiB pinned host scratch: eigensolver flags, PCG scalars
     int levels = 0, L = 0;
     long long nun = 0;
     msdd_stats stats{};
