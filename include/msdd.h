@@ -96,7 +96,9 @@ typedef struct msdd_options {
                             and 1e-6 in 3D; must be < 1 */
     unsigned long long seed;  /* start vectors of the subspace iteration */
     void* stream;        /* cudaStream_t */
-    int profile;         /* 1: time kernel families with CUDA events (see msdd_stats.prof) */
+    int profile;         /* 1: time every kernel family with CUDA events (see msdd_stats.prof);
+                            2: only the band-solve families (*_solve): two events per band solve
+                            instead of ~500 intervals per set-up, for timing runs */
     int fp32_start_iters;/* precision 1: fine-level FP32 subspace iterations (FP32 B apply and
                             solve, Euclidean CholQR) before the FP64 iterations (default 20) */
     const double* warm_start; /* device, may be NULL (default): start vectors of the fine-level

@@ -55,6 +55,9 @@ size_t dev_cache_bytes();
 // pinned host blocks, same rules (released blocks reusable after a collect)
 void* pinned_cache_alloc(size_t bytes);
 void pinned_cache_release(void* p, size_t bytes);
+// CUDA events with timing, reused (put back only after they completed)
+cudaEvent_t timing_event_get();
+void timing_event_put(cudaEvent_t e);
 
 // Device buffer (caching allocator above), move-only; borrow() makes a
 // non-owning view of another buffer's memory (never freed by the view).

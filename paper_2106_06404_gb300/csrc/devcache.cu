@@ -26,6 +26,7 @@ struct Cache {
     // pinned host blocks: same rules (device -1)
     std::map<size_t, std::vector<void*>> free_host;
     std::vector<std::pair<size_t, void*>> pending_host;
+    std::vector<cudaEvent_t> events;                                     // completed timing events
 };
 
 Cache& cache() {
@@ -131,6 +132,30 @@ void dev_cache_trim() {
     for (auto& kv : c.free_host)
         for (void* p : kv.second) cudaFreeHost(p);
     c.free_host.clear();
+}
+
+// timing events (default flags), reused across profiled intervals and hierarchies
+cudaEvent_t timing_event_get() {
+    Cache& c = cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        if (!c.events.empty()) {
+            cudaEvent_t e = c.events.back();
+            c.events.pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    const cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) throw CudaError(std::string("cudaEventCreate: ") + cudaGetErrorString(r));
+    return e;
+}
+
+void timing_event_put(cudaEvent_t e) {
+    if (!e) return;
+    Cache& c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.events.push_back(e);
 }
 
 size_t dev_cache_bytes() {

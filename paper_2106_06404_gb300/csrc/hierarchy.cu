@@ -387,6 +387,7 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     levels = dec.levels;
     L = levels - 1;
     prof.on = opt.profile != 0;
+    prof.solves_only = opt.profile == 2;
     g = make_geom(mesh, coeff);
     nun = (long long)g.ushape[0] * g.ushape[1] * g.ushape[2];
     upload_reference(g);
@@ -1208,7 +1209,7 @@ int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, doubl
         const int slot = k & 1;
         MSDD_CUDA(cudaEventSynchronize(ev_chunk[slot]));
         hs = hsc[slot];
-        if (prof.on) {
+        if (prof.on && prof.pend.size() >= 2) {
             // the profiled interval of chunk k is the (k+1)-th pending entry
             Prof::Pending& pe = prof.pend[prof.pend.size() - 2];
             const int done_it = hs.iters - prev_iters;

@@ -21,6 +21,8 @@ struct MsddError : std::runtime_error {
 // recorded with each launch are algorithmic amounts computed on the host.
 struct Prof {
     bool on = false;
+    bool solves_only = false;      // level 2: families whose name ends in "_solve"
+    bool skipped = false;          // the open interval was not recorded
     struct Fam {
         std::string name;
         int launches = 0;
@@ -41,14 +43,14 @@ struct Prof {
     }
     void begin(const std::string& name, cudaStream_t s) {
         if (!on) return;
-        Pending p{family(name), nullptr, nullptr, 0, 0};
-        MSDD_CUDA(cudaEventCreate(&p.a));
-        MSDD_CUDA(cudaEventCreate(&p.b));
+        skipped = solves_only && !(name.size() >= 6 && name.compare(name.size() - 6, 6, "_solve") == 0);
+        if (skipped) return;
+        Pending p{family(name), timing_event_get(), timing_event_get(), 0, 0};
         MSDD_CUDA(cudaEventRecord(p.a, s));
         pend.push_back(p);
     }
     void end(cudaStream_t s, double bytes, double flops) {
-        if (!on) return;
+        if (!on || skipped) return;
         Pending& p = pend.back();
         p.bytes = bytes;
         p.flops = flops;
@@ -64,8 +66,8 @@ struct Prof {
             f.ms += ms;
             f.bytes += p.bytes;
             f.flops += p.flops;
-            cudaEventDestroy(p.a);
-            cudaEventDestroy(p.b);
+            timing_event_put(p.a);
+            timing_event_put(p.b);
         }
         pend.clear();
     }

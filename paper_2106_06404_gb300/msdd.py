@@ -232,7 +232,7 @@ class Hierarchy:
         o.precision, o.block_p, o.eig_maxit = int(precision), int(block_p), int(eig_maxit)
         o.sigma, o.eig_tol, o.reg_tol, o.seed = float(sigma), float(eig_tol), float(reg_tol), int(seed)
         o.stream = torch.cuda.current_stream().cuda_stream
-        o.profile = 1 if profile else 0
+        o.profile = 2 if profile == 2 else (1 if profile else 0)
         if fp32_start_iters is not None:
             o.fp32_start_iters = int(fp32_start_iters)
         if warm_start is not None:
