@@ -1019,44 +1019,50 @@ __global__ void __launch_bounds__(TPB) k_gram32(const double* __restrict__ W, do
     }
 }
 
-// C = D R^{-1} with D = diag(G)^{-1/2} and D G D = R^T R (FP64 Cholesky, one
-// warp per problem).  A column whose pivot falls below 1e-10 of its scaled
-// diagonal is dependent on the previous ones: it is reset to its scaled self
-// (R row e_k) so that the basis stays finite; the FP64 phase removes it.
+// C = D R^{-1} with D = diag(G)^{-1/2} and D G D = R^T R (FP32 Cholesky, one
+// warp per problem: G holds FP32 products and X = W C is formed in FP32, so
+// FP64 here would only lengthen the serial chain).  A column whose pivot
+// falls below 1e-10 of its scaled diagonal is dependent on the previous
+// ones: it is reset to its scaled self (R row e_k) so that the basis stays
+// finite; the FP64 phase removes it.
+__device__ __forceinline__ float rsqrt_f32(float x) {
+    const float r = rsqrtf(x);
+    return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
 __global__ void k_cholqr(const double* __restrict__ Gp, int gsplit, double* __restrict__ C,
                          const int* __restrict__ p_) {
-    __shared__ double R[PMAX][LD], Ri[PMAX][LD], d[PMAX], d_inv[PMAX];
+    __shared__ float R[PMAX][LD], Ri[PMAX][LD], d[PMAX], d_inv[PMAX];
     const int i = blockIdx.x;
     const int p = p_[i];
     const int t = threadIdx.x;
     const double* Gi = Gp + (long long)i * gsplit * PMAX * PMAX;
     for (int e = t; e < PMAX * PMAX; e += 32) {       // G = sum of the row-range partials
         int a = e / PMAX, b = e % PMAX;
-        double g = 0.0;
+        float g = 0.f;
         if (a < p && b < p)
-            for (int sp = 0; sp < gsplit; ++sp) g += Gi[(long long)sp * PMAX * PMAX + e];
+            for (int sp = 0; sp < gsplit; ++sp) g += f64_to_f32(Gi[(long long)sp * PMAX * PMAX + e]);
         R[a][b] = g;
-        Ri[a][b] = 0.0;
+        Ri[a][b] = 0.f;
     }
     __syncwarp();
     if (t < PMAX) {
-        double g = t < p ? R[t][t] : 0.0;
-        d[t] = g > 0.0 ? rsqrt_nr(g) : 0.0;
+        const float g = t < p ? R[t][t] : 0.f;
+        d[t] = g > 0.f ? rsqrt_f32(g) : 0.f;
     }
     __syncwarp();
     for (int e = t; e < PMAX * PMAX; e += 32) {
         int a = e / PMAX, b = e % PMAX;
-        R[a][b] = (a < p && b < p) ? d[a] * R[a][b] * d[b] : 0.0;
+        R[a][b] = (a < p && b < p) ? d[a] * R[a][b] * d[b] : 0.f;
     }
     __syncwarp();
     // upper Cholesky in place: R <- U with D G D = U^T U
     for (int k = 0; k < p; ++k) {
-        double piv = R[k][k];
-        bool ok = piv > 1e-10;
-        const double ru = ok ? rsqrt_nr(piv) : 1.0;
+        const float piv = R[k][k];
+        const bool ok = piv > 1e-10f;
+        const float ru = ok ? rsqrt_f32(piv) : 1.f;
         __syncwarp();
-        if (t == 0) { R[k][k] = ok ? piv * ru : 1.0; d_inv[k] = ru; }
-        for (int j = k + 1 + t; j < p; j += 32) R[k][j] = ok ? R[k][j] * ru : 0.0;
+        if (t == 0) { R[k][k] = ok ? piv * ru : 1.f; d_inv[k] = ru; }
+        for (int j = k + 1 + t; j < p; j += 32) R[k][j] = ok ? R[k][j] * ru : 0.f;
         __syncwarp();
         for (int e = t; e < p * p; e += 32) {
             int a = e / p, b = e % p;
@@ -1067,7 +1073,7 @@ __global__ void k_cholqr(const double* __restrict__ Gp, int gsplit, double* __re
     // Ri = U^{-1} (upper), column-parallel back substitution
     if (t < p) {
         for (int r = t; r >= 0; --r) {
-            double v = (r == t) ? 1.0 : 0.0;
+            float v = (r == t) ? 1.f : 0.f;
             for (int j = r + 1; j <= t; ++j) v -= R[r][j] * Ri[j][t];
             Ri[r][t] = v * d_inv[r];
         }
@@ -1075,7 +1081,7 @@ __global__ void k_cholqr(const double* __restrict__ Gp, int gsplit, double* __re
     __syncwarp();
     for (int e = t; e < PMAX * PMAX; e += 32) {
         int a = e / PMAX, b = e % PMAX;
-        C[(long long)i * PMAX * PMAX + e] = (a < p && b < p) ? d[a] * Ri[a][b] : 0.0;
+        C[(long long)i * PMAX * PMAX + e] = (a < p && b < p) ? f32_to_f64(d[a] * Ri[a][b]) : 0.0;
     }
 }
 
