@@ -96,25 +96,52 @@ def select_count(lam, nev_max, eta):
     return int(min(nev_max, int(np.sum(lam < eta))))
 
 
-def fine_pencil(mesh, Ke, en, sub, chi, Ke_of_subdomain=False):
+def fine_pencil(mesh, Ke, en, sub, chi, Ke_of_subdomain=False, blf=1, overlap_elements=None):
     """Dense Neumann matrix Abar_i (Eq. locala_cg: the element forms of
-    T_{h,L,i} on all non-Dirichlet nodes of the closed subdomain) and
-    B_i = X_i Abar_i X_i (b^1, Eq. cg_rhs_blf) of one fine subdomain, rows in
-    its lexicographic Neumann-node order; en are the element nodes of the
-    whole mesh, Ke the element matrices of the whole mesh (or, with
-    Ke_of_subdomain, of the subdomain's elements in ascending order), chi the
-    subdomain's partition of unity on its Neumann nodes (Section 2.3)."""
+    T_{h,L,i} on all non-Dirichlet nodes of the closed subdomain) and the
+    right-hand side B_i of one fine subdomain's GEVP, rows in its
+    lexicographic Neumann-node order (Section 3.4, Eq. cg_rhs_blf):
+      blf = 1: b^1(u, v) = abar(chi u, chi v),       B = X Abar X;
+      blf = 2: b^2(u, v) = a_ring(chi u, chi v),     B = X Aring X, Aring the
+               element forms of the subdomain's elements that also belong to
+               another subdomain (overlap_elements[e], Eq. original_geneo);
+      blf = 3: b^3(u, v) = abar(u - chi u, v - chi v), B = (I - X) Abar (I - X).
+    en are the element nodes of the whole mesh, Ke the element matrices of
+    the whole mesh (or, with Ke_of_subdomain, of the subdomain's elements in
+    ascending order), chi the subdomain's partition of unity on its Neumann
+    nodes (Section 2.3), X = diag(chi)."""
     nn = sub.neumann_nodes()
     pos = -np.ones(mesh.num_nodes, dtype=np.int64)
     pos[nn] = np.arange(len(nn))
     Abar = np.zeros((len(nn), len(nn)))
+    Aring = np.zeros((len(nn), len(nn))) if blf == 2 else None
     for k, e in enumerate(np.nonzero(sub.element_mask)[0]):
         loc = pos[en[e]]
         ok = loc >= 0
         li = loc[ok]
-        Abar[np.ix_(li, li)] += (Ke[k] if Ke_of_subdomain else Ke[e])[np.ix_(ok, ok)]
-    B = chi[:, None] * Abar * chi[None, :]
+        ke = (Ke[k] if Ke_of_subdomain else Ke[e])[np.ix_(ok, ok)]
+        Abar[np.ix_(li, li)] += ke
+        if blf == 2 and overlap_elements[e]:
+            Aring[np.ix_(li, li)] += ke
+    if blf == 1:
+        B = chi[:, None] * Abar * chi[None, :]
+    elif blf == 2:
+        B = chi[:, None] * Aring * chi[None, :]
+    elif blf == 3:
+        w = 1.0 - chi
+        B = w[:, None] * Abar * w[None, :]
+    else:
+        raise ValueError("blf must be 1, 2 or 3")
     return nn, Abar, B
+
+
+def overlap_elements(dec):
+    """Elements of the fine level that belong to at least two fine subdomains
+    (the union over i of the element sets of Eq. original_geneo)."""
+    cover = np.zeros_like(dec.fine[0].element_mask, dtype=np.int64)
+    for s in dec.fine:
+        cover += s.element_mask
+    return cover >= 2
 
 
 class Level:
@@ -125,10 +152,11 @@ class Hierarchy:
     """Result of the oracle set-up: all levels, spaces and factors."""
 
     def __init__(self, mesh, coeff, parts, overlap, levels, group, nev_max, eta,
-                 keep_local=False):
+                 keep_local=False, blf=1):
         self.mesh = mesh
         self.nev_max = nev_max
         self.eta = eta
+        self.blf = blf
         self.A = fem.assemble_system(mesh, coeff)
         self.n = self.A.shape[0]
         self.dec = Decomposition(mesh, parts, overlap, levels, group)
@@ -153,12 +181,15 @@ class Hierarchy:
         self.pou_counts = counts
         Ke = fem.element_matrices(mesh, self._coeff)
         en = mesh.element_nodes()
+        ovl = overlap_elements(dec) if self.blf == 2 else None
 
         def local(i):
             s = dec.fine[i]
-            nn, Abar, B = fine_pencil(mesh, Ke, en, s, chis[i])
+            nn, Abar, B = fine_pencil(mesh, Ke, en, s, chis[i], blf=self.blf, overlap_elements=ovl)
             chi = chis[i]
-            lam, W = gevp(Abar, B, rank_reveal=False)
+            # b^2 and b^3 have larger kernels than b^1: take the rank-revealing
+            # route (complement of ker Abar cap ker B) for them
+            lam, W = gevp(Abar, B, rank_reveal=self.blf != 1)
             m = select_count(lam, self.nev_max, self.eta)
             Wm = normalise_sign(W[:, :m])
             dn = s.dirichlet_nodes()
