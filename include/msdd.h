@@ -81,6 +81,12 @@ typedef struct msdd_decomp {
 typedef struct msdd_spectral {
     int nev_max;         /* 1 .. 24 */
     double eta;          /* > 0 */
+    int blf;             /* right-hand side of the fine-level GEVPs (Section 3.4, Eq. cg_rhs_blf):
+                            1 (or 0) b^1 = abar(chi u, chi v); 2 b^2 = a_ring(chi u, chi v), the
+                            element forms of the subdomain's elements that also belong to another
+                            subdomain (Eq. original_geneo, the original GenEO); 3 b^3 =
+                            abar(u - chi u, v - chi v).  Coarse levels keep their masked form
+                            (Section 4.2).  Other values: MSDD_ERR_INVALID_ARG */
 } msdd_spectral;
 
 typedef struct msdd_options {

@@ -139,6 +139,7 @@ msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msd
         }
         if (spectral->nev_max < 1 || spectral->nev_max > 24 || !(spectral->eta > 0.0))
             return fail(MSDD_ERR_INVALID_ARG, "nev_max must be in 1..24 and eta > 0");
+        if (spectral->blf < 0 || spectral->blf > 3) return fail(MSDD_ERR_INVALID_ARG, "blf must be 1, 2 or 3");
         msdd_options opt;
         msdd_default_options(&opt);
         if (options) opt = *options;

@@ -438,6 +438,21 @@ void Hierarchy::build_fine() {
     Pf = P0 * P1 * P2;
     fboxes = make_fine_boxes(g, dec);
     d_fboxes = upload_vec(fboxes, st);
+    // right-hand side of the fine GEVPs (Section 3.4); b^2 needs to know which
+    // elements lie in more than one fine box (per axis: boxes are products)
+    g.blf = spec.blf == 0 ? 1 : spec.blf;
+    if (g.blf == 2) {
+        const int stride[3] = {1, P0, P0 * P1}, np[3] = {P0, P1, P2};
+        for (int d = 0; d < dim; ++d) {
+            std::vector<int> cov(g.n[d], 0);
+            for (int q = 0; q < np[d]; ++q) {
+                const ProbBox& b = fboxes[q * stride[d]];
+                for (int x = b.elo[d]; x < b.ehi[d]; ++x) ++cov[x];
+            }
+            d_ecov[d] = upload_vec(cov, st);
+            g.ecov[d] = d_ecov[d].p;
+        }
+    }
     // combine maps: per axis and node coordinate, the blocks whose Dirichlet range holds it
     cmaps.parts[0] = P0; cmaps.parts[1] = P1; cmaps.parts[2] = P2;
     for (int d = 0; d < 3; ++d) {

@@ -102,6 +102,7 @@ struct Hierarchy {
     std::vector<ProbBox> fboxes;
     DevBuf<ProbBox> d_fboxes;
     DevBuf<int> d_count;
+    DevBuf<int> d_ecov[3];          // b^2: per axis, fine element boxes holding each element index
     TileBatch fdir;                 // Dirichlet factors A_{L,i}
     GevpBatch fge;                  // GEVP of (Abar_i, B_i), K_i factors
     LocalStencil fst;               // stored stencils of Abar_i and B_i (rows of fge)

@@ -71,7 +71,17 @@ __device__ __forceinline__ double elem_entry(const Geom& g, long long e, int a, 
 
 // sum over elements tau of the element box containing nodes x and x + o of
 // a_tau(phi_{x+o}, phi_x).
-__device__ double stencil_coef(const Geom& g, const int* elo, const int* ehi, const int x[3], const int o[3]) {
+// Element l belongs to another fine subdomain as well: boxes are products of
+// per-axis intervals, so the element lies in >= 2 boxes iff some axis does.
+__device__ __forceinline__ bool overlap_element(const Geom& g, const int l[3]) {
+    for (int d = 0; d < g.dim; ++d)
+        if (g.ecov[d][l[d]] >= 2) return true;
+    return false;
+}
+
+// ring: sum only the elements that belong to another subdomain too (b^2)
+__device__ double stencil_coef(const Geom& g, const int* elo, const int* ehi, const int x[3], const int o[3],
+                               bool ring = false) {
     int lo[3], cnt[3];
     for (int d = 0; d < 3; ++d) {
         if (d >= g.dim) { lo[d] = 0; cnt[d] = 1; continue; }
@@ -87,7 +97,7 @@ __device__ double stencil_coef(const Geom& g, const int* elo, const int* ehi, co
                 bool inside = true;
                 for (int d = 0; d < g.dim; ++d)
                     if (l[d] < elo[d] || l[d] >= ehi[d]) inside = false;
-                if (!inside) continue;
+                if (!inside || (ring && !overlap_element(g, l))) continue;
                 int a = 0, b = 0;
                 for (int d = 0; d < g.dim; ++d) {
                     a |= (x[d] - l[d]) << d;
@@ -136,7 +146,13 @@ __global__ void k_assemble(Geom g, const ProbBox* __restrict__ boxes, const int*
         int c = box_index(lo, hi, y, g.dim);
         if (c > r) continue;   // lower triangle only
         double v = stencil_coef(g, pb.elo, pb.ehi, x, o);
-        if (mode == 1) v *= 1.0 + sigma * chi_at(g, pb, count, x) * chi_at(g, pb, count, y);
+        if (mode == 1) {
+            // K = Abar + sigma B with B of the chosen right-hand side form
+            const double cx = chi_at(g, pb, count, x), cy = chi_at(g, pb, count, y);
+            if (g.blf == 3) v *= 1.0 + sigma * (1.0 - cx) * (1.0 - cy);
+            else if (g.blf == 2) v += sigma * cx * stencil_coef(g, pb.elo, pb.ehi, x, o, true) * cy;
+            else v *= 1.0 + sigma * cx * cy;
+        }
         int R = r / NB, C = c / NB;
         tiles[toff + ((long long)R * (kb + 1) + (R - C)) * NB2 + (r % NB) * NB + (c % NB)] = (T)v;
     }
@@ -293,7 +309,12 @@ __global__ void k_local_stencil(Geom g, const ProbBox* __restrict__ boxes, const
             for (int d = 0; d < 3; ++d) y[d] = x[d] + o[d];
             if (in_box(pb.nlo, pb.nhi, y, g.dim)) {
                 a = stencil_coef(g, pb.elo, pb.ehi, x, o);
-                b = chi_at(g, pb, count, x) * a * chi_at(g, pb, count, y);
+                if (g.blf == 3)
+                    b = (1.0 - chi_at(g, pb, count, x)) * a * (1.0 - chi_at(g, pb, count, y));
+                else if (g.blf == 2)
+                    b = chi_at(g, pb, count, x) * stencil_coef(g, pb.elo, pb.ehi, x, o, true) * chi_at(g, pb, count, y);
+                else
+                    b = chi_at(g, pb, count, x) * a * chi_at(g, pb, count, y);
             }
         }
         A[base + w] = a;

@@ -18,6 +18,8 @@ struct Geom {
     int coeff_kind;    // 0 scalar per element, 1 symmetric tensor per element
     int ncomp;         // 1, 3 (2D tensor) or 6 (3D tensor)
     const double* coeff;
+    int blf;           // fine GEVP right-hand side b^1, b^2 or b^3 (Section 3.4)
+    const int* ecov[3];// b^2: per axis, fine element boxes holding each element index (device)
 };
 
 // One local problem on the fine level: its overlapping element box

@@ -40,7 +40,7 @@ class Decomp(ctypes.Structure):
 
 
 class Spectral(ctypes.Structure):
-    _fields_ = [("nev_max", ctypes.c_int), ("eta", ctypes.c_double)]
+    _fields_ = [("nev_max", ctypes.c_int), ("eta", ctypes.c_double), ("blf", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -209,7 +209,7 @@ class Hierarchy:
 
     def __init__(self, n, coeff, parts, overlap, levels, group, nev_max, eta, dirichlet_faces=0b1,
                  precision=0, block_p=0, eig_maxit=200, sigma=1e-2, eig_tol=1e-6, reg_tol=-1.0, seed=12345,
-                 allow_eig_unconverged=False, profile=False, fp32_start_iters=None, warm_start=None):
+                 allow_eig_unconverged=False, profile=False, fp32_start_iters=None, warm_start=None, blf=1):
         torch = _torch()
         lib = load()
         self._lib = lib
@@ -228,6 +228,7 @@ class Hierarchy:
         s = Spectral()
         s.nev_max = int(nev_max)
         s.eta = float(eta)
+        s.blf = int(blf)
         o = default_options()
         o.precision, o.block_p, o.eig_maxit = int(precision), int(block_p), int(eig_maxit)
         o.sigma, o.eig_tol, o.reg_tol, o.seed = float(sigma), float(eig_tol), float(reg_tol), int(seed)
