@@ -194,9 +194,10 @@ class Hierarchy:
             Wm = normalise_sign(W[:, :m])
             dn = s.dirichlet_nodes()
             du = self.n2u[dn]
+            chi_dir = 1.0 / counts[dn]          # chi_i on the Dirichlet-space nodes (Section 2.3)
             Ai = np.asarray(self.A[du][:, du].todense())
             Li = linalg.cholesky(Ai)
-            return dict(nn=nn, chi=chi, Abar=Abar if keep_local else None,
+            return dict(nn=nn, chi=chi, chi_dir=chi_dir, Abar=Abar if keep_local else None,
                         B=B if keep_local else None, lam=lam, m=m, W=Wm,
                         dof=du, Ai=Ai if keep_local else None, Li=Li)
 
@@ -302,6 +303,43 @@ class Hierarchy:
             z += P0 @ linalg.cho_solve(self.L0, P0.T @ r)
         return z
 
+    def apply_level(self, l, r, restricted=False):
+        """z = B_l r, the part of the additive preconditioner on level l alone:
+        l = L the fine local solves (restricted: prolongation weighted by chi_i,
+        restricted additive Schwarz), 0 < l < L the solves on the own
+        generators of level l, l = 0 the coarsest solve (Section 2.1,
+        Eq. mlsdd).  The additive preconditioner is the sum over l."""
+        z = np.zeros_like(r)
+        if l == self.L:
+            for s in self.levels[self.L].subs:
+                y = linalg.cho_solve(s["Li"], r[s["dof"]])
+                z[s["dof"]] += s["chi_dir"] * y if restricted else y
+        elif l > 0:
+            lev = self.levels[l]
+            rl = lev.P.T @ r
+            zl = np.zeros_like(rl)
+            for s in lev.subs:
+                if s["Li"] is not None:
+                    zl[s["own_cols"]] += linalg.cho_solve(s["Li"], rl[s["own_cols"]])
+            z = lev.P @ zl
+        elif self.n0 > 0:
+            P0 = self.levels[1].P_coarse
+            z = P0 @ linalg.cho_solve(self.L0, P0.T @ r)
+        return z
+
+    def apply_hybrid(self, r):
+        """z = B_h r, the hybrid form used with GMRES in Section 5 (Tabs. 4-6):
+        multiplicative subspace correction over the levels, restricted
+        additive Schwarz within the fine level (Section 2.1, Eq.
+        subspace_iteration applied level after level).  Reading: one sweep
+        from the fine level to the coarsest, z <- z + B_l (r - A z); on the
+        coarse levels the own-generator spaces do not overlap, so restricted
+        and plain additive Schwarz coincide there."""
+        z = self.apply_level(self.L, r, restricted=True)
+        for l in range(self.L - 1, -1, -1):
+            z = z + self.apply_level(l, r - self.A @ z)
+        return z
+
     def apply_one_level(self, r):
         """z = sum_i R_i^T A_i^{-1} R_i r over the fine subdomains only (no coarse space)."""
         z = np.zeros_like(r)
@@ -321,6 +359,59 @@ class Hierarchy:
 
     def counts(self, l):
         return [s["m"] for s in self.levels[l].subs]
+
+
+def gmres(A, b, precond, tol=1e-8, restart=200, maxit=1000):
+    """Right-preconditioned GMRES(restart) with modified Gram-Schmidt Arnoldi
+    and Givens rotations (Saad and Schultz): x = M y minimises ||b - A M y||
+    over the Krylov space of A M; stops when the residual estimate falls
+    below tol * ||b|| (x0 = 0, Section 5's stopping rule).  Returns
+    (x, iterations, history of ||r||/||b||)."""
+    n = b.shape[0]
+    x = np.zeros_like(b)
+    bn = np.linalg.norm(b)
+    hist = [1.0]
+    if bn == 0.0:
+        return x, 0, hist
+    it = 0
+    r = b.copy()
+    while it < maxit:
+        beta = np.linalg.norm(r)
+        V = np.zeros((n, restart + 1))
+        H = np.zeros((restart + 1, restart))
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        V[:, 0] = r / beta
+        k = 0
+        for k in range(restart):
+            w = A @ precond(V[:, k])
+            for i in range(k + 1):
+                H[i, k] = V[:, i] @ w
+                w = w - H[i, k] * V[:, i]
+            H[k + 1, k] = np.linalg.norm(w)
+            if H[k + 1, k] > 0.0:
+                V[:, k + 1] = w / H[k + 1, k]
+            for i in range(k):                      # previous rotations on the new column
+                t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+                H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
+                H[i, k] = t
+            den = np.hypot(H[k, k], H[k + 1, k])
+            cs[k], sn[k] = H[k, k] / den, H[k + 1, k] / den
+            H[k, k] = den
+            H[k + 1, k] = 0.0
+            g[k + 1] = -sn[k] * g[k]
+            g[k] = cs[k] * g[k]
+            it += 1
+            hist.append(abs(g[k + 1]) / bn)
+            if abs(g[k + 1]) < tol * bn or it >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:k + 1, :k + 1]), g[:k + 1])
+        x = x + precond(V[:, :k + 1] @ y)
+        r = b - A @ x
+        if np.linalg.norm(r) < tol * bn or it >= maxit:
+            break
+    return x, it, hist
 
 
 def pcg(A, b, precond, tol=1e-8, maxit=1000, x0=None):

@@ -1,0 +1,90 @@
+"""Pins of the oracle's GMRES and of the hybrid preconditioner (multiplicative
+over levels, restricted additive Schwarz within the fine level) used with
+GMRES in Section 5 (Tabs. 4-6).
+
+* GMRES: after k steps the residual equals the minimum of ||b - A M y|| over
+  the Krylov space K_k(A M, b), computed independently from an explicit
+  Krylov basis (QR) and least squares; n steps solve an n x n system;
+* the hybrid error propagation I - B_h A equals the product of the level
+  factors (I - B_0 A) ... (I - B_L A) built from the separately pinned
+  additive level parts;
+* restricted additive Schwarz on the fine level equals the plain additive
+  sum scaled by 1 / N(x) (the partition of unity is the same for every
+  subdomain holding a node, Section 2.3);
+* one subdomain covering the domain: B_h = A^{-1}, GMRES takes one step.
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import fem, method
+
+
+def test_gmres_minimal_residual_and_termination():
+    rng = np.random.default_rng(4)
+    n = 30
+    A = np.eye(n) * 4 + rng.standard_normal((n, n))       # nonsymmetric, well conditioned
+    M = np.eye(n) + 0.1 * rng.standard_normal((n, n))      # nonsymmetric preconditioner
+    b = rng.standard_normal(n)
+    AM = A @ M
+    for k in (1, 3, 7, 12):
+        x, it, hist = method.gmres(A, b, lambda v: M @ v, tol=1e-30, restart=n, maxit=k)
+        K = np.stack([np.linalg.matrix_power(AM, j) @ b for j in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(AM @ Q, b, rcond=None)
+        rmin = np.linalg.norm(b - AM @ (Q @ y))
+        assert it == k
+        assert abs(np.linalg.norm(b - A @ x) - rmin) <= 1e-8 * np.linalg.norm(b)
+        assert abs(hist[-1] * np.linalg.norm(b) - rmin) <= 1e-8 * np.linalg.norm(b)
+    x, it, _ = method.gmres(A, b, lambda v: M @ v, tol=1e-12, restart=n, maxit=n)
+    assert it <= n and np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+
+
+def _explicit(H, f):
+    n = H.n
+    I = np.eye(n)
+    return np.stack([f(I[:, j]) for j in range(n)], axis=1)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_hybrid_error_propagation_is_product_of_levels(levels):
+    mesh = fem.Mesh((12, 12), 0b1)
+    kap = si.channels_2d(12, 2, 1e3, seed=3)
+    H = method.Hierarchy(mesh, kap, (3, 3), 1, levels, (2, 2) if levels == 3 else (1, 1), 4, 0.3)
+    A = H.A.toarray()
+    I = np.eye(H.n)
+    Bh = _explicit(H, H.apply_hybrid)
+    E = I - Bh @ A
+    P = I - _explicit(H, lambda r: H.apply_level(H.L, r, restricted=True)) @ A
+    for l in range(H.L - 1, -1, -1):
+        P = (I - _explicit(H, lambda r: H.apply_level(l, r)) @ A) @ P
+    assert np.abs(E - P).max() <= 1e-9 * max(1.0, np.abs(E).max())
+    # the additive preconditioner is the sum of the same level parts
+    Ba = _explicit(H, H.apply_preconditioner)
+    S = sum(_explicit(H, lambda r: H.apply_level(l, r)) for l in range(H.L + 1))
+    assert np.abs(Ba - S).max() <= 1e-10 * np.abs(Ba).max()
+
+
+def test_restricted_fine_level_is_count_scaled_sum():
+    mesh = fem.Mesh((16, 12), 0b1)
+    kap = si.channels_2d(16, 2, 1e4, seed=5)[: 16 * 12]
+    H = method.Hierarchy(mesh, kap, (4, 3), 2, 2, (1, 1), 4, 0.3)
+    keep = H.n2u >= 0
+    N = np.zeros(H.n)
+    N[H.n2u[keep]] = H.pou_counts[keep]
+    r = np.random.default_rng(1).standard_normal(H.n)
+    zr = H.apply_level(H.L, r, restricted=True)
+    za = H.apply_level(H.L, r)
+    assert np.allclose(zr, za / N, rtol=1e-13, atol=0.0)
+
+
+def test_single_subdomain_hybrid_is_exact():
+    mesh = fem.Mesh((10, 10), 0b1)
+    kap = si.channels_2d(10, 2, 1e3, seed=0)
+    H = method.Hierarchy(mesh, kap, (1, 1), 1, 2, (1, 1), 3, 2.0)
+    b = fem.load_vector(mesh)
+    z = H.apply_hybrid(b)
+    xd = np.linalg.solve(H.A.toarray(), b)
+    assert np.linalg.norm(z - xd) <= 1e-10 * np.linalg.norm(xd)
+    x, it, _ = method.gmres(H.A, b, H.apply_hybrid, 1e-10)
+    assert it == 1
