@@ -189,6 +189,32 @@ msdd_status msdd_solve_host(msdd_hierarchy* h, const double* b, double tol, int 
 /* z = B r for the multilevel preconditioner (device, n doubles each). */
 msdd_status msdd_apply_preconditioner(msdd_hierarchy* h, const double* r, double* z);
 
+/* Hybrid form of the preconditioner, the one used inside GMRES in Section 5
+ * (Tabs. 4-6): multiplicative subspace correction over the levels (Section
+ * 2.1, Eq. subspace_iteration applied level after level) and restricted
+ * additive Schwarz on the fine level (local solutions weighted by the
+ * partition of unity chi_i = 1/N(x) of Section 2.3).  z = B_h r with
+ *   z = sum_i R_i^T X_i A_i^{-1} R_i r, then for l = L-1 .. 0:
+ *   z <- z + B_l (r - A z),
+ * B_l the level-l part of the additive preconditioner (coarse own-generator
+ * spaces do not overlap, so restriction changes nothing there).  The order
+ * of the levels is not stated in the paper: fine to coarse is this
+ * library's reading.  B_h is not symmetric; use it with GMRES.
+ * r, z: device, n unknowns; synchronous on the hierarchy's stream. */
+msdd_status msdd_apply_hybrid_preconditioner(msdd_hierarchy* h, const double* r, double* z);
+
+/* Right-preconditioned GMRES(restart) with B_h (x0 = 0): Arnoldi with
+ * classical Gram-Schmidt applied twice, Givens rotations; a cycle ends when
+ * the Arnoldi residual estimate falls below tol * ||b||_2, the solve when the
+ * true residual does (the stopping rule of Section 5); otherwise the next
+ * cycle restarts from the true residual.  b, x: device.  *iterations =
+ * Arnoldi steps; *rel_residual = ||b - A x||_2 / ||b||_2.
+ * MSDD_ERR_NO_CONVERGENCE at maxit (x holds the last iterate).  The true
+ * residual of an FP64 iterate cannot fall below about
+ * eps || |A| |x| ||_2 / ||b||_2, so tol must lie above that. */
+msdd_status msdd_solve_gmres(msdd_hierarchy* h, const double* b, double tol, int restart, int maxit, double* x,
+                             int* iterations, double* rel_residual);
+
 /* y = A x (device, n doubles each). */
 msdd_status msdd_apply_operator(msdd_hierarchy* h, const double* x, double* y);
 

@@ -209,6 +209,28 @@ msdd_status msdd_apply_preconditioner(msdd_hierarchy* h, const double* r, double
     });
 }
 
+msdd_status msdd_apply_hybrid_preconditioner(msdd_hierarchy* h, const double* r, double* z) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !r || !z) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        h->h.apply_hybrid(r, z);
+        MSDD_CUDA(cudaStreamSynchronize(h->h.st));
+        return MSDD_OK;
+    });
+}
+
+msdd_status msdd_solve_gmres(msdd_hierarchy* h, const double* b, double tol, int restart, int maxit, double* x,
+                             int* iterations, double* rel_residual) {
+    return guarded([&]() -> msdd_status {
+        if (!h || !b || !x) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        if (!(tol > 0.0) || maxit < 1 || restart < 1 || restart > 1000)
+            return fail(MSDD_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1 and restart in 1..1000");
+        int it = h->h.solve_gmres(b, tol, restart, maxit, x, rel_residual);
+        if (iterations) *iterations = it < 0 ? -it : it;
+        if (it < 0) return fail(MSDD_ERR_NO_CONVERGENCE, "GMRES reached maxit");
+        return MSDD_OK;
+    });
+}
+
 msdd_status msdd_apply_operator(msdd_hierarchy* h, const double* x, double* y) {
     return guarded([&]() -> msdd_status {
         if (!h || !x || !y) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");

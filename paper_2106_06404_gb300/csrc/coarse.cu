@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) k_fine_combine(
     const double* __restrict__ y, const double* __restrict__ Phi, const long long* __restrict__ phioff, int ldphi,
     const int* __restrict__ m_, const long long* __restrict__ c1off, const double* __restrict__ z1,
     double* __restrict__ z, const double* __restrict__ r, double* __restrict__ partial, long long nun,
-    const int* __restrict__ done) {
+    const int* __restrict__ done, int mode) {
     __shared__ double red[256];
     if (done && *done) return;
     double part = 0.0;
@@ -178,22 +178,30 @@ __global__ void __launch_bounds__(256) k_fine_combine(
             hi[d] = cm.last[d][x[d]];
         }
         double acc = 0.0;
+        int ncov = 0;
         for (int pz = lo[2]; pz <= hi[2]; ++pz)
             for (int py = lo[1]; py <= hi[1]; ++py)
                 for (int px = lo[0]; px <= hi[0]; ++px) {
                     int j = px + cm.parts[0] * (py + cm.parts[1] * pz);
                     const ProbBox pb = fine[j];
                     int loc = box_index(pb.dlo, pb.dhi, x, g.dim);
-                    double v = y[droff[j] + loc];
-                    const int m = m_[j];
-                    const double* ph = Phi + phioff[j] + (long long)loc * ldphi;
-                    const double* zz = z1 + c1off[j];
-                    for (int k = 0; k < m; ++k) v += ph[k] * zz[k];
+                    double v = (mode & COMB_Y) ? y[droff[j] + loc] : 0.0;
+                    if (mode & COMB_COARSE) {
+                        const int m = m_[j];
+                        const double* ph = Phi + phioff[j] + (long long)loc * ldphi;
+                        const double* zz = z1 + c1off[j];
+                        for (int k = 0; k < m; ++k) v += ph[k] * zz[k];
+                    }
                     acc += v;
+                    ++ncov;
                 }
+        // restricted: chi_j(x) = 1 / N(x) for every subdomain j holding x
+        if (mode & COMB_RAS) acc *= 1.0 / (double)ncov;
+        if (mode & COMB_ACC) acc += z[u];
         z[u] = acc;
-        part += acc * r[u];
+        if (partial) part += acc * r[u];
     }
+    if (!partial) return;
     red[threadIdx.x] = part;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -269,9 +277,17 @@ void fine_combine(const Geom& g, const CombineMaps& cm, const ProbBox* d_fine, c
                   const double* y, const double* Phi, const long long* d_phioff, int ldphi, const int* d_m,
                   const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
                   int nblocks, const int* done, cudaStream_t s) {
+    fine_combine_mode(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off, z1, z, r, partial, nblocks, done,
+                      COMB_Y | COMB_COARSE, s);
+}
+
+void fine_combine_mode(const Geom& g, const CombineMaps& cm, const ProbBox* d_fine, const long long* d_droff,
+                       const double* y, const double* Phi, const long long* d_phioff, int ldphi, const int* d_m,
+                       const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
+                       int nblocks, const int* done, int mode, cudaStream_t s) {
     long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
     k_fine_combine<<<nblocks, 256, 0, s>>>(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off, z1, z, r,
-                                           partial, nun, done);
+                                           partial, nun, done, mode);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -1251,4 +1251,134 @@ int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, doubl
     return hs.iters;
 }
 
+// z = B_h r: the fine level as restricted additive Schwarz (local solutions
+// weighted by chi = 1/N(x)), then each coarser level in turn on the current
+// residual, z <- z + B_l (r - A z), down to the coarsest (Section 2.1, Eq.
+// subspace_iteration applied level by level; the order is a reading).  All
+// on the main stream.
+void Hierarchy::apply_hybrid(const double* rr, double* zz) {
+    double* r1 = levels == 2 ? r0buf.p : v1.p;
+    if ((long long)hyb_t.n < nun) {
+        hyb_t.alloc(nun);
+        hyb_q.alloc(nun);
+    }
+    fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, rr, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p,
+                         d_c1off.p, r1, Pf, nullptr, st);
+    tile_solve(fdir, frhs.p, 1, 1, nullptr, st, nullptr);
+    fine_combine_mode(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p, r1,
+                      zz, rr, nullptr, nblocks, nullptr, COMB_Y | COMB_RAS, st);
+    for (int l = L - 1; l >= 0; --l) {
+        spmv_stencil_dot(g, stencil.p, zz, hyb_q.p, partial.p, nblocks, nullptr, st);
+        vec_sub(rr, hyb_q.p, hyb_t.p, nun, st);                       // t = r - A z
+        fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, hyb_t.p, frhs.p, Phi.p, d_phioff.p, ldphi,
+                             d_fm.p, d_c1off.p, r1, Pf, nullptr, st);   // r1 = Phi^T t
+        const double* zc;
+        if (levels == 2) {
+            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, nullptr);
+            zc = y0buf.p;
+        } else if (l == 1) {
+            gemv_batched(d_gemm_y1.p, Pm, 0, 1.0, Minv.p, v1.p, 0.0, z1t.p, gemm_y1_maxm, st, nullptr);
+            zc = z1t.p;
+        } else {
+            gemv_batched(d_gemm_r0.p, Pm, 1, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, st, nullptr);
+            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, nullptr);
+            gemv_batched(d_gemm_z1.p, Pm, 0, 1.0, Zb.p, y0buf.p, 0.0, z1t.p, gemm_z1_maxm, st, nullptr);
+            zc = z1t.p;
+        }
+        fine_combine_mode(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p,
+                          zc, zz, rr, nullptr, nblocks, nullptr, COMB_COARSE | COMB_ACC, st);
+    }
+}
+
+// Right-preconditioned GMRES(restart) with the hybrid preconditioner: x0 = 0,
+// Arnoldi with classical Gram-Schmidt applied twice (dot products of all
+// basis vectors in one launch, sums on the host in a fixed order), Givens
+// rotations on the host; the cycle ends when the residual estimate falls
+// below tol ||b|| and the run when the true residual does (or at maxit).
+int Hierarchy::solve_gmres(const double* b, double tol, int restart, int maxit, double* xout, double* relres) {
+    const long long n = nun;
+    const int m = restart, nbd = 64;
+    DevBuf<double> V((size_t)(m + 1) * n), w(n), t(n), x(n), cdev(m + 1), part((size_t)(m + 1) * nbd);
+    std::vector<double> hpart((size_t)(m + 1) * nbd), tmp;
+    auto dots = [&](const double* Vp, int nvec, const double* wp) {
+        vec_mdot(Vp, nvec, wp, n, part.p, nbd, st);
+        MSDD_CUDA(cudaMemcpyAsync(hpart.data(), part.p, (size_t)nvec * nbd * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSDD_CUDA(cudaStreamSynchronize(st));
+        tmp.assign(nvec, 0.0);
+        for (int k = 0; k < nvec; ++k)
+            for (int q = 0; q < nbd; ++q) tmp[k] += hpart[(size_t)k * nbd + q];
+    };
+    auto upload = [&](const std::vector<double>& c, int cnt) {
+        MSDD_CUDA(cudaMemcpyAsync(cdev.p, c.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+        MSDD_CUDA(cudaStreamSynchronize(st));
+    };
+    x.zero(st);
+    dots(b, 1, b);
+    const double bn = std::sqrt(tmp[0]);
+    int it = 0;
+    double rel = 0.0;
+    if (bn > 0.0) {
+        MSDD_CUDA(cudaMemcpyAsync(t.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));   // r = b
+        for (;;) {
+            dots(t.p, 1, t.p);
+            const double beta = std::sqrt(tmp[0]);
+            vec_scale_to(t.p, V.p, 1.0 / beta, n, st);
+            std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 1, 0.0);
+            auto Hat = [&](int i, int k) -> double& { return H[(size_t)i * m + k]; };
+            gv[0] = beta;
+            int kk = 0;
+            for (int k = 0; k < m; ++k) {
+                apply_hybrid(V.p + (size_t)k * n, t.p);
+                spmv_stencil_dot(g, stencil.p, t.p, w.p, partial.p, nblocks, nullptr, st);   // w = A M v_k
+                for (int pass = 0; pass < 2; ++pass) {
+                    dots(V.p, k + 1, w.p);
+                    for (int i = 0; i <= k; ++i) Hat(i, k) += tmp[i];
+                    upload(tmp, k + 1);
+                    vec_comb(w.p, V.p, cdev.p, k + 1, n, -1.0, false, st);
+                }
+                dots(w.p, 1, w.p);
+                Hat(k + 1, k) = std::sqrt(tmp[0]);
+                if (Hat(k + 1, k) > 0.0) vec_scale_to(w.p, V.p + (size_t)(k + 1) * n, 1.0 / Hat(k + 1, k), n, st);
+                for (int i = 0; i < k; ++i) {
+                    const double a = cs[i] * Hat(i, k) + sn[i] * Hat(i + 1, k);
+                    Hat(i + 1, k) = -sn[i] * Hat(i, k) + cs[i] * Hat(i + 1, k);
+                    Hat(i, k) = a;
+                }
+                const double den = std::hypot(Hat(k, k), Hat(k + 1, k));
+                cs[k] = Hat(k, k) / den;
+                sn[k] = Hat(k + 1, k) / den;
+                Hat(k, k) = den;
+                Hat(k + 1, k) = 0.0;
+                gv[k + 1] = -sn[k] * gv[k];
+                gv[k] = cs[k] * gv[k];
+                ++it;
+                kk = k + 1;
+                if (std::fabs(gv[k + 1]) < tol * bn || it >= maxit) break;
+            }
+            std::vector<double> y(kk);
+            for (int i = kk - 1; i >= 0; --i) {
+                double v = gv[i];
+                for (int j = i + 1; j < kk; ++j) v -= Hat(i, j) * y[j];
+                y[i] = v / Hat(i, i);
+            }
+            upload(y, kk);
+            vec_comb(w.p, V.p, cdev.p, kk, n, 1.0, true, st);             // w = V y
+            apply_hybrid(w.p, t.p);                                       // t = M V y
+            std::vector<double> one(1, 1.0);
+            upload(one, 1);
+            vec_comb(x.p, t.p, cdev.p, 1, n, 1.0, false, st);             // x += t
+            spmv_stencil_dot(g, stencil.p, x.p, w.p, partial.p, nblocks, nullptr, st);
+            vec_sub(b, w.p, t.p, n, st);                                  // r = b - A x
+            dots(t.p, 1, t.p);
+            rel = std::sqrt(tmp[0]) / bn;
+            if (rel < tol || it >= maxit) break;
+        }
+    }
+    MSDD_CUDA(cudaMemcpyAsync(xout, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    MSDD_CUDA(cudaStreamSynchronize(st));
+    tile_check_waits();
+    if (relres) *relres = rel;
+    return rel < tol ? it : -it;
+}
+
 }  // namespace msdd

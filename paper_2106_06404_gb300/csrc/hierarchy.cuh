@@ -162,6 +162,11 @@ struct Hierarchy {
     void setup(const msdd_mesh& mesh, const msdd_coeff& coeff);
     void apply_prec(const double* rr, double* zz, const int* gdone);
     int solve(const double* b, double tol, int maxit, double* xout, double* relres);
+    // hybrid form (multiplicative over levels, restricted additive Schwarz on
+    // the fine level) and right-preconditioned GMRES with it (Section 5)
+    DevBuf<double> hyb_t, hyb_q;
+    void apply_hybrid(const double* rr, double* zz);
+    int solve_gmres(const double* b, double tol, int restart, int maxit, double* xout, double* relres);
     size_t device_bytes() const;
 
    private:

@@ -117,7 +117,63 @@ __global__ void k_update_p(const PcgScalars* sc, const double* __restrict__ z, d
 
 unsigned vec_blocks(long long n) { return (unsigned)std::max(1u, std::min(ceil_div(n, 256), 152u * 8)); }
 
+// ---- GMRES building blocks (Arnoldi vectors V[k] = V + k * n)
+// partial[k * gridDim.x + b] = block b's share of V[k] . w
+__global__ void k_mdot(const double* __restrict__ V, const double* __restrict__ w, long long n,
+                       double* __restrict__ partial) {
+    __shared__ double red[256];
+    const double* v = V + (long long)blockIdx.y * n;
+    double part = 0.0;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        part += v[u] * w[u];
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// w = (init ? 0 : w) + alpha * sum_k c[k] V[k]
+__global__ void k_vcomb(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ c, int nvec,
+                        long long n, double alpha, int init) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int k = 0; k < nvec; ++k) a += c[k] * V[(long long)k * n + u];
+        w[u] = (init ? 0.0 : w[u]) + alpha * a;
+    }
+}
+
+__global__ void k_scale_to(const double* __restrict__ x, double* __restrict__ y, double a, long long n) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        y[u] = a * x[u];
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c, long long n) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        c[u] = a[u] - b[u];
+}
+
 }  // namespace
+
+void vec_mdot(const double* V, int nvec, const double* w, long long n, double* partial, int nblk, cudaStream_t s) {
+    k_mdot<<<dim3(nblk, nvec), 256, 0, s>>>(V, w, n, partial);
+    MSDD_LAUNCH_CHECK();
+}
+void vec_comb(double* w, const double* V, const double* c, int nvec, long long n, double alpha, bool init,
+              cudaStream_t s) {
+    k_vcomb<<<vec_blocks(n), 256, 0, s>>>(w, V, c, nvec, n, alpha, init ? 1 : 0);
+    MSDD_LAUNCH_CHECK();
+}
+void vec_scale_to(const double* x, double* y, double a, long long n, cudaStream_t s) {
+    k_scale_to<<<vec_blocks(n), 256, 0, s>>>(x, y, a, n);
+    MSDD_LAUNCH_CHECK();
+}
+void vec_sub(const double* a, const double* b, double* c, long long n, cudaStream_t s) {
+    k_sub<<<vec_blocks(n), 256, 0, s>>>(a, b, c, n);
+    MSDD_LAUNCH_CHECK();
+}
 
 void pcg_start(const double* b, double* x, double* r, long long n, double* partial, int nblocks, cudaStream_t s) {
     k_start<<<nblocks, 256, 0, s>>>(b, x, r, n, partial);

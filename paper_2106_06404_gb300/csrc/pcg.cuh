@@ -36,4 +36,13 @@ void pcg_fin_beta(PcgScalars* sc, const double* partial, int nblocks, cudaStream
 // p = z + beta p
 void pcg_update_p(PcgScalars* sc, const double* z, double* p, long long n, cudaStream_t s);
 
+// GMRES building blocks (Arnoldi vectors V[k] = V + k n, device).
+// partial[k * nblk + b]: block b's share of V[k] . w, k < nvec (sum on the host).
+void vec_mdot(const double* V, int nvec, const double* w, long long n, double* partial, int nblk, cudaStream_t s);
+// w = (init ? 0 : w) + alpha sum_k c[k] V[k] (c device, nvec entries)
+void vec_comb(double* w, const double* V, const double* c, int nvec, long long n, double alpha, bool init,
+              cudaStream_t s);
+void vec_scale_to(const double* x, double* y, double a, long long n, cudaStream_t s);   // y = a x
+void vec_sub(const double* a, const double* b, double* c, long long n, cudaStream_t s);  // c = a - b
+
 }  // namespace msdd

@@ -76,6 +76,7 @@ EXPORTED = [
     "msdd_band_factor", "msdd_band_solve", "msdd_band_destroy", "msdd_band_solve_noalloc", "msdd_kernel_launches",
     "msdd_fine_layout", "msdd_nn_patches", "msdd_nn_workspace_bytes", "msdd_nn_forward", "msdd_nn_loss_grad",
     "msdd_nn_adam", "msdd_nn_start_vectors", "msdd_nn_targets", "msdd_release_cache", "msdd_cached_bytes",
+    "msdd_apply_hybrid_preconditioner", "msdd_solve_gmres",
 ]
 
 # learned warm start (include/msdd.h, MSDD_NN_*)
@@ -103,6 +104,8 @@ def load(path=LIB_PATH):
     lib.msdd_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp, ip, dp]
     lib.msdd_solve_host.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp, ip, dp]
     lib.msdd_apply_preconditioner.argtypes = [vp, vp, vp]
+    lib.msdd_apply_hybrid_preconditioner.argtypes = [vp, vp, vp]
+    lib.msdd_solve_gmres.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, ip, dp]
     lib.msdd_apply_operator.argtypes = [vp, vp, vp]
     lib.msdd_assemble_rhs.argtypes = [P(Mesh), ctypes.c_double, vp, vp]
     lib.msdd_get_stats.argtypes = [vp, P(Stats)]
@@ -269,6 +272,25 @@ class Hierarchy:
                                   ctypes.c_void_p(x.data_ptr()), ctypes.byref(it), ctypes.byref(rel))
         _check(st, allow=(-3,) if allow_maxit else ())
         return x, it.value, rel.value
+
+    def solve_gmres(self, b, tol=1e-8, restart=200, maxit=1000, allow_maxit=False):
+        """msdd_solve_gmres: GMRES with the hybrid preconditioner (x0 = 0)."""
+        torch = _torch()
+        x = torch.empty_like(b)
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = self._lib.msdd_solve_gmres(self._h, ctypes.c_void_p(b.data_ptr()), float(tol), int(restart), int(maxit),
+                                        ctypes.c_void_p(x.data_ptr()), ctypes.byref(it), ctypes.byref(rel))
+        _check(st, allow=(-3,) if allow_maxit else ())
+        return x, it.value, rel.value
+
+    def apply_hybrid(self, r):
+        """msdd_apply_hybrid_preconditioner: z = B_h r."""
+        torch = _torch()
+        z = torch.empty_like(r)
+        _check(self._lib.msdd_apply_hybrid_preconditioner(self._h, ctypes.c_void_p(r.data_ptr()),
+                                                          ctypes.c_void_p(z.data_ptr())))
+        return z
 
     def solve_host(self, b, tol=1e-8, maxit=1000):
         b = np.ascontiguousarray(b, dtype=np.float64)
