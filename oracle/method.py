@@ -361,12 +361,16 @@ class Hierarchy:
         return [s["m"] for s in self.levels[l].subs]
 
 
-def gmres(A, b, precond, tol=1e-8, restart=200, maxit=1000):
+def gmres(A, b, precond, tol=1e-8, restart=200, maxit=1000, flexible=False):
     """Right-preconditioned GMRES(restart) with modified Gram-Schmidt Arnoldi
     and Givens rotations (Saad and Schultz): x = M y minimises ||b - A M y||
-    over the Krylov space of A M; stops when the residual estimate falls
-    below tol * ||b|| (x0 = 0, Section 5's stopping rule).  Returns
-    (x, iterations, history of ||r||/||b||)."""
+    over the Krylov space of A M; a cycle ends when the residual estimate
+    falls below tol * ||b|| (x0 = 0, Section 5's stopping rule), the run when
+    the true residual does.  flexible=True is Saad's flexible GMRES: the
+    preconditioned vectors z_k = M v_k are kept and the cycle's update is
+    Z y, which minimises ||r - A Z y|| even when M changes from step to step
+    (in exact arithmetic the same iterates as the plain form for a fixed M).
+    Returns (x, iterations, history of ||r||/||b||)."""
     n = b.shape[0]
     x = np.zeros_like(b)
     bn = np.linalg.norm(b)
@@ -383,9 +387,13 @@ def gmres(A, b, precond, tol=1e-8, restart=200, maxit=1000):
         g = np.zeros(restart + 1)
         g[0] = beta
         V[:, 0] = r / beta
+        Z = np.zeros((n, restart)) if flexible else None
         k = 0
         for k in range(restart):
-            w = A @ precond(V[:, k])
+            z = precond(V[:, k])
+            if flexible:
+                Z[:, k] = z
+            w = A @ z
             for i in range(k + 1):
                 H[i, k] = V[:, i] @ w
                 w = w - H[i, k] * V[:, i]
@@ -407,7 +415,7 @@ def gmres(A, b, precond, tol=1e-8, restart=200, maxit=1000):
             if abs(g[k + 1]) < tol * bn or it >= maxit:
                 break
         y = np.linalg.solve(np.triu(H[:k + 1, :k + 1]), g[:k + 1])
-        x = x + precond(V[:, :k + 1] @ y)
+        x = x + (Z[:, :k + 1] @ y if flexible else precond(V[:, :k + 1] @ y))
         r = b - A @ x
         if np.linalg.norm(r) < tol * bn or it >= maxit:
             break

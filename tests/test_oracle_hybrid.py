@@ -4,7 +4,12 @@ GMRES in Section 5 (Tabs. 4-6).
 
 * GMRES: after k steps the residual equals the minimum of ||b - A M y|| over
   the Krylov space K_k(A M, b), computed independently from an explicit
-  Krylov basis (QR) and least squares; n steps solve an n x n system;
+  Krylov basis (QR) and least squares; n steps solve an n x n system; the
+  same for the flexible form with a fixed M;
+* flexible GMRES with a preconditioner that changes every step: after k
+  steps the residual equals min ||b - A Z y|| over the span of the k vectors
+  the preconditioner returned (least squares on the recorded vectors), which
+  the plain form does not reach;
 * the hybrid error propagation I - B_h A equals the product of the level
   factors (I - B_0 A) ... (I - B_L A) built from the separately pinned
   additive level parts;
@@ -20,7 +25,8 @@ import synthetic_inputs as si
 from oracle import fem, method
 
 
-def test_gmres_minimal_residual_and_termination():
+@pytest.mark.parametrize("flexible", [False, True])
+def test_gmres_minimal_residual_and_termination(flexible):
     rng = np.random.default_rng(4)
     n = 30
     A = np.eye(n) * 4 + rng.standard_normal((n, n))       # nonsymmetric, well conditioned
@@ -28,7 +34,7 @@ def test_gmres_minimal_residual_and_termination():
     b = rng.standard_normal(n)
     AM = A @ M
     for k in (1, 3, 7, 12):
-        x, it, hist = method.gmres(A, b, lambda v: M @ v, tol=1e-30, restart=n, maxit=k)
+        x, it, hist = method.gmres(A, b, lambda v: M @ v, tol=1e-30, restart=n, maxit=k, flexible=flexible)
         K = np.stack([np.linalg.matrix_power(AM, j) @ b for j in range(k)], axis=1)
         Q, _ = np.linalg.qr(K)
         y, *_ = np.linalg.lstsq(AM @ Q, b, rcond=None)
@@ -36,8 +42,38 @@ def test_gmres_minimal_residual_and_termination():
         assert it == k
         assert abs(np.linalg.norm(b - A @ x) - rmin) <= 1e-8 * np.linalg.norm(b)
         assert abs(hist[-1] * np.linalg.norm(b) - rmin) <= 1e-8 * np.linalg.norm(b)
-    x, it, _ = method.gmres(A, b, lambda v: M @ v, tol=1e-12, restart=n, maxit=n)
+    x, it, _ = method.gmres(A, b, lambda v: M @ v, tol=1e-12, restart=n, maxit=n, flexible=flexible)
     assert it <= n and np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_flexible_gmres_with_changing_preconditioner():
+    rng = np.random.default_rng(7)
+    n = 30
+    A = np.eye(n) * 4 + rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    Ai = np.linalg.inv(A)
+    # close to A^{-1}, different at every step (like an inexact inner solve)
+    Ms = [Ai @ (np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)) for _ in range(n)]
+    for k in (2, 5, 9):
+        zs = []
+
+        def precond(v):
+            z = Ms[len(zs) % n] @ v
+            zs.append(z)
+            return z
+
+        x, it, hist = method.gmres(A, b, precond, tol=1e-30, restart=n, maxit=k, flexible=True)
+        Z = np.stack(zs[:k], axis=1)
+        y, *_ = np.linalg.lstsq(A @ Z, b, rcond=None)
+        rmin = np.linalg.norm(b - A @ Z @ y)
+        assert it == k
+        assert abs(np.linalg.norm(b - A @ x) - rmin) <= 1e-8 * np.linalg.norm(b)
+        assert abs(hist[-1] * np.linalg.norm(b) - rmin) <= 1e-8 * np.linalg.norm(b)
+        zs.clear()
+        xp, _, histp = method.gmres(A, b, precond, tol=1e-30, restart=n, maxit=k)
+        # the plain form's estimate is the same, its iterate is not the minimiser
+        assert abs(histp[-1] - hist[-1]) <= 1e-8
+        assert np.linalg.norm(b - A @ xp) > 4 * rmin
 
 
 def _explicit(H, f):
