@@ -203,15 +203,20 @@ msdd_status msdd_apply_preconditioner(msdd_hierarchy* h, const double* r, double
  * r, z: device, n unknowns; synchronous on the hierarchy's stream. */
 msdd_status msdd_apply_hybrid_preconditioner(msdd_hierarchy* h, const double* r, double* z);
 
-/* Right-preconditioned GMRES(restart) with B_h (x0 = 0): Arnoldi with
- * classical Gram-Schmidt applied twice, Givens rotations; a cycle ends when
- * the Arnoldi residual estimate falls below tol * ||b||_2, the solve when the
- * true residual does (the stopping rule of Section 5); otherwise the next
- * cycle restarts from the true residual.  b, x: device.  *iterations =
- * Arnoldi steps; *rel_residual = ||b - A x||_2 / ||b||_2.
- * MSDD_ERR_NO_CONVERGENCE at maxit (x holds the last iterate).  The true
- * residual of an FP64 iterate cannot fall below about
- * eps || |A| |x| ||_2 / ||b||_2, so tol must lie above that. */
+/* Flexible GMRES(restart) (Saad) with B_h (x0 = 0): the vectors z_k = B_h v_k
+ * are kept (restart x n more device doubles) and each cycle updates x by
+ * Z y, so the Arnoldi residual estimate remains the true residual (down to
+ * rounding) when B_h is not a fixed linear map (FP32 local solves); for a
+ * fixed B_h the iterates are those of right-preconditioned GMRES.  Section 5
+ * names GMRES without its variant.  Arnoldi with classical Gram-Schmidt
+ * applied twice, Givens rotations.  Stops when the residual estimate falls
+ * below tol * ||b||_2 (Section 5's rule on the solver's own residual, as
+ * msdd_solve does with CG's recursive residual) or the true residual at the
+ * end of a cycle does; a cycle that reaches `restart` steps restarts from
+ * the true residual.  b, x: device.  *iterations = Arnoldi steps;
+ * *rel_residual = ||b - A x||_2 / ||b||_2, the true residual, which cannot
+ * fall below about eps || |A| |x| ||_2 / ||b||_2 in FP64.
+ * MSDD_ERR_NO_CONVERGENCE at maxit (x holds the last iterate). */
 msdd_status msdd_solve_gmres(msdd_hierarchy* h, const double* b, double tol, int restart, int maxit, double* x,
                              int* iterations, double* rel_residual);
 

@@ -364,9 +364,12 @@ class Hierarchy:
 def gmres(A, b, precond, tol=1e-8, restart=200, maxit=1000, flexible=False):
     """Right-preconditioned GMRES(restart) with modified Gram-Schmidt Arnoldi
     and Givens rotations (Saad and Schultz): x = M y minimises ||b - A M y||
-    over the Krylov space of A M; a cycle ends when the residual estimate
-    falls below tol * ||b|| (x0 = 0, Section 5's stopping rule), the run when
-    the true residual does.  flexible=True is Saad's flexible GMRES: the
+    over the Krylov space of A M; x0 = 0; the run stops when the residual
+    estimate of the Arnoldi process falls below tol * ||b|| (Section 5's
+    stopping rule on the solver's own residual, as the recursive residual
+    for CG) or the true residual at the end of a cycle does; a cycle that
+    ends at the restart length restarts from the true residual.
+    flexible=True is Saad's flexible GMRES: the
     preconditioned vectors z_k = M v_k are kept and the cycle's update is
     Z y, which minimises ||r - A Z y|| even when M changes from step to step
     (in exact arithmetic the same iterates as the plain form for a fixed M).
@@ -417,7 +420,7 @@ def gmres(A, b, precond, tol=1e-8, restart=200, maxit=1000, flexible=False):
         y = np.linalg.solve(np.triu(H[:k + 1, :k + 1]), g[:k + 1])
         x = x + (Z[:, :k + 1] @ y if flexible else precond(V[:, :k + 1] @ y))
         r = b - A @ x
-        if np.linalg.norm(r) < tol * bn or it >= maxit:
+        if abs(g[k + 1]) < tol * bn or np.linalg.norm(r) < tol * bn or it >= maxit:
             break
     return x, it, hist
 

@@ -1290,15 +1290,22 @@ void Hierarchy::apply_hybrid(const double* rr, double* zz) {
     }
 }
 
-// Right-preconditioned GMRES(restart) with the hybrid preconditioner: x0 = 0,
-// Arnoldi with classical Gram-Schmidt applied twice (dot products of all
-// basis vectors in one launch, sums on the host in a fixed order), Givens
-// rotations on the host; the cycle ends when the residual estimate falls
-// below tol ||b|| and the run when the true residual does (or at maxit).
+// Flexible GMRES(restart) (Saad) with the hybrid preconditioner: x0 = 0,
+// z_k = B_h v_k kept beside the Arnoldi basis and the cycle's update x += Z y,
+// so that the residual estimate stays the true residual when the local
+// solves run in FP32 (B_h then is no fixed linear map); Arnoldi with
+// classical Gram-Schmidt applied twice (dot products of all basis vectors in
+// one launch, sums on the host in a fixed order), Givens rotations on the
+// host.  The run stops when the Arnoldi residual estimate falls below
+// tol ||b|| (the rule of Section 5 on the solver's own residual, as the
+// recursive residual stops CG) or the true residual at the end of a cycle
+// does; a cycle that reaches the restart length restarts from the true
+// residual.  Returns the step count (negative at maxit) and the true residual.
 int Hierarchy::solve_gmres(const double* b, double tol, int restart, int maxit, double* xout, double* relres) {
     const long long n = nun;
     const int m = restart, nbd = 64;
-    DevBuf<double> V((size_t)(m + 1) * n), w(n), t(n), x(n), cdev(m + 1), part((size_t)(m + 1) * nbd);
+    DevBuf<double> V((size_t)(m + 1) * n), Z((size_t)m * n), w(n), t(n), x(n), cdev(m + 1),
+        part((size_t)(m + 1) * nbd);
     std::vector<double> hpart((size_t)(m + 1) * nbd), tmp;
     auto dots = [&](const double* Vp, int nvec, const double* wp) {
         vec_mdot(Vp, nvec, wp, n, part.p, nbd, st);
@@ -1317,6 +1324,7 @@ int Hierarchy::solve_gmres(const double* b, double tol, int restart, int maxit, 
     const double bn = std::sqrt(tmp[0]);
     int it = 0;
     double rel = 0.0;
+    bool conv = bn == 0.0;
     if (bn > 0.0) {
         MSDD_CUDA(cudaMemcpyAsync(t.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));   // r = b
         for (;;) {
@@ -1328,8 +1336,9 @@ int Hierarchy::solve_gmres(const double* b, double tol, int restart, int maxit, 
             gv[0] = beta;
             int kk = 0;
             for (int k = 0; k < m; ++k) {
-                apply_hybrid(V.p + (size_t)k * n, t.p);
-                spmv_stencil_dot(g, stencil.p, t.p, w.p, partial.p, nblocks, nullptr, st);   // w = A M v_k
+                double* zk = Z.p + (size_t)k * n;
+                apply_hybrid(V.p + (size_t)k * n, zk);                                     // z_k = B_h v_k
+                spmv_stencil_dot(g, stencil.p, zk, w.p, partial.p, nblocks, nullptr, st);   // w = A z_k
                 for (int pass = 0; pass < 2; ++pass) {
                     dots(V.p, k + 1, w.p);
                     for (int i = 0; i <= k; ++i) Hat(i, k) += tmp[i];
@@ -1362,23 +1371,20 @@ int Hierarchy::solve_gmres(const double* b, double tol, int restart, int maxit, 
                 y[i] = v / Hat(i, i);
             }
             upload(y, kk);
-            vec_comb(w.p, V.p, cdev.p, kk, n, 1.0, true, st);             // w = V y
-            apply_hybrid(w.p, t.p);                                       // t = M V y
-            std::vector<double> one(1, 1.0);
-            upload(one, 1);
-            vec_comb(x.p, t.p, cdev.p, 1, n, 1.0, false, st);             // x += t
+            vec_comb(x.p, Z.p, cdev.p, kk, n, 1.0, false, st);            // x += Z y
             spmv_stencil_dot(g, stencil.p, x.p, w.p, partial.p, nblocks, nullptr, st);
             vec_sub(b, w.p, t.p, n, st);                                  // r = b - A x
             dots(t.p, 1, t.p);
             rel = std::sqrt(tmp[0]) / bn;
-            if (rel < tol || it >= maxit) break;
+            conv = std::fabs(gv[kk]) < tol * bn || rel < tol;
+            if (conv || it >= maxit) break;
         }
     }
     MSDD_CUDA(cudaMemcpyAsync(xout, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     MSDD_CUDA(cudaStreamSynchronize(st));
     tile_check_waits();
     if (relres) *relres = rel;
-    return rel < tol ? it : -it;
+    return conv ? it : -it;
 }
 
 }  // namespace msdd
