@@ -1255,128 +1255,149 @@ int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, doubl
 // weighted by chi = 1/N(x)), then each coarser level in turn on the current
 // residual, z <- z + B_l (r - A z), down to the coarsest (Section 2.1, Eq.
 // subspace_iteration applied level by level; the order is a reading).  All
-// on the main stream.
-void Hierarchy::apply_hybrid(const double* rr, double* zz) {
+// on the main stream; every kernel returns at once when `done` is set.
+void Hierarchy::apply_hybrid(const double* rr, double* zz, const int* done) {
     double* r1 = levels == 2 ? r0buf.p : v1.p;
     if ((long long)hyb_t.n < nun) {
         hyb_t.alloc(nun);
         hyb_q.alloc(nun);
     }
     fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, rr, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p,
-                         d_c1off.p, r1, Pf, nullptr, st);
-    tile_solve(fdir, frhs.p, 1, 1, nullptr, st, nullptr);
+                         d_c1off.p, r1, Pf, done, st);
+    tile_solve(fdir, frhs.p, 1, 1, nullptr, st, done);
     fine_combine_mode(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p, r1,
-                      zz, rr, nullptr, nblocks, nullptr, COMB_Y | COMB_RAS, st);
+                      zz, rr, nullptr, nblocks, done, COMB_Y | COMB_RAS, st);
     for (int l = L - 1; l >= 0; --l) {
-        spmv_stencil_dot(g, stencil.p, zz, hyb_q.p, partial.p, nblocks, nullptr, st);
-        vec_sub(rr, hyb_q.p, hyb_t.p, nun, st);                       // t = r - A z
+        spmv_stencil_dot(g, stencil.p, zz, hyb_q.p, partial.p, nblocks, done, st);
+        vec_sub(rr, hyb_q.p, hyb_t.p, nun, st, done);                       // t = r - A z
         fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, hyb_t.p, frhs.p, Phi.p, d_phioff.p, ldphi,
-                             d_fm.p, d_c1off.p, r1, Pf, nullptr, st);   // r1 = Phi^T t
+                             d_fm.p, d_c1off.p, r1, Pf, done, st);      // r1 = Phi^T t
         const double* zc;
         if (levels == 2) {
-            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, nullptr);
+            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, done);
             zc = y0buf.p;
         } else if (l == 1) {
-            gemv_batched(d_gemm_y1.p, Pm, 0, 1.0, Minv.p, v1.p, 0.0, z1t.p, gemm_y1_maxm, st, nullptr);
+            gemv_batched(d_gemm_y1.p, Pm, 0, 1.0, Minv.p, v1.p, 0.0, z1t.p, gemm_y1_maxm, st, done);
             zc = z1t.p;
         } else {
-            gemv_batched(d_gemm_r0.p, Pm, 1, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, st, nullptr);
-            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, nullptr);
-            gemv_batched(d_gemm_z1.p, Pm, 0, 1.0, Zb.p, y0buf.p, 0.0, z1t.p, gemm_z1_maxm, st, nullptr);
+            gemv_batched(d_gemm_r0.p, Pm, 1, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, st, done);
+            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, done);
+            gemv_batched(d_gemm_z1.p, Pm, 0, 1.0, Zb.p, y0buf.p, 0.0, z1t.p, gemm_z1_maxm, st, done);
             zc = z1t.p;
         }
         fine_combine_mode(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p,
-                          zc, zz, rr, nullptr, nblocks, nullptr, COMB_COARSE | COMB_ACC, st);
+                          zc, zz, rr, nullptr, nblocks, done, COMB_COARSE | COMB_ACC, st);
     }
 }
 
 // Flexible GMRES(restart) (Saad) with the hybrid preconditioner: x0 = 0,
 // z_k = B_h v_k kept beside the Arnoldi basis and the cycle's update x += Z y,
 // so that the residual estimate stays the true residual when the local
-// solves run in FP32 (B_h then is no fixed linear map); Arnoldi with
-// classical Gram-Schmidt applied twice (dot products of all basis vectors in
-// one launch, sums on the host in a fixed order), Givens rotations on the
-// host.  The run stops when the Arnoldi residual estimate falls below
-// tol ||b|| (the rule of Section 5 on the solver's own residual, as the
-// recursive residual stops CG) or the true residual at the end of a cycle
-// does; a cycle that reaches the restart length restarts from the true
-// residual.  Returns the step count (negative at maxit) and the true residual.
+// solves run in FP32 (B_h then is no fixed linear map).  Arnoldi with
+// classical Gram-Schmidt applied twice; the coefficients, the Hessenberg
+// matrix, the Givens rotations and the stop test stay on the device, so the
+// host enqueues the steps in chunks and reads the device state one chunk
+// behind (kernels return at once after the stop).  The run stops when the
+// Arnoldi residual estimate falls below tol ||b|| (the rule of Section 5 on
+// the solver's own residual, as the recursive residual stops CG) or the true
+// residual at the end of a cycle does; a cycle that reaches the restart
+// length restarts from the true residual.  Returns the step count (negative
+// at maxit) and the true residual.
 int Hierarchy::solve_gmres(const double* b, double tol, int restart, int maxit, double* xout, double* relres) {
     const long long n = nun;
-    const int m = restart, nbd = 64;
+    const int m = restart, nbd = 64, CH = 4;
     DevBuf<double> V((size_t)(m + 1) * n), Z((size_t)m * n), w(n), t(n), x(n), cdev(m + 1),
-        part((size_t)(m + 1) * nbd);
-    std::vector<double> hpart((size_t)(m + 1) * nbd), tmp;
-    auto dots = [&](const double* Vp, int nvec, const double* wp) {
-        vec_mdot(Vp, nvec, wp, n, part.p, nbd, st);
-        MSDD_CUDA(cudaMemcpyAsync(hpart.data(), part.p, (size_t)nvec * nbd * sizeof(double), cudaMemcpyDeviceToHost, st));
+        part((size_t)(m + 1) * nbd), Hd((size_t)(m + 1) * m), rot((size_t)3 * m + 2);
+    DevBuf<GmresState> gst(1);
+    double *cs = rot.p, *sn = rot.p + m, *gvd = rot.p + 2 * m, *hinv = rot.p + 3 * m + 1;
+    const int* done = &gst.p->done;
+    struct Pinned {
+        GmresState* p;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        Pinned() : p(static_cast<GmresState*>(pinned_cache_alloc(2 * sizeof(GmresState)))) {}
+        ~Pinned() {
+            for (auto e : ev)
+                if (e) cudaEventDestroy(e);
+            pinned_cache_release(p, 2 * sizeof(GmresState));
+        }
+    } pin;
+    for (auto& e : pin.ev) MSDD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+
+    std::vector<double> hpart(nbd), tmp;
+    auto norm = [&](const double* v) {
+        vec_mdot(v, 1, v, n, part.p, nbd, st);
+        MSDD_CUDA(cudaMemcpyAsync(hpart.data(), part.p, nbd * sizeof(double), cudaMemcpyDeviceToHost, st));
         MSDD_CUDA(cudaStreamSynchronize(st));
-        tmp.assign(nvec, 0.0);
-        for (int k = 0; k < nvec; ++k)
-            for (int q = 0; q < nbd; ++q) tmp[k] += hpart[(size_t)k * nbd + q];
+        double ss = 0.0;
+        for (int q = 0; q < nbd; ++q) ss += hpart[q];
+        return std::sqrt(ss);
     };
-    auto upload = [&](const std::vector<double>& c, int cnt) {
-        MSDD_CUDA(cudaMemcpyAsync(cdev.p, c.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, st));
-        MSDD_CUDA(cudaStreamSynchronize(st));
+    auto step = [&](int k) {
+        double* zk = Z.p + (size_t)k * n;
+        apply_hybrid(V.p + (size_t)k * n, zk, done);                               // z_k = B_h v_k
+        spmv_stencil_dot(g, stencil.p, zk, w.p, partial.p, nblocks, done, st);     // w = A z_k
+        for (int pass = 0; pass < 2; ++pass) {
+            vec_mdot(V.p, k + 1, w.p, n, part.p, nbd, st, done);
+            gm_gs_coef(part.p, nbd, k + 1, Hd.p, m, k, cdev.p, pass > 0, gst.p, st);
+            vec_comb(w.p, V.p, cdev.p, k + 1, n, -1.0, false, st, done);
+        }
+        vec_mdot(w.p, 1, w.p, n, part.p, nbd, st, done);
+        gm_fin(part.p, nbd, Hd.p, m, k, cs, sn, gvd, hinv, gst.p, st);
+        vec_scale_dev(w.p, V.p + (size_t)(k + 1) * n, hinv, n, done, st);
     };
+
     x.zero(st);
-    dots(b, 1, b);
-    const double bn = std::sqrt(tmp[0]);
+    const double bn = norm(b);
     int it = 0;
     double rel = 0.0;
     bool conv = bn == 0.0;
     if (bn > 0.0) {
         MSDD_CUDA(cudaMemcpyAsync(t.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));   // r = b
+        std::vector<double> H, gv(m + 1);
         for (;;) {
-            dots(t.p, 1, t.p);
-            const double beta = std::sqrt(tmp[0]);
+            const double beta = norm(t.p);
             vec_scale_to(t.p, V.p, 1.0 / beta, n, st);
-            std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 1, 0.0);
-            auto Hat = [&](int i, int k) -> double& { return H[(size_t)i * m + k]; };
+            GmresState s0{0, it, maxit, 0, tol * bn};
+            std::fill(gv.begin(), gv.end(), 0.0);
             gv[0] = beta;
-            int kk = 0;
-            for (int k = 0; k < m; ++k) {
-                double* zk = Z.p + (size_t)k * n;
-                apply_hybrid(V.p + (size_t)k * n, zk);                                     // z_k = B_h v_k
-                spmv_stencil_dot(g, stencil.p, zk, w.p, partial.p, nblocks, nullptr, st);   // w = A z_k
-                for (int pass = 0; pass < 2; ++pass) {
-                    dots(V.p, k + 1, w.p);
-                    for (int i = 0; i <= k; ++i) Hat(i, k) += tmp[i];
-                    upload(tmp, k + 1);
-                    vec_comb(w.p, V.p, cdev.p, k + 1, n, -1.0, false, st);
+            MSDD_CUDA(cudaMemcpyAsync(gst.p, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+            MSDD_CUDA(cudaMemcpyAsync(gvd, gv.data(), (m + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+            MSDD_CUDA(cudaMemsetAsync(Hd.p, 0, (size_t)(m + 1) * m * sizeof(double), st));
+            MSDD_CUDA(cudaStreamSynchronize(st));   // pageable sources above
+            int k = 0, slot = 0;
+            bool prev = false;
+            while (k < m) {
+                for (const int kend = std::min(m, k + CH); k < kend; ++k) step(k);
+                MSDD_CUDA(cudaMemcpyAsync(pin.p + slot, gst.p, sizeof(GmresState), cudaMemcpyDeviceToHost, st));
+                MSDD_CUDA(cudaEventRecord(pin.ev[slot], st));
+                slot ^= 1;
+                if (prev) {   // the state after the chunk before this one
+                    MSDD_CUDA(cudaEventSynchronize(pin.ev[slot]));
+                    if (pin.p[slot].done) break;
                 }
-                dots(w.p, 1, w.p);
-                Hat(k + 1, k) = std::sqrt(tmp[0]);
-                if (Hat(k + 1, k) > 0.0) vec_scale_to(w.p, V.p + (size_t)(k + 1) * n, 1.0 / Hat(k + 1, k), n, st);
-                for (int i = 0; i < k; ++i) {
-                    const double a = cs[i] * Hat(i, k) + sn[i] * Hat(i + 1, k);
-                    Hat(i + 1, k) = -sn[i] * Hat(i, k) + cs[i] * Hat(i + 1, k);
-                    Hat(i, k) = a;
-                }
-                const double den = std::hypot(Hat(k, k), Hat(k + 1, k));
-                cs[k] = Hat(k, k) / den;
-                sn[k] = Hat(k + 1, k) / den;
-                Hat(k, k) = den;
-                Hat(k + 1, k) = 0.0;
-                gv[k + 1] = -sn[k] * gv[k];
-                gv[k] = cs[k] * gv[k];
-                ++it;
-                kk = k + 1;
-                if (std::fabs(gv[k + 1]) < tol * bn || it >= maxit) break;
+                prev = true;
             }
+            GmresState sf;
+            MSDD_CUDA(cudaMemcpyAsync(&sf, gst.p, sizeof(sf), cudaMemcpyDeviceToHost, st));
+            MSDD_CUDA(cudaStreamSynchronize(st));
+            const int kk = sf.kk;
+            it = sf.it;
+            H.resize((size_t)kk * m);
+            MSDD_CUDA(cudaMemcpyAsync(H.data(), Hd.p, (size_t)kk * m * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MSDD_CUDA(cudaMemcpyAsync(gv.data(), gvd, (kk + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MSDD_CUDA(cudaStreamSynchronize(st));
             std::vector<double> y(kk);
             for (int i = kk - 1; i >= 0; --i) {
                 double v = gv[i];
-                for (int j = i + 1; j < kk; ++j) v -= Hat(i, j) * y[j];
-                y[i] = v / Hat(i, i);
+                for (int j = i + 1; j < kk; ++j) v -= H[(size_t)i * m + j] * y[j];
+                y[i] = v / H[(size_t)i * m + i];
             }
-            upload(y, kk);
-            vec_comb(x.p, Z.p, cdev.p, kk, n, 1.0, false, st);            // x += Z y
+            MSDD_CUDA(cudaMemcpyAsync(cdev.p, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, st));
+            vec_comb(x.p, Z.p, cdev.p, kk, n, 1.0, false, st);                 // x += Z y
             spmv_stencil_dot(g, stencil.p, x.p, w.p, partial.p, nblocks, nullptr, st);
-            vec_sub(b, w.p, t.p, n, st);                                  // r = b - A x
-            dots(t.p, 1, t.p);
-            rel = std::sqrt(tmp[0]) / bn;
-            conv = std::fabs(gv[kk]) < tol * bn || rel < tol;
+            vec_sub(b, w.p, t.p, n, st);                                        // r = b - A x
+            rel = norm(t.p) / bn;
+            conv = sf.done == 1 || rel < tol;
             if (conv || it >= maxit) break;
         }
     }

@@ -120,7 +120,8 @@ unsigned vec_blocks(long long n) { return (unsigned)std::max(1u, std::min(ceil_d
 // ---- GMRES building blocks (Arnoldi vectors V[k] = V + k * n)
 // partial[k * gridDim.x + b] = block b's share of V[k] . w
 __global__ void k_mdot(const double* __restrict__ V, const double* __restrict__ w, long long n,
-                       double* __restrict__ partial) {
+                       double* __restrict__ partial, const int* __restrict__ done) {
+    if (done && *done) return;
     __shared__ double red[256];
     const double* v = V + (long long)blockIdx.y * n;
     double part = 0.0;
@@ -137,7 +138,8 @@ __global__ void k_mdot(const double* __restrict__ V, const double* __restrict__ 
 
 // w = (init ? 0 : w) + alpha * sum_k c[k] V[k]
 __global__ void k_vcomb(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ c, int nvec,
-                        long long n, double alpha, int init) {
+                        long long n, double alpha, int init, const int* __restrict__ done) {
+    if (done && *done) return;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
         double a = 0.0;
         for (int k = 0; k < nvec; ++k) a += c[k] * V[(long long)k * n + u];
@@ -150,28 +152,101 @@ __global__ void k_scale_to(const double* __restrict__ x, double* __restrict__ y,
         y[u] = a * x[u];
 }
 
-__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c, long long n) {
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c, long long n,
+                      const int* __restrict__ done) {
+    if (done && *done) return;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
         c[u] = a[u] - b[u];
 }
 
+// y = (*a) x
+__global__ void k_scale_dev(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ a,
+                            long long n, const int* __restrict__ done) {
+    if (done && *done) return;
+    const double s = *a;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        y[u] = s * x[u];
+}
+
+// Gram-Schmidt coefficients c[i] = sum_b partial[i * nbd + b] (b in order),
+// added to column col of H (row-major, m columns; set on the first pass).
+__global__ void k_gs_coef(const double* __restrict__ partial, int nbd, int nvec, double* __restrict__ H, int m,
+                          int col, double* __restrict__ c, int accumulate, const GmresState* st) {
+    if (st->done) return;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < nbd; ++q) v += partial[(long long)i * nbd + q];
+        c[i] = v;
+        double* h = H + (long long)i * m + col;
+        *h = accumulate ? *h + v : v;
+    }
+}
+
+// End of Arnoldi step k: H(k+1, k) = ||w|| (partials summed in order),
+// 1 / H(k+1, k) for the next basis vector, the previous Givens rotations on
+// column k, a new rotation that zeroes H(k+1, k), the rotated right-hand
+// side g, and the stop test on the residual estimate |g[k+1]|.
+__global__ void k_gm_fin(const double* __restrict__ partial, int nbd, double* __restrict__ H, int m, int k,
+                         double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ gv,
+                         double* __restrict__ hinv, GmresState* st) {
+    if (st->done || threadIdx.x != 0) return;
+    double ss = 0.0;
+    for (int q = 0; q < nbd; ++q) ss += partial[q];
+    const double h = sqrt(ss);
+    auto Hat = [&](int i, int j) -> double& { return H[(long long)i * m + j]; };
+    Hat(k + 1, k) = h;
+    *hinv = h > 0.0 ? 1.0 / h : 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double a = cs[i] * Hat(i, k) + sn[i] * Hat(i + 1, k);
+        Hat(i + 1, k) = -sn[i] * Hat(i, k) + cs[i] * Hat(i + 1, k);
+        Hat(i, k) = a;
+    }
+    const double den = hypot(Hat(k, k), Hat(k + 1, k));
+    cs[k] = Hat(k, k) / den;
+    sn[k] = Hat(k + 1, k) / den;
+    Hat(k, k) = den;
+    Hat(k + 1, k) = 0.0;
+    gv[k + 1] = -sn[k] * gv[k];
+    gv[k] = cs[k] * gv[k];
+    st->it += 1;
+    st->kk = k + 1;
+    if (fabs(gv[k + 1]) < st->tol_bn) st->done = 1;
+    else if (st->it >= st->maxit) st->done = 2;
+}
+
 }  // namespace
 
-void vec_mdot(const double* V, int nvec, const double* w, long long n, double* partial, int nblk, cudaStream_t s) {
-    k_mdot<<<dim3(nblk, nvec), 256, 0, s>>>(V, w, n, partial);
+void gm_gs_coef(const double* partial, int nbd, int nvec, double* H, int m, int col, double* c, bool accumulate,
+                const GmresState* st, cudaStream_t s) {
+    k_gs_coef<<<1, 256, 0, s>>>(partial, nbd, nvec, H, m, col, c, accumulate ? 1 : 0, st);
+    MSDD_LAUNCH_CHECK();
+}
+void gm_fin(const double* partial, int nbd, double* H, int m, int k, double* cs, double* sn, double* gv, double* hinv,
+            GmresState* st, cudaStream_t s) {
+    k_gm_fin<<<1, 32, 0, s>>>(partial, nbd, H, m, k, cs, sn, gv, hinv, st);
+    MSDD_LAUNCH_CHECK();
+}
+void vec_scale_dev(const double* x, double* y, const double* a, long long n, const int* done, cudaStream_t s) {
+    k_scale_dev<<<vec_blocks(n), 256, 0, s>>>(x, y, a, n, done);
+    MSDD_LAUNCH_CHECK();
+}
+
+void vec_mdot(const double* V, int nvec, const double* w, long long n, double* partial, int nblk, cudaStream_t s,
+              const int* done) {
+    k_mdot<<<dim3(nblk, nvec), 256, 0, s>>>(V, w, n, partial, done);
     MSDD_LAUNCH_CHECK();
 }
 void vec_comb(double* w, const double* V, const double* c, int nvec, long long n, double alpha, bool init,
-              cudaStream_t s) {
-    k_vcomb<<<vec_blocks(n), 256, 0, s>>>(w, V, c, nvec, n, alpha, init ? 1 : 0);
+              cudaStream_t s, const int* done) {
+    k_vcomb<<<vec_blocks(n), 256, 0, s>>>(w, V, c, nvec, n, alpha, init ? 1 : 0, done);
     MSDD_LAUNCH_CHECK();
 }
 void vec_scale_to(const double* x, double* y, double a, long long n, cudaStream_t s) {
     k_scale_to<<<vec_blocks(n), 256, 0, s>>>(x, y, a, n);
     MSDD_LAUNCH_CHECK();
 }
-void vec_sub(const double* a, const double* b, double* c, long long n, cudaStream_t s) {
-    k_sub<<<vec_blocks(n), 256, 0, s>>>(a, b, c, n);
+void vec_sub(const double* a, const double* b, double* c, long long n, cudaStream_t s, const int* done) {
+    k_sub<<<vec_blocks(n), 256, 0, s>>>(a, b, c, n, done);
     MSDD_LAUNCH_CHECK();
 }
 

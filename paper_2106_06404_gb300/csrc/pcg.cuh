@@ -36,13 +36,34 @@ void pcg_fin_beta(PcgScalars* sc, const double* partial, int nblocks, cudaStream
 // p = z + beta p
 void pcg_update_p(PcgScalars* sc, const double* z, double* p, long long n, cudaStream_t s);
 
-// GMRES building blocks (Arnoldi vectors V[k] = V + k n, device).
-// partial[k * nblk + b]: block b's share of V[k] . w, k < nvec (sum on the host).
-void vec_mdot(const double* V, int nvec, const double* w, long long n, double* partial, int nblk, cudaStream_t s);
+// GMRES building blocks (Arnoldi vectors V[k] = V + k n, device).  Kernels
+// given `done` return at once when it is set, so Arnoldi steps can be
+// enqueued ahead of the host's convergence test.
+// partial[k * nblk + b]: block b's share of V[k] . w, k < nvec.
+void vec_mdot(const double* V, int nvec, const double* w, long long n, double* partial, int nblk, cudaStream_t s,
+              const int* done = nullptr);
 // w = (init ? 0 : w) + alpha sum_k c[k] V[k] (c device, nvec entries)
 void vec_comb(double* w, const double* V, const double* c, int nvec, long long n, double alpha, bool init,
-              cudaStream_t s);
+              cudaStream_t s, const int* done = nullptr);
 void vec_scale_to(const double* x, double* y, double a, long long n, cudaStream_t s);   // y = a x
-void vec_sub(const double* a, const double* b, double* c, long long n, cudaStream_t s);  // c = a - b
+void vec_sub(const double* a, const double* b, double* c, long long n, cudaStream_t s,
+             const int* done = nullptr);                                               // c = a - b
+void vec_scale_dev(const double* x, double* y, const double* a, long long n, const int* done,
+                   cudaStream_t s);                                                    // y = (*a) x
+
+// Device state of one GMRES cycle.
+struct GmresState {
+    int done;      // 0 running, 1 residual estimate below tol_bn, 2 maxit
+    int it;        // Arnoldi steps so far (all cycles)
+    int maxit;
+    int kk;        // steps of the current cycle
+    double tol_bn; // tol * ||b||
+};
+// c[i] = sum_b partial[i * nbd + b], i < nvec; H(i, col) = c[i] (+= on later passes)
+void gm_gs_coef(const double* partial, int nbd, int nvec, double* H, int m, int col, double* c, bool accumulate,
+                const GmresState* st, cudaStream_t s);
+// H(k+1, k) = sqrt(sum partial[0..nbd)), *hinv = 1 / H(k+1, k), Givens rotations, stop test
+void gm_fin(const double* partial, int nbd, double* H, int m, int k, double* cs, double* sn, double* gv, double* hinv,
+            GmresState* st, cudaStream_t s);
 
 }  // namespace msdd
