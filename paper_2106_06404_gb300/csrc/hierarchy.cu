@@ -1254,40 +1254,49 @@ int Hierarchy::solve(const double* b, double tol, int maxit, double* xout, doubl
 // z = B_h r: the fine level as restricted additive Schwarz (local solutions
 // weighted by chi = 1/N(x)), then each coarser level in turn on the current
 // residual, z <- z + B_l (r - A z), down to the coarsest (Section 2.1, Eq.
-// subspace_iteration applied level by level; the order is a reading).  All
-// on the main stream; every kernel returns at once when `done` is set.
+// subspace_iteration applied level by level; the order is a reading).  With
+// three levels the coarsest level's residual is formed on level 1: its space
+// Phi Z_1 lies in level 1's space Phi, so Z_1^T Phi^T (r - A (z + Phi z1)) =
+// Z_1^T (v1 - A_1 z1) with the Galerkin matrix A_1 = Phi^T A Phi and
+// v1 = Phi^T (r - A z); both coarse corrections are then prolonged together.
+// All on the main stream; every kernel returns at once when `done` is set.
 void Hierarchy::apply_hybrid(const double* rr, double* zz, const int* done) {
     double* r1 = levels == 2 ? r0buf.p : v1.p;
     if ((long long)hyb_t.n < nun) {
         hyb_t.alloc(nun);
         hyb_q.alloc(nun);
     }
+    if (levels == 3 && !d_gemm_a1.p) {
+        GemmItem a;
+        a.aoff = 0; a.lda = (int)n1;
+        a.boff = 0; a.ldb = 1;
+        a.coff = 0; a.ldc = 1;
+        a.m = (int)n1; a.n = 1; a.k = (int)n1;
+        d_gemm_a1 = upload_vec(std::vector<GemmItem>{a}, st);
+    }
     fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, rr, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p,
                          d_c1off.p, r1, Pf, done, st);
     tile_solve(fdir, frhs.p, 1, 1, nullptr, st, done);
     fine_combine_mode(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p, r1,
                       zz, rr, nullptr, nblocks, done, COMB_Y | COMB_RAS, st);
-    for (int l = L - 1; l >= 0; --l) {
-        spmv_stencil_dot(g, stencil.p, zz, hyb_q.p, partial.p, nblocks, done, st);
-        vec_sub(rr, hyb_q.p, hyb_t.p, nun, st, done);                       // t = r - A z
-        fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, hyb_t.p, frhs.p, Phi.p, d_phioff.p, ldphi,
-                             d_fm.p, d_c1off.p, r1, Pf, done, st);      // r1 = Phi^T t
-        const double* zc;
-        if (levels == 2) {
-            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, done);
-            zc = y0buf.p;
-        } else if (l == 1) {
-            gemv_batched(d_gemm_y1.p, Pm, 0, 1.0, Minv.p, v1.p, 0.0, z1t.p, gemm_y1_maxm, st, done);
-            zc = z1t.p;
-        } else {
-            gemv_batched(d_gemm_r0.p, Pm, 1, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, st, done);
-            gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, done);
-            gemv_batched(d_gemm_z1.p, Pm, 0, 1.0, Zb.p, y0buf.p, 0.0, z1t.p, gemm_z1_maxm, st, done);
-            zc = z1t.p;
-        }
-        fine_combine_mode(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p,
-                          zc, zz, rr, nullptr, nblocks, done, COMB_COARSE | COMB_ACC, st);
+    spmv_stencil_dot(g, stencil.p, zz, hyb_q.p, partial.p, nblocks, done, st);
+    vec_sub(rr, hyb_q.p, hyb_t.p, nun, st, done);                           // t = r - A z
+    fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, hyb_t.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p,
+                         d_c1off.p, r1, Pf, done, st);                      // r1 = Phi^T t
+    const double* zc;
+    if (levels == 2) {
+        gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, done);
+        zc = y0buf.p;
+    } else {
+        gemv_batched(d_gemm_y1.p, Pm, 0, 1.0, Minv.p, v1.p, 0.0, z1t.p, gemm_y1_maxm, st, done);      // z1
+        gemv_batched(d_gemm_a1.p, 1, 0, -1.0, A1.p, z1t.p, 1.0, v1.p, (int)n1, st, done);          // v1 -= A_1 z1
+        gemv_batched(d_gemm_r0.p, Pm, 1, 1.0, Zb.p, v1.p, 0.0, r0buf.p, gemm_r0_maxm, st, done);
+        gemv_batched(d_gemm_y0.p, 1, 0, 1.0, A0inv.p, r0buf.p, 0.0, y0buf.p, (int)n0, st, done);
+        gemv_batched(d_gemm_z1.p, Pm, 0, 1.0, Zb.p, y0buf.p, 1.0, z1t.p, gemm_z1_maxm, st, done);    // z1 += Z_1 y0
+        zc = z1t.p;
     }
+    fine_combine_mode(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p, zc,
+                      zz, rr, nullptr, nblocks, done, COMB_COARSE | COMB_ACC, st);
 }
 
 // Flexible GMRES(restart) (Saad) with the hybrid preconditioner: x0 = 0,

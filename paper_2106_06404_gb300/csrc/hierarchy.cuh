@@ -165,6 +165,7 @@ struct Hierarchy {
     // hybrid form (multiplicative over levels, restricted additive Schwarz on
     // the fine level) and right-preconditioned GMRES with it (Section 5)
     DevBuf<double> hyb_t, hyb_q;
+    DevBuf<GemmItem> d_gemm_a1;     // v1 -= A_1 z1 (one n1 x n1 item)
     void apply_hybrid(const double* rr, double* zz, const int* done = nullptr);
     int solve_gmres(const double* b, double tol, int restart, int maxit, double* xout, double* relres);
     size_t device_bytes() const;
