@@ -5,6 +5,8 @@ namespace msdd {
 
 namespace {
 
+constexpr int COMBINE_NT = 1024;
+
 __global__ void k_block_sum(const SumItem* __restrict__ items, const long long* __restrict__ contrib,
                             const double* __restrict__ G, double* __restrict__ dst) {
     const SumItem it = items[blockIdx.x];
@@ -113,16 +115,26 @@ __global__ void k_dense_shift(const double* __restrict__ A, double* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) k_fine_gather_restrict(
+// One CTA of 512 threads per fine subdomain; templated on the dimension so
+// that node coordinates and box bounds stay in registers.
+template <int D>
+__global__ void __launch_bounds__(512) k_fine_gather_restrict(
     Geom g, const ProbBox* __restrict__ fine, const long long* __restrict__ droff, const int* __restrict__ dK,
     const double* __restrict__ r, double* __restrict__ rhs, const double* __restrict__ Phi,
     const long long* __restrict__ phioff, int ldphi, const int* __restrict__ m_, const long long* __restrict__ c1off,
     double* __restrict__ r1, const int* __restrict__ done) {
-    __shared__ double red[PMAX][8];
+    __shared__ double red[PMAX][16];
     if (done && *done) return;
     const int j = blockIdx.x;
-    const ProbBox pb = fine[j];
-    const int n = box_size(pb.dlo, pb.dhi, g.dim);
+    int dlo[3], wd[3];
+    int n = 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        dlo[d] = d < D ? fine[j].dlo[d] : 0;
+        const int hi = d < D ? fine[j].dhi[d] : 0;
+        wd[d] = hi >= dlo[d] ? hi - dlo[d] + 1 : 0;
+        if (d < D) n *= wd[d];
+    }
     const int rows = dK[j] * NB;
     const int m = m_[j];
     const int t = threadIdx.x;
@@ -133,9 +145,16 @@ __global__ void __launch_bounds__(256) k_fine_gather_restrict(
     for (int rr = t; rr < rows; rr += blockDim.x) {
         double v = 0.0;
         if (rr < n) {
-            int x[3];
-            box_coords(rr, pb.dlo, pb.dhi, g.dim, x);
-            v = r[unknown_index(g, x)];
+            int rem = rr;
+            long long u = 0, stride = 1;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int xd = dlo[d] + rem % wd[d];
+                rem /= wd[d];
+                u += (xd - g.ulo[d]) * stride;
+                stride *= g.ushape[d];
+            }
+            v = r[u];
             const double* ph = Phi + phioff[j] + (long long)rr * ldphi;
 #pragma unroll
             for (int k = 0; k < PMAX; ++k)
@@ -153,27 +172,34 @@ __global__ void __launch_bounds__(256) k_fine_gather_restrict(
     __syncthreads();
     if (t < m) {
         double v = 0.0;
-        for (int w = 0; w < 8; ++w) v += red[t][w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[t][w];
         r1[c1off[j] + t] = v;
     }
 }
 
-__global__ void __launch_bounds__(256) k_fine_combine(
+// Threads over the unknowns (the grid is the dot-product block count);
+// templated on the dimension so that node coordinates and the covering
+// subdomains' box bounds stay in registers.  32-bit coordinate divisions
+// (the set-up rejects 2^31 unknowns or more).
+template <int D>
+__global__ void __launch_bounds__(COMBINE_NT, 1) k_fine_combine(
     Geom g, CombineMaps cm, const ProbBox* __restrict__ fine, const long long* __restrict__ droff,
     const double* __restrict__ y, const double* __restrict__ Phi, const long long* __restrict__ phioff, int ldphi,
     const int* __restrict__ m_, const long long* __restrict__ c1off, const double* __restrict__ z1,
     double* __restrict__ z, const double* __restrict__ r, double* __restrict__ partial, long long nun,
     const int* __restrict__ done, int mode) {
-    __shared__ double red[256];
+    __shared__ double red[COMBINE_NT];
     if (done && *done) return;
     double part = 0.0;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
-        int x[3] = {0, 0, 0};
-        long long rem = u;
-        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-        for (int d = 0; d < g.dim; ++d) {
-            x[d] = g.ulo[d] + (int)(rem % g.ushape[d]);
-            rem /= g.ushape[d];
+        int x[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        unsigned rem = (unsigned)u;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const unsigned sd = (unsigned)g.ushape[d];
+            const unsigned q = rem / sd;
+            x[d] = g.ulo[d] + (int)(rem - q * sd);
+            rem = q;
             lo[d] = cm.first[d][x[d]];
             hi[d] = cm.last[d][x[d]];
         }
@@ -182,9 +208,14 @@ __global__ void __launch_bounds__(256) k_fine_combine(
         for (int pz = lo[2]; pz <= hi[2]; ++pz)
             for (int py = lo[1]; py <= hi[1]; ++py)
                 for (int px = lo[0]; px <= hi[0]; ++px) {
-                    int j = px + cm.parts[0] * (py + cm.parts[1] * pz);
-                    const ProbBox pb = fine[j];
-                    int loc = box_index(pb.dlo, pb.dhi, x, g.dim);
+                    const int j = px + cm.parts[0] * (py + cm.parts[1] * pz);
+                    int loc = 0, stride = 1;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        const int dl = fine[j].dlo[d];
+                        loc += (x[d] - dl) * stride;
+                        stride *= fine[j].dhi[d] - dl + 1;
+                    }
                     double v = (mode & COMB_Y) ? y[droff[j] + loc] : 0.0;
                     if (mode & COMB_COARSE) {
                         const int m = m_[j];
@@ -268,7 +299,11 @@ void fine_gather_restrict(const Geom& g, const ProbBox* d_fine, const long long*
                           const int* d_m, const long long* d_c1off, double* r1, int P, const int* done,
                           cudaStream_t s) {
     if (P == 0) return;
-    k_fine_gather_restrict<<<P, 256, 0, s>>>(g, d_fine, d_droff, d_K, r, rhs, Phi, d_phioff, ldphi, d_m, d_c1off, r1,
+    if (g.dim == 3)
+        k_fine_gather_restrict<3><<<P, 512, 0, s>>>(g, d_fine, d_droff, d_K, r, rhs, Phi, d_phioff, ldphi, d_m, d_c1off, r1,
+                                             done);
+    else
+        k_fine_gather_restrict<2><<<P, 512, 0, s>>>(g, d_fine, d_droff, d_K, r, rhs, Phi, d_phioff, ldphi, d_m, d_c1off, r1,
                                              done);
     MSDD_LAUNCH_CHECK();
 }
@@ -286,8 +321,12 @@ void fine_combine_mode(const Geom& g, const CombineMaps& cm, const ProbBox* d_fi
                        const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
                        int nblocks, const int* done, int mode, cudaStream_t s) {
     long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
-    k_fine_combine<<<nblocks, 256, 0, s>>>(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off, z1, z, r,
-                                           partial, nun, done, mode);
+    if (g.dim == 3)
+        k_fine_combine<3><<<nblocks, COMBINE_NT, 0, s>>>(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off,
+                                                         z1, z, r, partial, nun, done, mode);
+    else
+        k_fine_combine<2><<<nblocks, COMBINE_NT, 0, s>>>(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off,
+                                                         z1, z, r, partial, nun, done, mode);
     MSDD_LAUNCH_CHECK();
 }
 

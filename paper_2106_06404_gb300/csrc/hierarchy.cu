@@ -390,6 +390,8 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     prof.solves_only = opt.profile == 2;
     g = make_geom(mesh, coeff);
     nun = (long long)g.ushape[0] * g.ushape[1] * g.ushape[2];
+    // node coordinates in the combine kernel use 32-bit divisions
+    if (nun >= (1LL << 31)) throw MsddError(MSDD_ERR_UNSUPPORTED, "more than 2^31 unknowns");
     upload_reference(g);
 
     memset(&stats, 0, sizeof(stats));

@@ -13,9 +13,9 @@ __device__ double sum_partials(const double* partial, int nblocks) {
     return v;
 }
 
-__global__ void k_start(const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r, long long n,
+__global__ void __launch_bounds__(1024) k_start(const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r, long long n,
                         double* __restrict__ partial) {
-    __shared__ double red[256];
+    __shared__ double red[1024];
     double part = 0.0;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
         double v = b[u];
@@ -65,10 +65,10 @@ __global__ void k_fin_alpha(PcgScalars* sc, const double* __restrict__ partial, 
     }
 }
 
-__global__ void k_axpy(const PcgScalars* sc, double* __restrict__ x, double* __restrict__ r,
+__global__ void __launch_bounds__(1024) k_axpy(const PcgScalars* sc, double* __restrict__ x, double* __restrict__ r,
                        const double* __restrict__ p, const double* __restrict__ q, long long n,
                        double* __restrict__ partial) {
-    __shared__ double red[256];
+    __shared__ double red[1024];
     if (sc->done) return;
     const double a = sc->alpha;
     double part = 0.0;
@@ -251,7 +251,7 @@ void vec_sub(const double* a, const double* b, double* c, long long n, cudaStrea
 }
 
 void pcg_start(const double* b, double* x, double* r, long long n, double* partial, int nblocks, cudaStream_t s) {
-    k_start<<<nblocks, 256, 0, s>>>(b, x, r, n, partial);
+    k_start<<<nblocks, 1024, 0, s>>>(b, x, r, n, partial);
     MSDD_LAUNCH_CHECK();
 }
 void pcg_fin_bb(PcgScalars* sc, const double* partial, int nblocks, double tol, int maxit, cudaStream_t s) {
@@ -271,7 +271,7 @@ void pcg_fin_alpha(PcgScalars* sc, const double* partial, int nblocks, cudaStrea
 }
 void pcg_axpy(PcgScalars* sc, double* x, double* r, const double* p, const double* q, long long n, double* partial,
               int nblocks, cudaStream_t s) {
-    k_axpy<<<nblocks, 256, 0, s>>>(sc, x, r, p, q, n, partial);
+    k_axpy<<<nblocks, 1024, 0, s>>>(sc, x, r, p, q, n, partial);
     MSDD_LAUNCH_CHECK();
 }
 void pcg_fin_rr(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s) {

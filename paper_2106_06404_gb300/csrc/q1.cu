@@ -516,23 +516,29 @@ __global__ void k_global_stencil(Geom g, double* __restrict__ S, long long nun) 
 
 // q = A p from the stored stencil (one thread per unknown, neighbours of an
 // x-row are contiguous), plus partial sums of p.q.
-__global__ void __launch_bounds__(256) k_spmv_stencil_dot(Geom g, const double* __restrict__ S,
-                                                          const double* __restrict__ p, double* __restrict__ q,
-                                                          long long nun, double* __restrict__ partial,
-                                                          const int* __restrict__ done) {
-    __shared__ double red[256];
+// q = S p over the unknowns with the stored 3^D-point stencil, and block
+// partial sums of p.q.  Every neighbour index is clamped into [0, nun): a
+// neighbour outside the unknown box has coefficient exactly 0 in S, so its
+// term adds nothing and the loads need no branch.  1024 threads a block
+// (the grid is the dot-product block count, a few blocks per SM).
+template <int D>
+__global__ void __launch_bounds__(1024) k_spmv_stencil_dot(Geom g, const double* __restrict__ S,
+                                                           const double* __restrict__ p, double* __restrict__ q,
+                                                           long long nun, double* __restrict__ partial,
+                                                           const int* __restrict__ done) {
+    __shared__ double red[1024];
     if (done && *done) return;
-    const int noff = g.dim == 3 ? 27 : 9;
-    const long long sx = 1, sy = g.ushape[0], sz = (long long)g.ushape[0] * g.ushape[1];
+    constexpr int NOFF = D == 3 ? 27 : 9;
+    const long long sy = g.ushape[0], sz = (long long)g.ushape[0] * g.ushape[1];
     double part = 0.0;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nun; u += (long long)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int oi = 0; oi < noff; ++oi) {
-            double c = S[(long long)oi * nun + u];
-            if (c != 0.0) {
-                long long v = u + (oi % 3 - 1) * sx + ((oi / 3) % 3 - 1) * sy + (g.dim == 3 ? oi / 9 - 1 : 0) * sz;
-                acc += c * p[v];
-            }
+#pragma unroll
+        for (int oi = 0; oi < NOFF; ++oi) {
+            const double c = S[(long long)oi * nun + u];
+            long long v = u + (oi % 3 - 1) + ((oi / 3) % 3 - 1) * sy + (D == 3 ? (oi / 9 - 1) * sz : 0);
+            v = v < 0 ? 0 : (v >= nun ? nun - 1 : v);
+            acc += c * p[v];
         }
         q[u] = acc;
         part += acc * p[u];
@@ -693,7 +699,10 @@ void global_stencil(const Geom& g, double* S, cudaStream_t s) {
 void spmv_stencil_dot(const Geom& g, const double* S, const double* p, double* q, double* partial, int nblocks,
                       const int* done, cudaStream_t s) {
     long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
-    k_spmv_stencil_dot<<<nblocks, 256, 0, s>>>(g, S, p, q, nun, partial, done);
+    if (g.dim == 3)
+        k_spmv_stencil_dot<3><<<nblocks, 1024, 0, s>>>(g, S, p, q, nun, partial, done);
+    else
+        k_spmv_stencil_dot<2><<<nblocks, 1024, 0, s>>>(g, S, p, q, nun, partial, done);
     MSDD_LAUNCH_CHECK();
 }
 
