@@ -76,6 +76,19 @@ def test_num_unknowns_and_validation(lib):
     assert st == -1 and b"invalid mesh" in lib.msdd_last_error()
 
 
+def test_hybrid_and_gmres_reject_null_arguments(lib):
+    """The hybrid preconditioner and GMRES entry points validate their
+    arguments before any device work."""
+    buf = (ctypes.c_double * 4)()
+    it = ctypes.c_int(-7)
+    rel = ctypes.c_double(0.0)
+    st = lib.msdd_apply_hybrid_preconditioner(None, buf, buf)
+    assert st == -1 and b"NULL" in lib.msdd_last_error()
+    st = lib.msdd_solve_gmres(None, buf, ctypes.c_double(1e-8), 200, 1000, buf, ctypes.byref(it), ctypes.byref(rel))
+    assert st == -1 and b"NULL" in lib.msdd_last_error()
+    assert it.value == -7                                 # outputs untouched on error
+
+
 def test_product_package_does_not_import_oracle():
     code = ("import sys; sys.path.insert(0, %r); import paper_2106_06404_gb300; "
             "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules), 'oracle imported'") % ROOT
