@@ -124,3 +124,27 @@ def test_single_subdomain_hybrid_is_exact():
     assert np.linalg.norm(z - xd) <= 1e-10 * np.linalg.norm(xd)
     x, it, _ = method.gmres(H.A, b, H.apply_hybrid, 1e-10)
     assert it == 1
+
+
+def test_coarsest_residual_from_level_one():
+    """Three levels: the coarsest space lies in level 1's space (P_0 = P_1 Z_1),
+    so the coarsest level's restricted residual after a level-1 correction
+    P_1 z1 equals Z_1^T (P_1^T (r - A z) - A_1 z1) with the Galerkin matrix
+    A_1 = P_1^T A P_1.  The GPU's hybrid preconditioner forms it that way; here
+    the identity is checked on the oracle's own spaces."""
+    mesh = fem.Mesh((16, 16), 0b1)
+    kap = si.channels_2d(16, 2, 1e4, seed=7)
+    H = method.Hierarchy(mesh, kap, (4, 4), 1, 3, (2, 2), 4, 0.3)
+    P1 = H.levels[1].P.toarray() if hasattr(H.levels[1].P, "toarray") else H.levels[1].P
+    P0 = H.levels[1].P_coarse
+    P0 = P0.toarray() if hasattr(P0, "toarray") else P0
+    Z1, *_ = np.linalg.lstsq(P1, P0, rcond=None)
+    assert np.linalg.norm(P1 @ Z1 - P0) <= 1e-10 * np.linalg.norm(P0)       # nested spaces
+    A = H.A.toarray()
+    A1 = P1.T @ A @ P1
+    rng = np.random.default_rng(3)
+    r, z = rng.standard_normal(H.n), rng.standard_normal(H.n)
+    z1 = rng.standard_normal(P1.shape[1])
+    plain = P0.T @ (r - A @ (z + P1 @ z1))
+    nested = Z1.T @ (P1.T @ (r - A @ z) - A1 @ z1)
+    assert np.linalg.norm(plain - nested) <= 1e-9 * np.linalg.norm(plain)
