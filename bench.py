@@ -72,6 +72,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """The job's time is that of its slowest rank: the largest value over all
+    ranks of the process group (a CPU tensor for gloo, a device tensor for
+    NCCL); the value itself with no process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(name, seed):
     import synthetic_inputs as si
     return si.grf512(seed=seed) if name == "grf512" else si.channels64(seed=seed)
@@ -295,11 +307,7 @@ def run_ours(args, rank, world, local_rank):
             if k >= args.warmup:
                 e2e_times.append(time.perf_counter() - t0)
 
-    total = sum(t_chosen)
-    if dist is not None:
-        tt = torch.tensor([total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
+    total = max_over_ranks(sum(t_chosen), dist, dev)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()

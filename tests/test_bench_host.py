@@ -1,0 +1,79 @@
+"""Host logic of bench.py that needs no GPU: the replica workloads of the
+ranks, the max-over-ranks timing on a world-size-2 gloo process group, and
+the reference arm (the oracle on a bounded sample) with its JSON line on rank
+0 and no output on the other ranks."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_replica_workloads_are_seeded_by_rank():
+    a = bench.workload("channels64", 0).coefficient()
+    b = bench.workload("channels64", 1).coefficient()
+    assert a.shape == b.shape and not np.array_equal(a, b)
+    assert np.array_equal(a, bench.workload("channels64", 0).coefficient())
+
+
+def test_max_over_ranks_without_process_group():
+    assert bench.max_over_ranks(3.25) == 3.25
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    v = bench.max_over_ranks(1.5 + rank, dist)
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out, "r%d" % rank), "w") as f:
+        f.write(repr(v))
+
+
+def test_max_over_ranks_gloo_world_size_2(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    assert [float(open(tmp_path / ("r%d" % r)).read()) for r in range(2)] == [2.5, 2.5]
+
+
+def _run_reference(rank, world):
+    env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                           "--warmup", "0", "--workload", "channels64", "--cpu-subdomains", "1"],
+                          capture_output=True, text=True, env=env, timeout=300)
+
+
+def test_reference_arm_json_line_on_rank_0():
+    p = _run_reference(0, 1)
+    assert p.returncode == 0, p.stderr
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["higher_is_better"] is False
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["value"] > 0
+
+
+def test_reference_arm_other_ranks_exit_silently():
+    p = _run_reference(1, 2)
+    assert p.returncode == 0, p.stderr
+    assert p.stdout.strip() == ""
