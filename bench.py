@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--forms", choices=["both", "chosen"], default="both",
                     help="chosen: time only the chosen form (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-solvers", action="store_true",
+                    help="skip the PCG / hybrid-GMRES comparison after the timed steps")
     ap.add_argument("--no-breakdown", action="store_true",
                     help="skip the extra all-families profiled step (profiling runs: one step only)")
     return ap.parse_args()
@@ -82,6 +84,33 @@ def max_over_ranks(value, dist=None, device=None):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def solver_leg(H, b, steps, warmup, sync):
+    """Median wall time per solve (ms, synchronised on both sides) of PCG with
+    the additive preconditioner and of flexible GMRES with the hybrid one on
+    the same hierarchy, with iterations and residuals.  Outside the timed
+    step; a failure is recorded, not raised."""
+    out = {}
+    for name, f in (("pcg_additive", lambda: H.solve(b, tol=TOL, allow_maxit=True)),
+                    ("gmres_hybrid", lambda: H.solve_gmres(b, tol=TOL, allow_maxit=True))):
+        try:
+            for _ in range(warmup):
+                f()
+            ts, it, rel = [], 0, float("nan")
+            for _ in range(max(1, steps)):
+                sync()
+                t0 = time.perf_counter()
+                _, it, rel = f()
+                sync()
+                ts.append(time.perf_counter() - t0)
+            out[name] = {"ms": round(1e3 * statistics.median(ts), 3), "iterations": int(it),
+                         "rel_residual": float(rel)}
+        except Exception as e:                                    # recorded in the JSON line
+            out[name] = {"error": repr(e)[:200]}
+    out["note"] = ("one hierarchy of the chosen form; pcg rel_residual is the recursive residual, "
+                   "gmres rel_residual the true residual (FP64 attainable accuracy ~1e-6 here)")
+    return out
 
 
 def workload(name, seed):
@@ -307,6 +336,17 @@ def run_ours(args, rank, world, local_rank):
             if k >= args.warmup:
                 e2e_times.append(time.perf_counter() - t0)
 
+        # solver comparison on one hierarchy (not part of the timed step)
+        solvers = None
+        if not args.no_solvers:
+            try:
+                H = pkg.Hierarchy(w.n, kappa, w.parts, w.overlap, w.levels, w.group, w.nev_max, w.eta,
+                                  dirichlet_faces=w.dirichlet_faces, precision=1)
+                solvers = solver_leg(H, b, args.steps, args.warmup, lambda: torch.cuda.synchronize(dev))
+                H.close()
+            except Exception as e:
+                solvers = {"error": repr(e)[:200]}
+
     total = max_over_ranks(sum(t_chosen), dist, dev)
     if rank != 0:
         if dist is not None:
@@ -391,6 +431,7 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(kap_np.nbytes + n * 8), "d2h_bytes_per_step": int(n * 8)},
         "gpu_launches": int(launches),
         "cpu_baseline": cpu_baseline_obj(cpu, w.name) if cpu_p is not None else None,
+        "solvers": solvers,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -77,3 +77,30 @@ def test_reference_arm_other_ranks_exit_silently():
     p = _run_reference(1, 2)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+class _FakeHierarchy:
+    def __init__(self, fail_gmres):
+        self.fail_gmres = fail_gmres
+        self.calls = {"solve": 0, "solve_gmres": 0}
+
+    def solve(self, b, tol=1e-8, allow_maxit=False):
+        self.calls["solve"] += 1
+        return None, 66, 9e-9
+
+    def solve_gmres(self, b, tol=1e-8, allow_maxit=False):
+        self.calls["solve_gmres"] += 1
+        if self.fail_gmres:
+            raise RuntimeError("no convergence")
+        return None, 35, 8e-7
+
+
+def test_solver_leg_times_both_solvers_and_records_failures():
+    H = _FakeHierarchy(fail_gmres=False)
+    syncs = []
+    out = bench.solver_leg(H, None, steps=3, warmup=2, sync=lambda: syncs.append(1))
+    assert H.calls == {"solve": 5, "solve_gmres": 5} and len(syncs) == 12
+    assert out["pcg_additive"]["iterations"] == 66 and out["gmres_hybrid"]["iterations"] == 35
+    assert out["gmres_hybrid"]["rel_residual"] == 8e-7 and out["pcg_additive"]["ms"] >= 0.0
+    out = bench.solver_leg(_FakeHierarchy(fail_gmres=True), None, steps=1, warmup=0, sync=lambda: None)
+    assert "error" in out["gmres_hybrid"] and out["pcg_additive"]["iterations"] == 66
