@@ -39,7 +39,7 @@ typedef enum msdd_status {
     MSDD_OK = 0,
     MSDD_ERR_INVALID_ARG = -1,        /* a size, pointer or option is out of range          */
     MSDD_ERR_NOT_SPD = -2,            /* a local factorisation met a non-positive pivot      */
-    MSDD_ERR_NO_CONVERGENCE = -3,     /* CG reached maxit (x holds the last iterate)          */
+    MSDD_ERR_NO_CONVERGENCE = -3,     /* CG or GMRES reached maxit (x holds the last iterate) */
     MSDD_ERR_EIG_NO_CONVERGENCE = -4, /* subspace iteration reached eig_maxit (set-up kept)   */
     MSDD_ERR_OOM = -5,                /* device allocation failed                            */
     MSDD_ERR_CUDA = -6,               /* any other CUDA runtime error                        */
@@ -163,10 +163,16 @@ typedef struct msdd_stats {
 
 typedef struct msdd_hierarchy msdd_hierarchy;   /* opaque, library-owned */
 
-/* Fill *opt with the defaults listed above.  Never fails for non-NULL opt. */
+/* Fill *opt (host) with the defaults listed in msdd_options (precision 0,
+ * automatic block size, eig_maxit 200, sigma 1e-2, eig_tol 1e-6, automatic
+ * reg_tol, fp32_start_iters 20, no warm start, legacy default stream).
+ * MSDD_ERR_INVALID_ARG for NULL opt; no device work. */
 msdd_status msdd_default_options(msdd_options* opt);
 
-/* Number of unknowns of the mesh, or -1 if the mesh is invalid. */
+/* Number of unknowns of the mesh: its nodes not on a Dirichlet face (the
+ * length of every vector argument below).  -1 if the mesh is invalid (dim not
+ * 2 or 3, an axis without elements, or no Dirichlet face, which would leave A
+ * singular).  Host only, no device work. */
 long long msdd_num_unknowns(const msdd_mesh* mesh);
 
 /* Build the hierarchy (Section 2.3 construction, recursive over levels):
@@ -182,11 +188,19 @@ msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msd
 msdd_status msdd_solve(msdd_hierarchy* h, const double* b, double tol, int maxit, double* x, int* iterations,
                        double* rel_residual);
 
-/* Same with host buffers b, x (n doubles each); copies are part of the call. */
+/* msdd_solve with host buffers: b and x are host arrays of n doubles; the
+ * host-to-device copy of b, the solve and the device-to-host copy of x all
+ * happen inside the call (device staging buffers owned by the library).  On
+ * MSDD_ERR_NO_CONVERGENCE x still receives the last iterate; on any other
+ * error x is left unspecified. */
 msdd_status msdd_solve_host(msdd_hierarchy* h, const double* b, double tol, int maxit, double* x,
                             int* iterations, double* rel_residual);
 
-/* z = B r for the multilevel preconditioner (device, n doubles each). */
+/* z = B r, one application of the additive multilevel preconditioner that
+ * msdd_solve uses (Section 2.1, Eq. mlsdd): fine local Dirichlet solves plus
+ * the coarse levels down to the coarsest direct solve.  B is symmetric
+ * positive definite.  r, z: device, n doubles each, distinct; synchronous on
+ * the hierarchy's stream.  MSDD_ERR_INVALID_ARG for NULL arguments. */
 msdd_status msdd_apply_preconditioner(msdd_hierarchy* h, const double* r, double* z);
 
 /* Hybrid form of the preconditioner, the one used inside GMRES in Section 5
@@ -220,12 +234,23 @@ msdd_status msdd_apply_hybrid_preconditioner(msdd_hierarchy* h, const double* r,
 msdd_status msdd_solve_gmres(msdd_hierarchy* h, const double* b, double tol, int restart, int maxit, double* x,
                              int* iterations, double* rel_residual);
 
-/* y = A x (device, n doubles each). */
+/* y = A x, the global stiffness matrix of the form a_h (Section 3.4, Eq.
+ * ScalarBVP) on the unknowns, applied element by element from the
+ * coefficient (not from the stored stencil that CG uses), so it serves as an
+ * independent check of residuals.  x, y: device, n doubles each, distinct;
+ * synchronous.  MSDD_ERR_INVALID_ARG for NULL arguments. */
 msdd_status msdd_apply_operator(msdd_hierarchy* h, const double* x, double* y);
 
-/* Load vector l(v) = int f v for constant f (device, n doubles). */
+/* Load vector b_u = l(phi_u) = int f phi_u dx for constant f over the
+ * unknowns of `mesh` (Section 3.4, the form l; no Neumann flux).  b: device,
+ * n doubles (n = msdd_num_unknowns(mesh)), written on `stream`
+ * (cudaStream_t, NULL = legacy default stream); returns after completion.
+ * MSDD_ERR_INVALID_ARG for an invalid mesh or NULL b.  Needs no hierarchy. */
 msdd_status msdd_assemble_rhs(const msdd_mesh* mesh, double f, double* b, void* stream);
 
+/* Copy the hierarchy's statistics (set-up counts and timings, the last
+ * solve's iterations and residual, kernel-family profile) into *out (host).
+ * MSDD_ERR_INVALID_ARG for NULL arguments; no device work. */
 msdd_status msdd_get_stats(const msdd_hierarchy* h, msdd_stats* out);
 
 /* Ritz values of subdomain `subdomain` on level `level` (1 <= level <= L),
@@ -245,6 +270,9 @@ msdd_status msdd_get_eigen_residuals(const msdd_hierarchy* h, int level, int sub
  * row-major, unknown-major), m = selected count; *m_out receives m. */
 msdd_status msdd_get_fine_basis(const msdd_hierarchy* h, int subdomain, double* out, long long cap, int* m_out);
 
+/* Free the hierarchy and every device buffer it holds (they return to the
+ * library's device cache; see msdd_release_cache).  NULL is ignored.  The
+ * coefficient array passed to msdd_setup may be freed afterwards. */
 void msdd_destroy(msdd_hierarchy* h);
 
 /* ---- device memory -------------------------------------------------------
@@ -266,7 +294,9 @@ long long msdd_cached_bytes(void);
  * (a replayed CUDA graph counts the kernels it holds).  Not thread-safe. */
 long long msdd_kernel_launches(void);
 
-/* Message of the last failure on this thread ("" if none). */
+/* Message of the last failure on the calling thread ("" if none; most entry
+ * points clear it when they start).  The string is owned by the library;
+ * copy it before the next call on this thread. */
 const char* msdd_last_error(void);
 
 /* ---- batched SPD (semi-definite with reg_tol > 0) band solver ------------
@@ -284,6 +314,8 @@ msdd_status msdd_band_factor(int batch, const int* n, int nmax, int bw, const do
  * right-hand sides at X + i * nmax * nrhs, row-major n[i] x nrhs, nrhs <= 32.
  * Uses a library-allocated staging buffer. */
 msdd_status msdd_band_solve(const msdd_band_batch* bb, int nrhs, double* X, void* stream);
+/* Free a batch from msdd_band_factor and its device factors (returned to the
+ * device cache).  NULL is ignored. */
 void msdd_band_destroy(msdd_band_batch* bb);
 
 /* Same solve as msdd_band_solve, for callers that must not allocate device
