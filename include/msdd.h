@@ -373,12 +373,20 @@ msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nrhs, double*
  * node counts of its Neumann box (nx, ny, 1) and the row offset of the box
  * in warm_start layouts (as int, rows < 2^31).  count receives the number. */
 msdd_status msdd_fine_layout(const msdd_mesh* mesh, const msdd_decomp* decomp, int* out, int cap, int* count);
-/* Network inputs of all fine subdomains: X (count x MSDD_NN_IN floats). */
+/* Network inputs of all fine subdomains of (mesh, decomp): X (device,
+ * count x MSDD_NN_IN floats, count = the fine subdomains in the order of
+ * msdd_fine_layout), read from coeff's element values.
+ * MSDD_ERR_UNSUPPORTED unless mesh->dim == 2 and coeff->kind == 0;
+ * MSDD_ERR_INVALID_ARG for NULL or invalid arguments. */
 msdd_status msdd_nn_patches(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp, float* X,
                             void* stream);
-/* Bytes of caller-owned device workspace for a batch of `batch` samples. */
+/* Bytes of caller-owned device workspace that msdd_nn_forward and
+ * msdd_nn_loss_grad need for a batch of `batch` samples (0 for batch < 1). */
 size_t msdd_nn_workspace_bytes(int batch);
-/* out (batch x MSDD_NN_OUT floats) = network(params, X). */
+/* out = network(params, X): X batch x MSDD_NN_IN floats, out batch x
+ * MSDD_NN_OUT floats, params MSDD_NN_NPARAM floats, work
+ * msdd_nn_workspace_bytes(batch) bytes.  MSDD_ERR_INVALID_ARG for NULL
+ * pointers or batch < 1. */
 msdd_status msdd_nn_forward(const float* params, int batch, const float* X, float* out, void* work, void* stream);
 /* Batch loss (one double) and its gradient with respect to params (grad,
  * MSDD_NN_NPARAM floats).  T: batch x MSDD_NN_NVEC x GRID^2 floats, unit
