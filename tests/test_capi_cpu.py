@@ -100,3 +100,60 @@ def test_no_source_mentions_oracle_in_library():
     for f in os.listdir(csrc):
         txt = open(os.path.join(csrc, f)).read().lower()
         assert "oracle" not in txt, f
+
+
+def _setup_args(msdd):
+    mesh = msdd.make_mesh((16, 16), 0b1)
+    coeff = msdd.Coeff()
+    coeff.kind = 0
+    coeff.data = ctypes.c_void_p(0x1000)     # never dereferenced: every case fails validation first
+    dec = msdd.Decomp()
+    for d, v in enumerate((4, 4, 1)):
+        dec.parts[d] = v
+        dec.group[d] = 2
+    dec.overlap, dec.levels = 1, 3
+    spec = msdd.Spectral()
+    spec.nev_max, spec.eta, spec.blf = 6, 0.3, 1
+    return mesh, coeff, dec, spec, msdd.default_options()
+
+
+SETUP_CASES = [
+    # (field, value, expected status, message fragment)
+    ("mesh.dim", 4, -1, b"invalid mesh"),
+    ("mesh.dirichlet_faces", 0, -1, b"invalid mesh"),
+    ("coeff.kind", 2, -1, b"invalid coefficient"),
+    ("dec.levels", 1, -1, b"levels must be"),
+    ("dec.levels", 4, -7, b"2 or 3 levels"),
+    ("dec.overlap", 0, -1, b"overlap"),
+    ("dec.parts", 17, -1, b"parts"),
+    ("dec.group", 0, -1, b"group"),
+    ("spec.nev_max", 25, -1, b"nev_max"),
+    ("spec.eta", 0.0, -1, b"eta"),
+    ("spec.blf", 4, -1, b"blf"),
+    ("opt.precision", 2, -1, b"precision"),
+    ("opt.block_p", 6, -1, b"block_p must exceed nev_max"),
+    ("opt.block_p", 33, -1, b"block_p out of range"),
+    ("opt.sigma", 0.0, -1, b"eigensolver options"),
+    ("opt.reg_tol", 1.0, -1, b"eigensolver options"),
+    ("opt.warm_cols", 0, -1, b"warm_cols"),
+]
+
+
+@pytest.mark.parametrize("field,value,status,msg", SETUP_CASES)
+def test_setup_rejects_invalid_arguments_before_device_work(lib, field, value, status, msg):
+    from paper_2106_06404_gb300 import msdd
+    mesh, coeff, dec, spec, opt = _setup_args(msdd)
+    obj, name = field.split(".")
+    target = {"mesh": mesh, "coeff": coeff, "dec": dec, "spec": spec, "opt": opt}[obj]
+    if name in ("parts", "group"):
+        getattr(target, name)[0] = value
+    else:
+        setattr(target, name, value)
+    if field == "opt.warm_cols":
+        opt.warm_start = ctypes.c_void_p(0x2000)
+    h = ctypes.c_void_p(0x1234)
+    st = lib.msdd_setup(ctypes.byref(mesh), ctypes.byref(coeff), ctypes.byref(dec), ctypes.byref(spec),
+                        ctypes.byref(opt), ctypes.byref(h))
+    assert st == status, (field, st, lib.msdd_last_error())
+    assert msg in lib.msdd_last_error()
+    assert not h.value                                    # *out cleared on failure
