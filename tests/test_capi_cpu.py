@@ -10,6 +10,7 @@ import re
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -157,3 +158,31 @@ def test_setup_rejects_invalid_arguments_before_device_work(lib, field, value, s
     assert st == status, (field, st, lib.msdd_last_error())
     assert msg in lib.msdd_last_error()
     assert not h.value                                    # *out cleared on failure
+
+
+@pytest.mark.parametrize("n,parts,overlap,faces", [
+    ((16, 16), (4, 4), 1, 0b1),
+    ((52, 44), (6, 5), 2, 0b1),
+    ((37, 23), (5, 3), 3, 0b0101),          # Dirichlet on x = 0 and y = 0
+    ((20, 9), (3, 2), 2, 0b1010),           # Dirichlet on x = 1 and y = 1
+    ((12, 10, 8), (3, 2, 2), 1, 0b1),
+    ((11, 9, 7), (2, 3, 2), 2, 0b100001),   # Dirichlet on x = 0 and z = 1
+])
+def test_fine_boxes_match_oracle_decomposition(lib, n, parts, overlap, faces):
+    """The library's fine box partition with overlap (the same host code the
+    set-up uses) gives each subdomain the Neumann box of the oracle's
+    decomposition (Section 2.2 box partition, first N mod P blocks one element
+    larger), in the same order, with row offsets the running sums."""
+    from oracle import fem
+    from oracle.decomposition import Decomposition
+    from paper_2106_06404_gb300 import msdd
+    lay = msdd.fine_layout(n, parts, overlap, faces)
+    mesh = fem.Mesh(n, faces)
+    dec = Decomposition(mesh, parts, overlap, 2, (1,) * len(n))
+    assert lay.shape == (len(dec.fine), 4)
+    off = 0
+    for i, s in enumerate(dec.fine):
+        want = [hi - lo + 1 for lo, hi in s.neumann_box] + [1] * (3 - len(n))
+        assert list(lay[i, :3]) == want, (i, list(lay[i]), want)
+        assert lay[i, 3] == off
+        off += int(np.prod(want))
