@@ -151,6 +151,26 @@ def composite128(seed=0):
                     seed=seed, kind="composite")
 
 
+def batch256(seed=0, count=256):
+    """Batch of independent 2D problems of uneven size: per problem, from one
+    PCG64(seed) stream in this order, the side N ~ U{128..384} elements, the
+    subdomains per axis P ~ U{4..12}, the contrast 10^U[4, 6] and the field
+    seed.  Coefficient: exp(GRF) (correlation length 0.05, variance 2) times
+    the contrast on N // 16 one-element channels, no inclusions.  Two levels,
+    overlap 2, nev <= 8, eta = 0.3, Dirichlet on x = 0."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = int(rng.integers(128, 385))
+        P = int(rng.integers(4, 13))
+        contrast = float(10.0 ** rng.uniform(4.0, 6.0))
+        fseed = int(rng.integers(0, 2**31 - 1))
+        out.append(Workload("batch2d_%03d_%dx%d_%dx%d" % (i, N, N, P, P), (N, N), (P, P), 2, 2, (1, 1), 8, 0.3,
+                            seed=fseed, kind="grf", contrast=contrast,
+                            extra={"n_channels": N // 16, "channel_width": 1, "n_inclusions": 0}))
+    return out
+
+
 def mlp_init(seed, shapes):
     """Seeded He-normal weights (std sqrt(2 / fan_in) for 2-D shapes (fan_out, fan_in)),
     zero biases (1-D shapes), concatenated row-major as float32."""
