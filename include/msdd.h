@@ -344,7 +344,7 @@ msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nrhs, double*
  * Not part of the paper's method (its eigensolver starts without a learned
  * guess): a small network maps a fine subdomain's coefficient patch to start
  * vectors for the subspace iteration of Eq. theGEVP; the Rayleigh-Ritz step
- * and the residual test stay the judge, so a poor prediction costs
+ * and the residual test still decide convergence, so a poor prediction costs
  * iterations, never accuracy.  2D scalar coefficients only.
  *
  * Network: input = log10 kappa of the subdomain's element box area-averaged
