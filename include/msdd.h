@@ -20,6 +20,10 @@
  *   - Nothing throws across the ABI.  Every entry point returns an msdd_status;
  *     on failure msdd_last_error() returns a message for the calling thread and
  *     outputs are left unspecified unless stated otherwise.
+ *   - Every wait of a kernel on its own asynchronous copies is bounded: when the
+ *     bound runs out the kernel records it and returns early, and the call that
+ *     launched it returns MSDD_ERR_TIMEOUT with invalid outputs; the CUDA
+ *     context stays usable.
  *   - Unknowns are the mesh nodes not on a Dirichlet face, numbered
  *     lexicographically (x fastest) within the box of such nodes.  Element
  *     (ex, ey, ez) has index ex + nx * (ey + ny * ez).
@@ -43,7 +47,9 @@ typedef enum msdd_status {
     MSDD_ERR_EIG_NO_CONVERGENCE = -4, /* subspace iteration reached eig_maxit (set-up kept)   */
     MSDD_ERR_OOM = -5,                /* device allocation failed                            */
     MSDD_ERR_CUDA = -6,               /* any other CUDA runtime error                        */
-    MSDD_ERR_UNSUPPORTED = -7         /* valid request outside what this build implements    */
+    MSDD_ERR_UNSUPPORTED = -7,        /* valid request outside what this build implements    */
+    MSDD_ERR_TIMEOUT = -8             /* a bounded wait inside a kernel ran out: the kernel
+                                         stopped early and its results are not valid        */
 } msdd_status;
 
 /* Structured Q1 mesh of n[0] x n[1] (x n[2]) equal elements on the unit box.

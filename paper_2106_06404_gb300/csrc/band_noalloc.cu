@@ -87,6 +87,8 @@ extern "C" msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nr
         MSDD_LAUNCH_CHECK();
         MSDD_CUDA(cudaStreamSynchronize(st));
         msdd::tile_check_waits();
+    } catch (const msdd::WaitTimeout& ex) {
+        return noalloc_fail(MSDD_ERR_TIMEOUT, ex.what());
     } catch (const std::exception& ex) {
         return noalloc_fail(MSDD_ERR_CUDA, ex.what());
     }

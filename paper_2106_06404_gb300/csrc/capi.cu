@@ -39,6 +39,8 @@ msdd_status guarded_call(F&& f) {
         std::string m = e.what();
         if (m.find("out of memory") != std::string::npos) return fail(MSDD_ERR_OOM, m);
         return fail(MSDD_ERR_CUDA, m);
+    } catch (const msdd::WaitTimeout& e) {
+        return fail(MSDD_ERR_TIMEOUT, e.what());
     } catch (const std::bad_alloc&) {
         return fail(MSDD_ERR_OOM, "host allocation failed");
     } catch (const std::exception& e) {

@@ -25,6 +25,11 @@ struct CudaError : std::runtime_error {
     explicit CudaError(const std::string& s) : std::runtime_error(s) {}
 };
 
+// A kernel's bounded wait ran out (it recorded the event and returned early).
+struct WaitTimeout : std::runtime_error {
+    explicit WaitTimeout(const std::string& s) : std::runtime_error(s) {}
+};
+
 #define MSDD_CUDA(call)                                                                  \
     do {                                                                                 \
         cudaError_t err__ = (call);                                                      \

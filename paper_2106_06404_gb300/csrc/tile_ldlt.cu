@@ -1518,7 +1518,7 @@ void tile_check_waits() {
     if (n) {
         const int zero = 0;
         MSDD_CUDA(cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(int)));
-        throw std::runtime_error("a band solve gave up waiting for its tile copies (" + std::to_string(n) + " CTAs)");
+        throw WaitTimeout("a band solve gave up waiting for its tile copies (" + std::to_string(n) + " CTAs)");
     }
 }
 

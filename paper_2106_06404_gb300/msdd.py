@@ -16,6 +16,7 @@ MSDD_OK = 0
 STATUS_NAMES = {
     0: "MSDD_OK", -1: "MSDD_ERR_INVALID_ARG", -2: "MSDD_ERR_NOT_SPD", -3: "MSDD_ERR_NO_CONVERGENCE",
     -4: "MSDD_ERR_EIG_NO_CONVERGENCE", -5: "MSDD_ERR_OOM", -6: "MSDD_ERR_CUDA", -7: "MSDD_ERR_UNSUPPORTED",
+    -8: "MSDD_ERR_TIMEOUT",
 }
 MAX_LEVELS = 8
 
