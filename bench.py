@@ -184,7 +184,8 @@ def cpu_baseline_obj(res, wname):
         "sample": ("%s: oracle fine-level local set-up of %d of %d subdomains (Neumann/Dirichlet assembly, "
                    "partition of unity, dense Cholesky of A_i and Abar_i+B_i, spectral transform) + global "
                    "assembly, %.1f s measured, extrapolated to all subdomains on %d cores; excludes the "
-                   "oracle's Jacobi eigen-iteration (~5 min per subdomain per core), coarse levels and PCG, so "
+                   "oracle's Jacobi eigen-iteration (~5 min per 1369-node subdomain of the 512^2 workload per "
+                   "core), coarse levels and PCG, so "
                    "the oracle's full step is much slower than this value")
                   % (wname, res["subdomains"], res["total_subdomains"], res["sample_s"], res["cores"]),
     }
