@@ -375,6 +375,28 @@ msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nrhs, double*
 #define MSDD_NN_NPARAM (MSDD_NN_HIDDEN * MSDD_NN_IN + MSDD_NN_HIDDEN + MSDD_NN_HIDDEN * MSDD_NN_HIDDEN + \
                         MSDD_NN_HIDDEN + MSDD_NN_OUT * MSDD_NN_HIDDEN + MSDD_NN_OUT)
 
+/* ---- batches of independent problems --------------------------------------
+ * Work items of a batch of problems for one persistent launch: every fine
+ * subdomain of every problem, ordered by decreasing cost c = n (b + 1) of its
+ * Neumann-box band (n nodes, lexicographic half-bandwidth b; the band
+ * factorisation and each band solve of the subspace iteration scale with
+ * it), ties in problem then subdomain order.  Section 5 (strong scaling in
+ * 3D, the T_i,min / T_i,max columns) reports a wide spread of per-subdomain
+ * eigensolve times and suggests more subdomains than processors to average
+ * them; a work queue handing out the largest items first does that.
+ * meshes, decomps: host arrays of nprob entries (as for msdd_setup).
+ * items (2 ints per item: problem, subdomain) and cost (1 double per item):
+ * host buffers of cap items, each may be NULL; *count = number of items.
+ * *makespan = the largest worker load when nworkers workers take the items
+ * in this order, each item going to the least loaded worker (lowest index
+ * among equals), which is the order an atomic work counter hands them out;
+ * *lower_bound = max(total cost / nworkers, largest cost).  Host only, no
+ * device work.  MSDD_ERR_INVALID_ARG for invalid arguments or cap < count
+ * (when a buffer is given). */
+msdd_status msdd_batch_plan(int nprob, const msdd_mesh* meshes, const msdd_decomp* decomps, int nworkers,
+                            int* items, double* cost, long long cap, long long* count, double* makespan,
+                            double* lower_bound);
+
 /* Number of fine subdomains and, per subdomain (host, 4 * count ints), the
  * node counts of its Neumann box (nx, ny, 1) and the row offset of the box
  * in warm_start layouts (as int, rows < 2^31).  count receives the number. */

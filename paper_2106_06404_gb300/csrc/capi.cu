@@ -1,4 +1,6 @@
 // C ABI of the msdd library (declarations and contracts in include/msdd.h).
+#include <algorithm>
+#include <queue>
 #include <cstring>
 #include <new>
 #include <string>
@@ -432,6 +434,68 @@ void msdd_band_destroy(msdd_band_batch* bb) {
 }
 
 // ---- learned warm start
+msdd_status msdd_batch_plan(int nprob, const msdd_mesh* meshes, const msdd_decomp* decomps, int nworkers,
+                            int* items, double* cost, long long cap, long long* count, double* makespan,
+                            double* lower_bound) {
+    return guarded_call([&]() -> msdd_status {
+        if (nprob < 1 || !meshes || !decomps || nworkers < 1)
+            return fail(MSDD_ERR_INVALID_ARG, "nprob >= 1, meshes, decomps and nworkers >= 1 are required");
+        struct Item {
+            double c;
+            int p, s;
+        };
+        std::vector<Item> all;
+        for (int p = 0; p < nprob; ++p) {
+            if (!mesh_ok(&meshes[p]) || !decomp_parts_ok(&meshes[p], &decomps[p]))
+                return fail(MSDD_ERR_INVALID_ARG, "invalid mesh or decomposition of problem " + std::to_string(p));
+            msdd_coeff none{0, nullptr};
+            const msdd::Geom g = msdd::make_geom(meshes[p], none);
+            const std::vector<msdd::ProbBox> boxes = msdd::make_fine_boxes(g, decomps[p]);
+            for (int i = 0; i < (int)boxes.size(); ++i) {
+                long long w[3] = {1, 1, 1}, n = 1;
+                for (int d = 0; d < meshes[p].dim; ++d) {
+                    w[d] = boxes[i].nhi[d] - boxes[i].nlo[d] + 1;
+                    n *= w[d];
+                }
+                // lexicographic half-bandwidth of the Q1 stencil on the Neumann box
+                const long long b = meshes[p].dim == 3 ? w[0] * w[1] + w[0] + 1 : w[0] + 1;
+                all.push_back({(double)n * (double)(b + 1), p, i});
+            }
+        }
+        std::stable_sort(all.begin(), all.end(), [](const Item& a, const Item& b) { return a.c > b.c; });
+        if (count) *count = (long long)all.size();
+        // greedy list scheduling in this order: each item to the least loaded
+        // worker (lowest index among equals)
+        std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
+                            std::greater<std::pair<double, int>>>
+            heap;
+        for (int w = 0; w < nworkers; ++w) heap.push({0.0, w});
+        double total = 0.0, cmax = 0.0, mk = 0.0;
+        for (const Item& it : all) {
+            std::pair<double, int> t = heap.top();
+            heap.pop();
+            t.first += it.c;
+            mk = std::max(mk, t.first);
+            heap.push(t);
+            total += it.c;
+            cmax = std::max(cmax, it.c);
+        }
+        if (makespan) *makespan = mk;
+        if (lower_bound) *lower_bound = std::max(total / nworkers, cmax);
+        if (items || cost) {
+            if (cap < (long long)all.size()) return fail(MSDD_ERR_INVALID_ARG, "buffers smaller than the item count");
+            for (size_t k = 0; k < all.size(); ++k) {
+                if (items) {
+                    items[2 * k] = all[k].p;
+                    items[2 * k + 1] = all[k].s;
+                }
+                if (cost) cost[k] = all[k].c;
+            }
+        }
+        return MSDD_OK;
+    });
+}
+
 msdd_status msdd_fine_layout(const msdd_mesh* mesh, const msdd_decomp* decomp, int* out, int cap, int* count) {
     return guarded([&]() -> msdd_status {
         if (!mesh_ok(mesh) || !decomp_parts_ok(mesh, decomp)) return fail(MSDD_ERR_INVALID_ARG, "invalid mesh or decomposition");

@@ -77,7 +77,7 @@ EXPORTED = [
     "msdd_band_factor", "msdd_band_solve", "msdd_band_destroy", "msdd_band_solve_noalloc", "msdd_kernel_launches",
     "msdd_fine_layout", "msdd_nn_patches", "msdd_nn_workspace_bytes", "msdd_nn_forward", "msdd_nn_loss_grad",
     "msdd_nn_adam", "msdd_nn_start_vectors", "msdd_nn_targets", "msdd_release_cache", "msdd_cached_bytes",
-    "msdd_apply_hybrid_preconditioner", "msdd_solve_gmres",
+    "msdd_apply_hybrid_preconditioner", "msdd_solve_gmres", "msdd_batch_plan",
 ]
 
 # learned warm start (include/msdd.h, MSDD_NN_*)
@@ -128,6 +128,8 @@ def load(path=LIB_PATH):
     lib.msdd_cached_bytes.argtypes = []
     lib.msdd_cached_bytes.restype = ctypes.c_longlong
     lib.msdd_fine_layout.argtypes = [P(Mesh), P(Decomp), ip, ctypes.c_int, ip]
+    lib.msdd_batch_plan.argtypes = [ctypes.c_int, P(Mesh), P(Decomp), ctypes.c_int, ip, dp, ctypes.c_longlong,
+                                    P(ctypes.c_longlong), dp, dp]
     lib.msdd_nn_patches.argtypes = [P(Mesh), P(Coeff), P(Decomp), vp, vp]
     lib.msdd_nn_workspace_bytes.argtypes = [ctypes.c_int]
     lib.msdd_nn_workspace_bytes.restype = ctypes.c_size_t
@@ -417,6 +419,27 @@ def _decomp(parts, overlap):
     d.overlap = int(overlap)
     d.levels = 2
     return d
+
+
+def batch_plan(problems, nworkers):
+    """msdd_batch_plan for a list of (n, parts, overlap, dirichlet_faces):
+    returns (items (K, 2) int32 of (problem, subdomain) in queue order,
+    costs (K,), makespan, lower_bound)."""
+    lib = load()
+    k = len(problems)
+    meshes, decs = (Mesh * k)(), (Decomp * k)()
+    for i, (n, parts, overlap, faces) in enumerate(problems):
+        meshes[i] = make_mesh(n, faces)
+        decs[i] = _decomp(parts, overlap)
+    cnt = ctypes.c_longlong()
+    _check(lib.msdd_batch_plan(k, meshes, decs, int(nworkers), None, None, 0, ctypes.byref(cnt), None, None))
+    items = np.zeros(2 * cnt.value, dtype=np.int32)
+    cost = np.zeros(cnt.value, dtype=np.float64)
+    mk, lb = ctypes.c_double(), ctypes.c_double()
+    _check(lib.msdd_batch_plan(k, meshes, decs, int(nworkers), items.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               cost.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt.value, ctypes.byref(cnt),
+                               ctypes.byref(mk), ctypes.byref(lb)))
+    return items.reshape(-1, 2), cost, mk.value, lb.value
 
 
 def fine_layout(n, parts, overlap, dirichlet_faces=0b1):
