@@ -1,9 +1,11 @@
 // C ABI of the msdd library (declarations and contracts in include/msdd.h).
 #include <algorithm>
+#include <functional>
 #include <queue>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "capi_types.cuh"
 #include "warmstart.cuh"
