@@ -186,3 +186,12 @@ def test_fine_boxes_match_oracle_decomposition(lib, n, parts, overlap, faces):
         assert list(lay[i, :3]) == want, (i, list(lay[i]), want)
         assert lay[i, 3] == off
         off += int(np.prod(want))
+
+
+def test_status_names_match_header_enum():
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef enum msdd_status \{(.*?)\} msdd_status;", txt, flags=re.S).group(1)
+    enum = {int(v): k for k, v in re.findall(r"(MSDD_[A-Z_]+)\s*=\s*(-?\d+)", body)}
+    from paper_2106_06404_gb300 import msdd
+    assert enum == msdd.STATUS_NAMES
+    assert enum[-8] == "MSDD_ERR_TIMEOUT"
