@@ -148,3 +148,15 @@ def test_coarsest_residual_from_level_one():
     plain = P0.T @ (r - A @ (z + P1 @ z1))
     nested = Z1.T @ (P1.T @ (r - A @ z) - A1 @ z1)
     assert np.linalg.norm(plain - nested) <= 1e-9 * np.linalg.norm(plain)
+
+
+def test_zero_right_hand_side():
+    """b = 0: both solvers return x = 0 after no iteration (x0 = 0 is exact)."""
+    mesh = fem.Mesh((8, 8), 0b1)
+    H = method.Hierarchy(mesh, si.channels_2d(8, 2, 1e3, seed=0), (2, 2), 1, 2, (1, 1), 3, 0.3)
+    b = np.zeros(H.n)
+    x, it, *_ = method.pcg(H.A, b, H.apply_preconditioner)
+    assert it == 0 and not np.any(x)
+    for flexible in (False, True):
+        x, it, _ = method.gmres(H.A, b, H.apply_hybrid, flexible=flexible)
+        assert it == 0 and not np.any(x)
