@@ -329,21 +329,26 @@ void msdd_band_destroy(msdd_band_batch* bb);
  * all device memory through its own pool, or a tight loop where a cudaMalloc
  * or cudaFree would synchronise the device and stall other streams.
  * The paper has no counterpart; this is an interface convenience.
- *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- *    The staging buffer is a file-scope device array of 2^21 doubles
- *    (16 MiB) that every GPU which loads the library holds until exit.
+ *  - Allocates nothing itself: no cudaMalloc, cudaFree or allocating library
+ *    call.  The staging buffer is a file-scope device array of 2^21 doubles
+ *    (16 MiB) that each GPU keeps until the process exits once the array has
+ *    been loaded there.
+ *  - First call on a device: it looks up the array's device address with that
+ *    device current (cudaGetSymbolAddress).  With CUDA's lazy module loading
+ *    (the default) that lookup is also when the driver loads the array and
+ *    commits its 16 MiB on the device, so make the first call before applying
+ *    a memory budget and before any stream capture on that device; if the
+ *    driver cannot commit the array the call returns MSDD_ERR_OOM.
  *  - Limit: the batch's padded rows (32 * ceil(n[i] / 32) summed over i)
  *    times nrhs must not exceed 2^21; otherwise MSDD_ERR_INVALID_ARG and
  *    X is untouched (use msdd_band_solve).
- *  - The first call on a device looks up the array's device address for that
- *    device (cudaGetSymbolAddress, with that device current); make that first
- *    call before any stream capture on it.
  *  - All calls share the one array and it keeps the last call's contents
  *    (padding rows are rewritten with zeros by every call).  Calls that
  *    overlap on the GPU, e.g. from several threads or streams at once, race
  *    on it and must be serialised by the caller.
- * Arguments and layout of X are those of msdd_band_solve; returns after the
- * work on `stream` has completed. */
+ *  - Status codes and msdd_last_error follow the rules of msdd_band_solve.
+ * Arguments and layout of X are those of msdd_band_solve; the call
+ * synchronises `stream` before it returns. */
 msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nrhs, double* X, void* stream);
 
 /* ---- learned warm start of the fine subspace iteration ----------------------

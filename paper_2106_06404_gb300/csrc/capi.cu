@@ -52,6 +52,14 @@ msdd_status guarded_call(F&& f) {
     }
 }
 
+}  // namespace
+
+msdd_status msdd::classified_call(msdd_status (*f)(void*), void* ctx) {
+    return guarded_call([&]() -> msdd_status { return f(ctx); });
+}
+
+namespace {
+
 // every entry point: blocks released during the call become reusable
 // (device synchronised once, only if the call released any)
 template <class F>

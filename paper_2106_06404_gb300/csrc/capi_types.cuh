@@ -20,4 +20,9 @@ struct msdd_band_batch {
 namespace msdd {
 // Record the message returned by msdd_last_error() on this thread; returns s.
 msdd_status set_last_error(msdd_status s, const std::string& msg);
+// Clear the message, run f and map what it throws to a status with the same
+// rules as every other entry point (out of memory -> MSDD_ERR_OOM, a bounded
+// wait that gave up -> MSDD_ERR_TIMEOUT, MsddError -> its own status, any
+// other failure -> MSDD_ERR_CUDA).  Allocates nothing itself.
+msdd_status classified_call(msdd_status (*f)(void*), void* ctx);
 }  // namespace msdd
