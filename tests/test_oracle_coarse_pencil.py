@@ -1,0 +1,194 @@
+"""Pins of the oracle's coarse-level generating-system GEVP (Section 4.2).
+
+On a level l < L the Neumann space of subdomain (l, i) is spanned by the
+own children's coarse basis functions phi_{l+1,j,k} (j in J_{l,i}) and the
+restrictions to Omega_{l,i} of the neighbouring children's ones (j in
+Jbar_{l,i} minus J_{l,i}, Jbar the children whose element sets meet
+T_{h,l,i}).  The oracle forms Abar_{l,i} = G^T Abar_{T_{h,l,i}} G from a
+global Neumann matrix and sparse column products.  These tests rebuild the
+same pencil by an independent route and check what Section 3.3 fixes:
+
+  * the neighbour set, found by brute force over element sets;
+  * Abar_{l,i} assembled element by element over T_{h,l,i}, each
+    neighbour function explicitly restricted (zeroed outside the closure of
+    Omega_{l,i}) and each own function taken whole;
+  * B_{l,i} = X Abar_{l,i} X with X the own-generator mask;
+  * the own-own block of Abar_{l,i} equals the coarse Dirichlet matrix
+    A_{l,i} (own functions vanish outside Omega_{l,i}), which the oracle
+    takes from the Galerkin matrix instead;
+  * the spectrum structure of the pencil with ker A cap ker B != {0}: on
+    the complement of the common kernel, #finite eigenvalues = rank B and
+    #(lambda = 0) = rank(A + B) - rank A (the non-defectiveness lemma and
+    the spectrum display after it, with ranks from numpy's SVD);
+  * brute force: scipy's LAPACK symmetric-definite solver on the
+    rank-reduced, spectrally transformed pencil;
+  * the projection stability estimates (Lemma gevp_properties) for the
+    oracle's eigenvectors on random vectors.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import synthetic_inputs as si
+from oracle import fem, method
+
+
+@pytest.fixture(scope="module")
+def three_level():
+    mesh = fem.Mesh((16, 16), 0b1)
+    kap = si.channels_2d(16, 3, 1e4, seed=1)
+    H = method.Hierarchy(mesh, kap, (4, 4), 1, 3, (2, 2), 6, 0.3, keep_local=True)
+    return mesh, kap, H
+
+
+@pytest.fixture(scope="module")
+def ragged_three_level():
+    # 2 x 2 middle subdomains with 3 and 2 children along x (uneven groups)
+    mesh = fem.Mesh((20, 18), 0b1)
+    kap = si.channels_2d(20, 3, 1e5, seed=4)[: 20 * 18]
+    H = method.Hierarchy(mesh, kap, (5, 4), 2, 3, (2, 2), 5, 0.3, keep_local=True)
+    return mesh, kap, H
+
+
+def _node_functions(mesh, H, l):
+    """Level-(l+1) coarse basis functions phi_{l+1,j,k} as nodal arrays over all
+    mesh nodes (zero on Dirichlet nodes), one list per child j."""
+    P = H.levels[l + 1].P_coarse.toarray()       # unknown coordinates
+    n2u = H.n2u
+    out = []
+    for a, b in H.levels[l + 1].col_range:
+        cols = []
+        for c in range(a, b):
+            v = np.zeros(mesh.num_nodes)
+            on = n2u >= 0
+            v[on] = P[n2u[on], c]
+            cols.append(v)
+        out.append(cols)
+    return out
+
+
+def _child_masks(H, l):
+    return H.dec.element_mask[l + 1]
+
+
+def _independent_pencil(mesh, kap, H, l, i):
+    """(own children, neighbour children, Abar, B) of subdomain (l, i) from an
+    element loop over T_{h,l,i}."""
+    dec = H.dec
+    mask = dec.element_mask[l][i]
+    own = list(dec.members[l][i])
+    kids = _child_masks(H, l)
+    nbr = sorted(j for j in range(len(kids)) if j not in own and np.any(kids[j] & mask))
+    en = mesh.element_nodes()
+    # closure of Omega_{l,i}: nodes of its elements
+    closure = np.zeros(mesh.num_nodes, dtype=bool)
+    closure[np.unique(en[mask])] = True
+    phis = _node_functions(mesh, H, l)
+    gens = [phi for j in own for phi in phis[j]]
+    n_own = len(gens)
+    gens += [np.where(closure, phi, 0.0) for j in nbr for phi in phis[j]]
+    G = np.stack(gens, axis=1) if gens else np.zeros((mesh.num_nodes, 0))
+    Ke = fem.element_matrices(mesh, kap)
+    Abar = np.zeros((G.shape[1], G.shape[1]))
+    for e in np.nonzero(mask)[0]:
+        Ge = G[en[e]]                              # element nodal values of every generator
+        Abar += Ge.T @ Ke[e] @ Ge
+    x = np.zeros(G.shape[1])
+    x[:n_own] = 1.0
+    B = x[:, None] * Abar * x[None, :]
+    return own, nbr, Abar, B, n_own
+
+
+def _cases(H):
+    return range(H.dec.num_subdomains(1))
+
+
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level"])
+def test_generating_system_matches_element_assembly(fixture, request):
+    mesh, kap, H = request.getfixturevalue(fixture)
+    lev = H.levels[1]
+    for i in _cases(H):
+        own, nbr, Abar, B, n_own = _independent_pencil(mesh, kap, H, 1, i)
+        s = lev.subs[i]
+        assert list(s["own"]) == own
+        assert list(s["nbr"]) == nbr
+        scale = max(1.0, np.abs(Abar).max())
+        assert s["Abar"].shape == Abar.shape
+        assert np.abs(s["Abar"] - Abar).max() <= 1e-11 * scale, i
+        assert np.abs(s["B"] - B).max() <= 1e-11 * scale, i
+        # own functions vanish outside Omega_{l,i}: Neumann own block = Dirichlet matrix
+        assert np.abs(s["Ai"] - Abar[:n_own, :n_own]).max() <= 1e-10 * scale, i
+
+
+def _rank(M, rel=1e-9):
+    s = np.linalg.svd(M, compute_uv=False)
+    if s.size == 0 or s[0] == 0.0:
+        return 0, s
+    return int(np.sum(s > rel * s[0])), s
+
+
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level"])
+def test_coarse_spectrum_structure(fixture, request):
+    """Spectrum of the generating-system pencil on the complement of
+    ker A cap ker B: rank B finite eigenvalues, rank(A+B) - rank A zeros."""
+    mesh, kap, H = request.getfixturevalue(fixture)
+    checked_zero = False
+    for s in H.levels[1].subs:
+        A, B = s["Abar"], s["B"]
+        rAB, sAB = _rank(A + B)
+        rA, sA = _rank(A)
+        rB, sB = _rank(B)
+        # the ranks are numerically unambiguous on these cases
+        for r, sv in ((rAB, sAB), (rA, sA), (rB, sB)):
+            if r < len(sv):
+                assert sv[r] < 1e-11 * sv[0] and sv[r - 1] > 1e-7 * sv[0]
+        lam = s["lam"]
+        assert len(lam) == rB
+        zeros = int(np.sum(lam < 1e-8))
+        assert zeros == rAB - rA
+        checked_zero = checked_zero or zeros > 0
+        assert np.all(lam >= -1e-9)
+    assert checked_zero                           # some floating middle subdomain
+
+
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level"])
+def test_coarse_eigenvalues_brute_force(fixture, request):
+    mesh, kap, H = request.getfixturevalue(fixture)
+    for s in H.levels[1].subs:
+        A, B = s["Abar"], s["B"]
+        S = A + B
+        w, U = np.linalg.eigh(S)
+        U = U[:, w > 1e-9 * w.max()]
+        mu = sla.eigh(U.T @ B @ U, U.T @ S @ U, eigvals_only=True)
+        mu = np.sort(mu[mu > 1e-10])[::-1]
+        lam_ref = 1.0 / mu - 1.0
+        lam = s["lam"]
+        assert len(lam) == len(lam_ref)
+        k = min(len(lam), 12)
+        err = np.abs(lam[:k] - lam_ref[:k]) / np.maximum(np.abs(lam_ref[:k]), 1e-6)
+        assert err.max() < 1e-7, err
+
+
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level"])
+def test_coarse_projection_stability(fixture, request):
+    """|Pi_m v|_a <= |v|_a, |v - Pi_m v|_a <= |v|_a and, for m >= #zeros,
+    |v - Pi_m v|_b^2 <= |v - Pi_m v|_a^2 / lambda_{m+1} (Lemma gevp_properties)."""
+    mesh, kap, H = request.getfixturevalue(fixture)
+    rng = np.random.default_rng(0)
+    for s in H.levels[1].subs:
+        A, B = s["Abar"], s["B"]
+        # full eigenvector set of the finite part, b-orthonormal
+        lam, W = method.gevp(A, B, rank_reveal=True)
+        assert np.allclose(W.T @ B @ W, np.eye(len(lam)), atol=1e-7)
+        r = int(np.sum(lam < 1e-8))
+        an = lambda v: np.sqrt(max(v @ A @ v, 0.0))
+        bn2 = lambda v: max(v @ B @ v, 0.0)
+        for _ in range(5):
+            v = rng.standard_normal(A.shape[0])
+            for m in range(0, len(lam)):
+                Pv = W[:, :m] @ (W[:, :m].T @ (B @ v))
+                assert an(Pv) <= an(v) * (1 + 1e-8) + 1e-12
+                assert an(v - Pv) <= an(v) * (1 + 1e-8) + 1e-12
+                if m >= r and m < len(lam):
+                    d = v - Pv
+                    assert bn2(d) <= an(d) ** 2 / lam[m] * (1 + 1e-7) + 1e-12
