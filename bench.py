@@ -62,8 +62,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["grf512", "channels64"], default="grf512")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-subdomains", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the CPU oracle step (and the error summary against it)")
+    ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--forms", choices=["both", "chosen"], default="both",
                     help="chosen: time only the chosen form (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
@@ -118,61 +119,123 @@ def workload(name, seed):
     return si.grf512(seed=seed) if name == "grf512" else si.channels64(seed=seed)
 
 
-# ------------------------------------------------------------------ oracle sample
-def oracle_sample(wname, k, threads):
-    """Time the CPU oracle on a bounded sample of the workload.
+# ------------------------------------------------------------------ CPU oracle step
+def workload_config(w, unknowns, world):
+    """The config object of the JSON line (the same for both arms)."""
+    return {"workload": w.name, "n_elements": list(w.n), "unknowns": int(unknowns), "subdomains": list(w.parts),
+            "overlap": w.overlap, "levels": w.levels, "nev_max": w.nev_max, "eta": w.eta, "tol": TOL,
+            "form": "chosen (precision=1)", "l2": "flushed between steps (512 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
-    The sample is the fine-level local set-up of k subdomains of the workload
-    by the oracle as it stands (local Neumann assembly, partition of unity,
-    B = X Abar X, dense Cholesky of the Dirichlet matrix and of Abar + B, and
-    the spectral transformation C = L^{-1} B L^{-T}), i.e. everything of the
-    oracle's local set-up except the cyclic Jacobi iteration on C, which alone
-    takes ~5 min per 1369-node subdomain on one core.  Returns seconds for the
-    sample and the extrapolation to all fine subdomains on `threads` cores.
-    """
+
+def save_gpu_results(pkg, w, kappa, b):
+    """Selected Ritz values and counts of every fine and middle subdomain,
+    level dimensions, and the PCG solution of one chosen-form hierarchy
+    (bench defaults), written to a temporary .npz for the oracle leg."""
     import numpy as np
-    from concurrent.futures import ThreadPoolExecutor
-    from oracle import decomposition as dd
-    from oracle import fem, linalg
+    H = pkg.Hierarchy(w.n, kappa, w.parts, w.overlap, w.levels, w.group, w.nev_max, w.eta,
+                      dirichlet_faces=w.dirichlet_faces, precision=1)
+    x, it, _ = H.solve(b, tol=TOL)
+    st = H.stats()
+    out = {"level_dim": np.array(st["level_dim"]), "iterations": np.array(it), "x": x.cpu().numpy()}
+    L = w.levels - 1
+    for name, lev in (("fine", L), ("middle", 1)):
+        if name == "middle" and L < 2:
+            continue
+        P = st["subdomains"][lev]
+        lam = np.full((P, 32), np.nan)
+        ms = np.zeros(P, dtype=np.int64)
+        for i in range(P):
+            th, m = H.eigenvalues(lev, i)
+            lam[i, :len(th)] = th
+            ms[i] = m
+        out["%s_lam" % name], out["%s_m" % name] = lam, ms
+    H.close()
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, **out)
+    return path
+
+
+def oracle_step(wname, processes):
+    """One full step of the CPU oracle in method mode on the workload: set-up
+    (assembly, decomposition, band Cholesky factors and block subspace
+    iteration on every fine subdomain in `processes` spawned worker
+    processes, dense generating-system GEVPs on the middle level, Galerkin
+    and coarsest factors) and PCG with the additive preconditioner to
+    relative residual 1e-8.  Returns (seconds, result dict)."""
+    from oracle import fem, method, method_mode
     w = workload(wname, 0)
+    t0 = time.perf_counter()
     mesh = fem.Mesh(w.n, w.dirichlet_faces)
     kap = w.coefficient()
-    t0 = time.perf_counter()
-    dec = dd.Decomposition(mesh, w.parts, w.overlap, 2, w.group)
-    chis, _ = dec.partition_of_unity()
-    A = fem.assemble_system(mesh, kap)
-    n2u = mesh.node_to_unknown()
-    t_global = time.perf_counter() - t0
-    P = len(dec.fine)
-    idx = [int(v) for v in np.linspace(0, P - 1, k)]
-
-    def local(i):
-        s = dec.fine[i]
-        nn = s.neumann_nodes()
-        Ab = fem.assemble_neumann(mesh, kap, s.element_mask)[nn][:, nn].toarray()
-        B = chis[i][:, None] * Ab * chis[i][None, :]
-        du = n2u[s.dirichlet_nodes()]
-        linalg.cholesky(A[du][:, du].toarray())
-        L = linalg.cholesky(Ab + B)
-        T = linalg.forward(L, B)
-        linalg.forward(L, T.T)
-        return 0
-
+    H = method_mode.MethodModeHierarchy(mesh, kap, w.parts, w.overlap, w.levels, w.group, w.nev_max, w.eta,
+                                        processes=processes)
     t1 = time.perf_counter()
-    with ThreadPoolExecutor(threads) as ex:
-        list(ex.map(local, idx))
-    t_local = time.perf_counter() - t1
-    per_sub_core = t_local * min(threads, k) / k
-    full = t_global + per_sub_core * P / threads
-    return dict(sample_s=t_global + t_local, full_estimate_s=full, subdomains=k, total_subdomains=P,
-                cores=threads)
+    b = fem.load_vector(mesh)
+    x, it, *_ = method.pcg(H.A, b, H.apply_preconditioner, TOL)
+    t2 = time.perf_counter()
+    return t2 - t0, dict(H=H, x=x, b=b, iterations=it, setup_s=t1 - t0, pcg_s=t2 - t1)
 
 
-def _cpu_worker(q, wname, k, threads):
-    try:
-        q.put(oracle_sample(wname, k, threads))
-    except Exception as e:  # pragma: no cover - reported in the JSON line
-        q.put({"error": repr(e)})
+def error_vs_oracle(gpu, res, eta):
+    """Errors of the GPU's chosen form against the oracle's method-mode
+    results on the same workload: selected eigenvalues (relative, floor
+    1e-3 eta) and counts on the fine and middle levels, coarse dimensions,
+    CG iterations, and both solutions against a sparse direct solve."""
+    import numpy as np
+    import scipy.sparse.linalg as spla
+    H = res["H"]
+    out = {}
+    for name, lev in (("fine", H.L), ("middle", 1)):
+        if lev < 1 or lev > H.L or (name == "middle" and H.L < 2):
+            continue
+        subs = H.levels[lev].subs
+        g_l, g_m = gpu["%s_lam" % name], gpu["%s_m" % name]
+        worst, mism = 0.0, []
+        for i, s in enumerate(subs):
+            if int(g_m[i]) != s["m"]:
+                mism.append([i, int(g_m[i]), int(s["m"])])
+                continue
+            m = s["m"]
+            if m:
+                lam = np.asarray(s["lam"][:m])
+                e = np.abs(g_l[i][:m] - lam) / np.maximum(np.abs(lam), 1e-3 * eta)
+                worst = max(worst, float(e.max()))
+        out[name] = {"subdomains": len(subs), "max_rel_eig_err": worst, "count_mismatch": mism}
+    out["coarse_dims"] = {"gpu": [int(v) for v in gpu["level_dim"]],
+                          "oracle": [int(H.coarse_dims()[l]) for l in range(H.L)] + [int(H.n)]}
+    out["iterations"] = {"gpu": int(gpu["iterations"]), "oracle": int(res["iterations"])}
+    A = H.A.tocsc()
+    xd = spla.spsolve(A, res["b"])
+    an = lambda v: float(np.sqrt(max(v @ (A @ v), 0.0)))
+    for key, x in (("gpu", gpu["x"]), ("oracle", res["x"])):
+        out["solution_%s" % key] = {"rel_err_2": float(np.linalg.norm(x - xd) / np.linalg.norm(xd)),
+                                    "rel_err_A": an(x - xd) / an(xd)}
+    out["note"] = ("oracle = method mode (FP64 band Cholesky + block subspace iteration to eigen-residual 1e-8, "
+                   "exact dense GEVPs on the middle level); both CG runs stop at rel. residual 1e-8, so the "
+                   "solution errors are those of that stopping rule")
+    return out
+
+
+def oracle_leg(args):
+    """Run by bench.py itself in a fresh interpreter after the GPU work: one
+    timed oracle step on all host cores, and (given the GPU's results) the
+    error summary.  Prints one JSON object."""
+    import numpy as np
+    procs = os.cpu_count() or 1
+    secs, res = oracle_step(args.workload, procs)
+    out = {"seconds": secs, "setup_s": res["setup_s"], "pcg_s": res["pcg_s"], "iterations": res["iterations"],
+           "cores": procs}
+    if args.oracle_leg and os.path.exists(args.oracle_leg):
+        g = np.load(args.oracle_leg, allow_pickle=True)
+        gpu = {k: g[k] for k in g.files}
+        w = workload(args.workload, 0)
+        try:
+            out["error_vs_oracle"] = error_vs_oracle(gpu, res, w.eta)
+        except Exception as e:                                    # recorded in the JSON line
+            out["error_vs_oracle"] = {"error": repr(e)[:300]}
+    print(json.dumps(out), flush=True)
 
 
 def cpu_baseline_obj(res, wname):
@@ -180,15 +243,24 @@ def cpu_baseline_obj(res, wname):
         return {"value": None, "unit": "s", "cores": None, "kind": "oracle",
                 "sample": "failed: %s" % (res or {}).get("error", "not run")}
     return {
-        "value": round(res["full_estimate_s"], 3), "unit": "s", "cores": res["cores"], "kind": "oracle",
-        "sample": ("%s: oracle fine-level local set-up of %d of %d subdomains (Neumann/Dirichlet assembly, "
-                   "partition of unity, dense Cholesky of A_i and Abar_i+B_i, spectral transform) + global "
-                   "assembly, %.1f s measured, extrapolated to all subdomains on %d cores; excludes the "
-                   "oracle's Jacobi eigen-iteration (~5 min per 1369-node subdomain of the 512^2 workload per "
-                   "core), coarse levels and PCG, so "
-                   "the oracle's full step is much slower than this value")
-                  % (wname, res["subdomains"], res["total_subdomains"], res["sample_s"], res["cores"]),
+        "value": round(res["seconds"], 3), "unit": "s", "cores": res["cores"], "kind": "oracle",
+        "sample": ("%s: one full oracle step, method mode (the whole workload: set-up %.1f s, PCG %.1f s, "
+                   "%d iterations), run after the GPU timed region on all %d host cores (fine subdomains in "
+                   "worker processes)") % (wname, res["setup_s"], res["pcg_s"], res["iterations"], res["cores"]),
     }
+
+
+def run_oracle_leg(args, gpu_npz):
+    """Start the oracle leg as a fresh interpreter and parse its JSON line."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-leg", gpu_npz or "-", "--workload", args.workload]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=1800)
+        for line in reversed(r.stdout.strip().splitlines()):
+            if line.startswith("{"):
+                return json.loads(line)
+        return {"error": "no output (rc %d): %s" % (r.returncode, r.stderr[-300:])}
+    except Exception as e:
+        return {"error": repr(e)[:300]}
 
 
 # ------------------------------------------------------------------ clocks
@@ -243,15 +315,6 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args, rank, world, local_rank):
-    import multiprocessing as mp
-    cpu_q = cpu_p = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ctx = mp.get_context("spawn")            # before any CUDA call
-        cpu_q = ctx.Queue()
-        threads = max(1, min(os.cpu_count() or 1, args.cpu_subdomains))
-        cpu_p = ctx.Process(target=_cpu_worker, args=(cpu_q, args.workload, args.cpu_subdomains, threads))
-        cpu_p.start()
-
     import numpy as np
     import torch
     torch.cuda.set_device(local_rank)
@@ -348,6 +411,15 @@ def run_ours(args, rank, world, local_rank):
             except Exception as e:
                 solvers = {"error": repr(e)[:200]}
 
+        # the chosen form's results for the error summary against the CPU oracle
+        gpu_npz = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            try:
+                gpu_npz = save_gpu_results(pkg, w, kappa, b)
+            except Exception as e:
+                gpu_npz = None
+                print("gpu results not saved: %r" % (e,), file=sys.stderr)
+
     total = max_over_ranks(sum(t_chosen), dist, dev)
     if rank != 0:
         if dist is not None:
@@ -381,16 +453,17 @@ def run_ours(args, rank, world, local_rank):
                  "algorithmic_flops_per_launch": pf["flops"] / pf["launches"],
                  "arith_intensity_flop_per_byte": round(intensity, 3),
                  "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
-                 "traffic": None, "share_of_step": round(pf["ms"] / 1e3 / (total / args.steps) / args.steps, 4)})
+                 "traffic": None,
+                 # the family's time per timed step over the step's time
+                 "share_of_step": round((pf["ms"] / 1e3 / args.steps) / (total / args.steps), 4)})
     roof.update(measured_traffic(fam))
 
+    # the CPU oracle: one full step on all host cores, after all GPU work
     cpu = None
-    if cpu_p is not None:
-        try:
-            cpu = cpu_q.get(timeout=900)
-        except Exception as e:
-            cpu = {"error": repr(e)}
-        cpu_p.join(timeout=10)
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = run_oracle_leg(args, gpu_npz)
+        if gpu_npz:
+            os.unlink(gpu_npz)
 
     n = st_chosen["n"]
     e2e_val = statistics.mean(e2e_times) if e2e_times else None
@@ -407,10 +480,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f64 outer / f32 fine factors",
         "data": "synthetic (seeded GRF x channels/inclusions, contrast 1e6)",
-        "config": {"workload": w.name, "n_elements": list(w.n), "unknowns": n, "subdomains": list(w.parts),
-                   "overlap": w.overlap, "levels": w.levels, "nev_max": w.nev_max, "eta": w.eta, "tol": TOL,
-                   "form": "chosen (precision=1)", "l2": "flushed between steps (512 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(w, n, world),
         "iterations": it_chosen[-1],
         "step_seconds": [round(t, 6) for t in t_chosen],
         "setup_ms": round(st_chosen["setup_ms"], 3),
@@ -431,7 +501,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": round(e2e_val, 6) if e2e_val else None, "unit": "s",
                 "h2d_bytes_per_step": int(kap_np.nbytes + n * 8), "d2h_bytes_per_step": int(n * 8)},
         "gpu_launches": int(launches),
-        "cpu_baseline": cpu_baseline_obj(cpu, w.name) if cpu_p is not None else None,
+        "cpu_baseline": cpu_baseline_obj(cpu, w.name) if cpu is not None else None,
+        "error_vs_oracle": (cpu or {}).get("error_vs_oracle"),
         "solvers": solvers,
     }
     print(json.dumps(line), flush=True)
@@ -441,25 +512,32 @@ def run_ours(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
-    """The CPU oracle, as it stands, on a bounded sample per step (rank 0 only)."""
+    """The reference arm: the CPU oracle, as it stands (method mode), on the
+    same workload, config and metric; rank 0 only.  Each timed step is one
+    full oracle step (set-up + PCG) on all host cores; the warm-up steps run
+    the oracle on the small 64 x 64 channel workload."""
     if rank != 0:
         return
-    threads = max(1, min(os.cpu_count() or 1, args.cpu_subdomains))
+    procs = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_sample(args.workload, 1, 1)
-    vals, samples = [], []
+        oracle_step("channels64", procs)
+    vals, last = [], None
     for _ in range(args.steps):
-        r = oracle_sample(args.workload, args.cpu_subdomains, threads)
-        vals.append(r["full_estimate_s"])
-        samples.append(r)
+        secs, res = oracle_step(args.workload, procs)
+        vals.append(secs)
+        last = {"seconds": secs, "setup_s": res["setup_s"], "pcg_s": res["pcg_s"], "iterations": res["iterations"],
+                "cores": procs}
+        n = res["H"].n
     v = statistics.mean(vals)
     w = workload(args.workload, 0)
-    cb = cpu_baseline_obj(samples[-1], w.name)
+    cb = cpu_baseline_obj(last, w.name)
+    cb["sample"] = cb["sample"].replace("run after the GPU timed region on", "on")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * v, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_elements": list(w.n), "subdomains": list(w.parts), "levels": w.levels},
+        "config": workload_config(w, n, world),
+        "step_seconds": [round(t, 3) for t in vals],
         "cpu_baseline": dict(cb, value=round(v, 3)),
         "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -471,7 +549,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.oracle_leg is not None:
+        oracle_leg(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)

@@ -9,10 +9,12 @@
  *   - forward / backward substitution with several right-hand sides,
  *   - the cyclic Jacobi eigenvalue algorithm for a dense symmetric matrix
  *     (used to compute every eigenpair of the local generalized eigenproblems,
- *     Eq. (theGEVP) and Section 3.3, through a spectral transformation).
+ *     Eq. (theGEVP) and Section 3.3, through a spectral transformation),
+ *   - for the oracle's method mode: band Cholesky, band solves and the band
+ *     LDL^T inertia count (storage described above those routines).
  *
- * All matrices are row-major, n x n, double precision.  Nothing is blocked,
- * fused or reordered: each routine is the textbook definition.
+ * Dense matrices are row-major, n x n, double precision.  Nothing is
+ * blocked, fused or reordered: each routine is the textbook definition.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -156,6 +158,90 @@ int orc_ldlt_negative_count(int n, const double *A)
             double lik = W[(size_t)i * n + k] / d;
             if (lik == 0.0) continue;
             for (int j = k + 1; j <= i; ++j) W[(size_t)i * n + j] -= lik * W[(size_t)j * n + k];
+        }
+    }
+    free(W);
+    return neg;
+}
+
+/*
+ * Band matrices (method mode of the oracle): a symmetric matrix of order n
+ * and half-bandwidth b is held by its lower band, row-major by rows, entry
+ * (i, j), i - b <= j <= i, at AB[i * (b + 1) + (j - i + b)] (the diagonal in
+ * the last column of each row; entries with j < 0 are unused).
+ */
+
+/* In place A = L L^T on the lower band (the textbook column algorithm
+ * restricted to the band).  Returns 0 on success, k+1 if pivot k is not
+ * positive. */
+int orc_band_cholesky(int n, int b, double *AB)
+{
+    const int w = b + 1;
+    for (int j = 0; j < n; ++j) {
+        const int k0 = j - b > 0 ? j - b : 0;
+        double d = AB[(size_t)j * w + b];
+        for (int k = k0; k < j; ++k) {
+            const double ljk = AB[(size_t)j * w + (k - j + b)];
+            d -= ljk * ljk;
+        }
+        if (!(d > 0.0)) return j + 1;
+        const double ljj = sqrt(d);
+        AB[(size_t)j * w + b] = ljj;
+        const int iend = j + b < n - 1 ? j + b : n - 1;
+        for (int i = j + 1; i <= iend; ++i) {
+            const int ki = i - b > 0 ? i - b : 0;
+            double s = AB[(size_t)i * w + (j - i + b)];
+            for (int k = ki; k < j; ++k)
+                s -= AB[(size_t)i * w + (k - i + b)] * AB[(size_t)j * w + (k - j + b)];
+            AB[(size_t)i * w + (j - i + b)] = s / ljj;
+        }
+    }
+    return 0;
+}
+
+/* Solve L L^T X = B in place with the band factor from orc_band_cholesky
+ * (B is n x nrhs, row-major): forward then backward substitution. */
+void orc_band_solve(int n, int b, const double *LB, int nrhs, double *X)
+{
+    const int w = b + 1;
+    for (int i = 0; i < n; ++i) {
+        const int k0 = i - b > 0 ? i - b : 0;
+        for (int c = 0; c < nrhs; ++c) {
+            double s = X[(size_t)i * nrhs + c];
+            for (int k = k0; k < i; ++k) s -= LB[(size_t)i * w + (k - i + b)] * X[(size_t)k * nrhs + c];
+            X[(size_t)i * nrhs + c] = s / LB[(size_t)i * w + b];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        const int kend = i + b < n - 1 ? i + b : n - 1;
+        for (int c = 0; c < nrhs; ++c) {
+            double s = X[(size_t)i * nrhs + c];
+            for (int k = i + 1; k <= kend; ++k) s -= LB[(size_t)k * w + (i - k + b)] * X[(size_t)k * nrhs + c];
+            X[(size_t)i * nrhs + c] = s / LB[(size_t)i * w + b];
+        }
+    }
+}
+
+/* Inertia count of a symmetric band matrix by LDL^T without pivoting on a
+ * copy of the band (the band is preserved by the elimination): number of
+ * negative pivots, or -1 if a pivot is exactly zero. */
+int orc_band_negative_count(int n, int b, const double *AB)
+{
+    const int w = b + 1;
+    double *W = (double *)malloc(sizeof(double) * (size_t)n * (size_t)w);
+    if (!W) return -2;
+    memcpy(W, AB, sizeof(double) * (size_t)n * (size_t)w);
+    int neg = 0;
+    for (int k = 0; k < n; ++k) {
+        const double d = W[(size_t)k * w + b];
+        if (d == 0.0) { free(W); return -1; }
+        if (d < 0.0) ++neg;
+        const int iend = k + b < n - 1 ? k + b : n - 1;
+        for (int i = k + 1; i <= iend; ++i) {
+            const double lik = W[(size_t)i * w + (k - i + b)] / d;
+            if (lik == 0.0) continue;
+            for (int j = k + 1; j <= i; ++j)
+                W[(size_t)i * w + (j - i + b)] -= lik * W[(size_t)j * w + (k - j + b)];
         }
     }
     free(W);

@@ -4,26 +4,40 @@ Test infrastructure only.  FP64 throughout.  Nothing here is shared with the
 CUDA library.
 """
 import ctypes
+import threading
+
 import numpy as np
 
 from . import _build
 
 _lib = None
+_lib_lock = threading.Lock()
 
 
 def _L():
     global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(_build.build())
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(_build.build())
         dp = ctypes.POINTER(ctypes.c_double)
-        _lib.orc_cholesky.argtypes = [ctypes.c_int, dp, dp]
-        _lib.orc_cholesky.restype = ctypes.c_int
-        _lib.orc_forward.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
-        _lib.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
-        _lib.orc_jacobi.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_double]
-        _lib.orc_jacobi.restype = ctypes.c_int
-        _lib.orc_ldlt_negative_count.argtypes = [ctypes.c_int, dp]
-        _lib.orc_ldlt_negative_count.restype = ctypes.c_int
+        lib.orc_cholesky.argtypes = [ctypes.c_int, dp, dp]
+        lib.orc_cholesky.restype = ctypes.c_int
+        lib.orc_forward.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.orc_jacobi.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_double]
+        lib.orc_jacobi.restype = ctypes.c_int
+        lib.orc_ldlt_negative_count.argtypes = [ctypes.c_int, dp]
+        lib.orc_ldlt_negative_count.restype = ctypes.c_int
+        lib.orc_band_cholesky.argtypes = [ctypes.c_int, ctypes.c_int, dp]
+        lib.orc_band_cholesky.restype = ctypes.c_int
+        lib.orc_band_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
+        lib.orc_band_solve.restype = None
+        lib.orc_band_negative_count.argtypes = [ctypes.c_int, ctypes.c_int, dp]
+        lib.orc_band_negative_count.restype = ctypes.c_int
+        _lib = lib
     return _lib
 
 
@@ -97,4 +111,61 @@ def negative_count(A):
     k = _L().orc_ldlt_negative_count(A.shape[0], _p(A))
     if k < 0:
         raise RuntimeError("LDL^T met a zero pivot")
+    return k
+
+
+# ---- band matrices (method mode): lower band, row-major by rows, entry
+# (i, j), i - b <= j <= i, at AB[i, j - i + b]
+
+def half_bandwidth(A):
+    """Largest |i - j| over the nonzero entries of a dense or sparse matrix."""
+    if hasattr(A, "tocoo"):
+        c = A.tocoo()
+        r, k = c.row[c.data != 0], c.col[c.data != 0]
+    else:
+        r, k = np.nonzero(A)
+    return int(np.abs(r - k).max()) if len(r) else 0
+
+
+def to_band(A, b):
+    """Lower band (n x (b+1)) of the symmetric matrix A (dense or sparse)."""
+    n = A.shape[0]
+    AB = np.zeros((n, b + 1))
+    if hasattr(A, "tocoo"):
+        c = A.tocoo()
+        low = c.row >= c.col
+        r, k, v = c.row[low], c.col[low], c.data[low]
+        if np.any(r - k > b):
+            raise ValueError("entry outside the band")
+        np.add.at(AB, (r, k - r + b), v)
+    else:
+        for d in range(b + 1):
+            AB[d:, b - d] = np.diagonal(A, -d)
+    return AB
+
+
+def band_cholesky(AB):
+    """Band factor L (same storage) with A = L L^T."""
+    L = np.ascontiguousarray(AB, dtype=np.float64).copy()
+    info = _L().orc_band_cholesky(L.shape[0], L.shape[1] - 1, _p(L))
+    if info:
+        raise NotSPDError(info - 1)
+    return L
+
+
+def band_solve(LB, B):
+    """Solve (L L^T) X = B with a band factor from band_cholesky."""
+    LB = np.ascontiguousarray(LB, dtype=np.float64)
+    vec = B.ndim == 1
+    X = np.ascontiguousarray(B.reshape(LB.shape[0], -1), dtype=np.float64).copy()
+    _L().orc_band_solve(LB.shape[0], LB.shape[1] - 1, _p(LB), X.shape[1], _p(X))
+    return X[:, 0] if vec else X
+
+
+def band_negative_count(AB):
+    """Number of negative eigenvalues of a symmetric band matrix (LDL^T inertia)."""
+    AB = np.ascontiguousarray(AB, dtype=np.float64)
+    k = _L().orc_band_negative_count(AB.shape[0], AB.shape[1] - 1, _p(AB))
+    if k < 0:
+        raise RuntimeError("band LDL^T met a zero pivot")
     return k

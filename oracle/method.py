@@ -284,12 +284,25 @@ class Hierarchy:
         self.levels[l] = lev
 
     # --- preconditioner and CG --------------------------------------------
+    def _fine_solve(self, s, r):
+        """A_i^{-1} r for fine subdomain s (Eq. dirichlet_space), from its factor."""
+        return linalg.cho_solve(s["Li"], r)
+
+    def _fine_local_solves(self, r):
+        """[A_i^{-1} R_i r for every fine subdomain i], in subdomain order."""
+        return [self._fine_solve(s, r[s["dof"]]) for s in self.levels[self.L].subs]
+
+    def _fine_sum(self, r, restricted=False):
+        """sum_i R_i^T A_i^{-1} R_i r over the fine subdomains (restricted:
+        each local solution weighted by chi_i first)."""
+        z = np.zeros_like(r)
+        for s, y in zip(self.levels[self.L].subs, self._fine_local_solves(r)):
+            z[s["dof"]] += s["chi_dir"] * y if restricted else y
+        return z
+
     def apply_preconditioner(self, r):
         """z = B r, the additive multilevel Schwarz preconditioner."""
-        z = np.zeros_like(r)
-        fine = self.levels[self.L]
-        for s in fine.subs:
-            z[s["dof"]] += linalg.cho_solve(s["Li"], r[s["dof"]])
+        z = self._fine_sum(r)
         for l in range(self.L - 1, 0, -1):
             lev = self.levels[l]
             rl = lev.P.T @ r
@@ -311,9 +324,7 @@ class Hierarchy:
         Eq. mlsdd).  The additive preconditioner is the sum over l."""
         z = np.zeros_like(r)
         if l == self.L:
-            for s in self.levels[self.L].subs:
-                y = linalg.cho_solve(s["Li"], r[s["dof"]])
-                z[s["dof"]] += s["chi_dir"] * y if restricted else y
+            z = self._fine_sum(r, restricted)
         elif l > 0:
             lev = self.levels[l]
             rl = lev.P.T @ r
@@ -342,10 +353,7 @@ class Hierarchy:
 
     def apply_one_level(self, r):
         """z = sum_i R_i^T A_i^{-1} R_i r over the fine subdomains only (no coarse space)."""
-        z = np.zeros_like(r)
-        for s in self.levels[self.L].subs:
-            z[s["dof"]] += linalg.cho_solve(s["Li"], r[s["dof"]])
-        return z
+        return self._fine_sum(r)
 
     def coarse_dims(self):
         """n_l for l = L-1 ... 0: dimension of each coarse space."""

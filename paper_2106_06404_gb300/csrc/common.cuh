@@ -135,9 +135,10 @@ __host__ __device__ inline double hash_uniform(uint64_t key) {
 
 // ---- FP64 <-> FP32 conversions on the integer pipe.  On this GPU the
 // conversion instructions share the narrow FP64 pipe; these bit-level
-// versions (IEEE 754 binary64/binary32 layouts) keep mixed-precision kernels
-// off it.  Round to nearest even; magnitudes below 2^-126 are flushed to a
-// signed zero (both directions); overflow gives infinity; NaN stays NaN.
+// versions, written from the IEEE 754 binary64/binary32 formats, keep
+// mixed-precision kernels off it.  Round to nearest even with gradual
+// underflow (subnormal results and inputs are exact IEEE), overflow to
+// infinity, NaN stays NaN (quiet).
 #ifdef __CUDACC__
 __device__ __forceinline__ float f64_to_f32(double x) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
@@ -149,7 +150,19 @@ __device__ __forceinline__ float f64_to_f32(double x) {
     const unsigned rest = lo & 0x1fffffffu;                        // the 29 dropped bits
     unsigned v = ((unsigned)ef << 23) + m;
     v += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;   // a carry may give infinity
-    if (ef <= 0) v = 0u;
+    if (ef <= 0) {
+        // subnormal (or zero) result: the significand with its leading one,
+        // in units of 2^-149, is sig >> (926 - e); a round-up to 2^23 is the
+        // smallest normal number's encoding
+        const unsigned long long sig = (1ull << 52) | (u & 0x000fffffffffffffull);
+        const int sh = 926 - e;                                   // >= 30 here
+        if (sh > 53 || e == 0) {
+            v = 0u;
+        } else {
+            const unsigned long long q = sig >> sh, r = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+            v = (unsigned)q + ((r > half || (r == half && (q & 1ull))) ? 1u : 0u);
+        }
+    }
     if (ef >= 255) v = (e == 0x7ff && ((hi & 0x000fffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
     return __uint_as_float(sign | v);
 }
@@ -160,7 +173,18 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     const unsigned m = u & 0x007fffffu;
     unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
     unsigned lo = m << 29;
-    if (e == 0u) { hi = sign; lo = 0u; }
+    if (e == 0u) {
+        if (m == 0u) {
+            hi = sign;
+            lo = 0u;
+        } else {
+            // subnormal input m 2^-149: leading one at bit p, exponent p - 149
+            const unsigned p = 31u - (unsigned)__clz(m);
+            const unsigned mn = (m << (23u - p)) & 0x007fffffu;
+            hi = sign | ((p + 874u) << 20) | (mn >> 3);
+            lo = mn << 29;
+        }
+    }
     if (e == 0xffu) { hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x00080000u : 0u); lo = m << 29; }
     return __hiloint2double((int)hi, (int)lo);
 }

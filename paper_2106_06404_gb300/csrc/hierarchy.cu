@@ -151,7 +151,9 @@ void run_eig(GevpBatch& g, const EigParams& ep, Apply apply, Solve solve, BApply
         for (int i = 0; i < v.P; ++i) {
             const double n = v.K.n[i], b = v.K.b[i], p = v.p[i];
             am[k].pm = std::max(am[k].pm, v.p[i]);
-            am[k].sb0 += 2.0 * n * (b + 1) * fsz + 4.0 * n * p * 8.0;
+            // factor band read by both sweeps; right-hand sides read once and
+            // solutions written once (FP64)
+            am[k].sb0 += 2.0 * n * (b + 1) * fsz + 2.0 * n * p * 8.0;
             am[k].sf0 += 4.0 * n * b * p;
             am[k].vec_n += n * p;
         }

@@ -1,7 +1,8 @@
 """Host logic of bench.py that needs no GPU: the replica workloads of the
-ranks, the max-over-ranks timing on a world-size-2 gloo process group, and
-the reference arm (the oracle on a bounded sample) with its JSON line on rank
-0 and no output on the other ranks."""
+ranks, the max-over-ranks timing on a world-size-2 gloo process group, the
+reference arm (one full oracle step per timed step) with its JSON line on
+rank 0 and no output on the other ranks, and the oracle leg with its error
+summary against given results."""
 import json
 import os
 import socket
@@ -55,7 +56,7 @@ def test_max_over_ranks_gloo_world_size_2(tmp_path):
 def _run_reference(rank, world):
     env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                           "--warmup", "0", "--workload", "channels64", "--cpu-subdomains", "1"],
+                           "--warmup", "0", "--workload", "channels64"],
                           capture_output=True, text=True, env=env, timeout=300)
 
 
@@ -71,6 +72,10 @@ def test_reference_arm_json_line_on_rank_0():
     assert d["impl"] == "reference" and d["higher_is_better"] is False
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["value"] > 0
+    # same config object as the GPU arm's
+    w = bench.workload("channels64", 0)
+    assert d["config"] == bench.workload_config(w, 4160, 1)
+    assert d["step_seconds"][0] <= d["value"] * 1.0001
 
 
 def test_reference_arm_other_ranks_exit_silently():
@@ -104,3 +109,37 @@ def test_solver_leg_times_both_solvers_and_records_failures():
     assert out["gmres_hybrid"]["rel_residual"] == 8e-7 and out["pcg_additive"]["ms"] >= 0.0
     out = bench.solver_leg(_FakeHierarchy(fail_gmres=True), None, steps=1, warmup=0, sync=lambda: None)
     assert "error" in out["gmres_hybrid"] and out["pcg_additive"]["iterations"] == 66
+
+
+def test_oracle_leg_error_summary(tmp_path):
+    """The oracle leg on the 64 x 64 workload, given the dense oracle's results
+    in the place of the GPU's: eigenvalue errors at the subspace iteration's
+    accuracy, equal counts, dimensions and iterations; a planted count
+    difference is reported."""
+    from oracle import fem, method
+    w = bench.workload("channels64", 0)
+    mesh = fem.Mesh(w.n, w.dirichlet_faces)
+    H = method.Hierarchy(mesh, w.coefficient(), w.parts, w.overlap, w.levels, w.group, w.nev_max, w.eta)
+    b = fem.load_vector(mesh)
+    x, it, *_ = method.pcg(H.A, b, H.apply_preconditioner, 1e-8)
+    subs = H.levels[H.L].subs
+    lam = np.full((len(subs), 32), np.nan)
+    for i, s in enumerate(subs):
+        k = min(32, len(s["lam"]))
+        lam[i, :k] = s["lam"][:k]
+    ms = np.array([s["m"] for s in subs])
+    ms[3] += 1                                            # planted difference
+    dims = [H.coarse_dims()[0], H.n]
+    path = tmp_path / "gpu.npz"
+    np.savez(path, level_dim=np.array(dims), iterations=np.array(it), x=x, fine_lam=lam, fine_m=ms)
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-leg", str(path),
+                        "--workload", "channels64"], capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr
+    d = json.loads(p.stdout.strip().splitlines()[-1])
+    assert d["seconds"] > 0 and d["cores"] >= 1 and d["iterations"] == it
+    e = d["error_vs_oracle"]
+    assert e["fine"]["max_rel_eig_err"] < 1e-8
+    assert e["fine"]["count_mismatch"] == [[3, int(ms[3]), int(ms[3]) - 1]]
+    assert e["coarse_dims"]["gpu"] == e["coarse_dims"]["oracle"]
+    assert e["iterations"]["gpu"] == e["iterations"]["oracle"]
+    assert e["solution_gpu"]["rel_err_A"] < 1e-6 and e["solution_oracle"]["rel_err_A"] < 1e-6

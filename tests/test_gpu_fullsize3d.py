@@ -78,7 +78,7 @@ def test_fine_ritz_values_and_selection(case, pidx):
     assert 1 <= m <= w.nev_max
     for k in sorted({1, 2, m - 1, m} - {0}):
         th = theta[k - 1]
-        d = 1e-4 * (th + SIGMA)
+        d = 1e-6 * (th + SIGMA)
         assert count_below(Abar, B, th - d) <= k - 1, (i, k, th)
         assert count_below(Abar, B, th + d) >= k, (i, k, th)
     lo = min(w.nev_max, count_below(Abar, B, w.eta * (1 - 1e-6)))
