@@ -247,3 +247,43 @@ int orc_band_negative_count(int n, int b, const double *AB)
     free(W);
     return neg;
 }
+
+/*
+ * Regularised LDL^T of a symmetric positive semi-definite matrix K (n x n,
+ * row-major, not modified), without pivoting, in the given order: pivot k
+ * is a null pivot when d_k <= tau * K_kk (K_kk the original diagonal entry),
+ * the epsilon-regularisation of Section 4.2 taken to its limit (D^+_k = 0):
+ * then d_k = 0, column k of L is zero below the diagonal and the remaining
+ * Schur complement is not updated by row k (the generator is dropped as
+ * dependent on the earlier ones).  Outputs L (unit lower, n x n), d (n) and
+ * null (n flags).  Returns the number of null pivots, or -2 on allocation
+ * failure.
+ */
+int orc_ldlt_null(int n, const double *K, double tau, double *L, double *d, int *null)
+{
+    double *W = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    if (!W) return -2;
+    memcpy(W, K, sizeof(double) * (size_t)n * (size_t)n);
+    memset(L, 0, sizeof(double) * (size_t)n * (size_t)n);
+    int nn = 0;
+    for (int k = 0; k < n; ++k) {
+        L[(size_t)k * n + k] = 1.0;
+        const double dk = W[(size_t)k * n + k];
+        if (!(dk > tau * K[(size_t)k * n + k])) {
+            d[k] = 0.0;
+            null[k] = 1;
+            ++nn;
+            continue;
+        }
+        d[k] = dk;
+        null[k] = 0;
+        for (int i = k + 1; i < n; ++i) L[(size_t)i * n + k] = W[(size_t)i * n + k] / dk;
+        for (int i = k + 1; i < n; ++i) {
+            const double lik = L[(size_t)i * n + k];
+            if (lik == 0.0) continue;
+            for (int j = k + 1; j <= i; ++j) W[(size_t)i * n + j] -= lik * W[(size_t)j * n + k];
+        }
+    }
+    free(W);
+    return nn;
+}

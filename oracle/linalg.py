@@ -37,6 +37,9 @@ def _L():
         lib.orc_band_solve.restype = None
         lib.orc_band_negative_count.argtypes = [ctypes.c_int, ctypes.c_int, dp]
         lib.orc_band_negative_count.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.orc_ldlt_null.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, ip]
+        lib.orc_ldlt_null.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -169,3 +172,19 @@ def band_negative_count(AB):
     if k < 0:
         raise RuntimeError("band LDL^T met a zero pivot")
     return k
+
+
+def ldlt_null(K, tau):
+    """Regularised LDL^T of symmetric positive semi-definite K in the given
+    order (linalg.c: orc_ldlt_null): returns (L unit lower, d, null flags);
+    pivots with d_k <= tau K_kk are null (d_k = 0, column k of L zero)."""
+    K = np.ascontiguousarray(0.5 * (K + K.T), dtype=np.float64)
+    n = K.shape[0]
+    L = np.zeros_like(K)
+    d = np.zeros(n)
+    null = np.zeros(n, dtype=np.int32)
+    r = _L().orc_ldlt_null(n, _p(K), float(tau), _p(L), _p(d),
+                           null.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if r < 0:
+        raise MemoryError("orc_ldlt_null")
+    return L, d, null.astype(bool)

@@ -8,11 +8,13 @@ Steps, in the paper's order and notation:
      (Eq. locala_cg) and the partition-of-unity weighted form
      b^1_{l,i}(u, v) = abar_{l,i}(chi u, chi v) (Eq. cg_rhs_blf, first line).
   2. Local GEVPs abar(w, v) = lambda b(w, v) (Eq. theGEVP), solved exactly:
-     after dropping the common kernel ker A cap ker B (Section 3.3 remark and
-     Section 4.2: on coarse levels only a generating system is available),
      the spectral transformation b(p, v) = mu (a + b)(p, v), mu = 1/(1+lambda)
      (proof of the non-defectiveness lemma, Section 3.3) turns the pencil into
      a standard symmetric problem that the Jacobi method solves completely.
+     On coarse levels only a generating system is available and
+     ker A cap ker B is not trivial (Section 3.3 remark); the generators
+     that the regularised LDL^T of Section 4.2 (Eq. evp_reg) finds dependent
+     are dropped first (gevp_regularised).
   3. Coarse space V_{h,l-1} = span{ e chi w : lambda < eta } (Eq.
      coarse_space_def), at most nev_max per subdomain (Section 5.1.1 offers a
      fixed count or a threshold; both are applied, the smaller wins).
@@ -26,10 +28,14 @@ Steps, in the paper's order and notation:
      Euclidean norm.
 
 Readings where the paper is silent (listed with the others in the design
-notes): rank threshold 1e-12 * max eigenvalue of (A + B) for dropping the
-common kernel; eigenvalues with mu <= 1e-13 are treated as +infinity; an
-eigenvector is normalised to b(w, w) = 1 and signed so that its entry of
-largest magnitude is positive; selection uses lambda < eta strictly.
+notes): on coarse levels the regularised LDL^T factors K = A + sigma B
+(sigma = 1e-2) in generator order, and a pivot d_k <= tau K_kk is a null
+pivot (tau = 1e-10 in 2D, 1e-6 in 3D; eps^{-1} -> 0); for the b^2 and b^3
+forms on the fine level the common kernel is dropped by a rank threshold
+1e-12 * max eigenvalue of (A + B); eigenvalues with mu <= 1e-13 are treated
+as +infinity; an eigenvector is normalised to b(w, w) = 1 and signed so that
+its entry of largest magnitude is positive; selection uses lambda < eta
+strictly.
 """
 import os
 from concurrent.futures import ThreadPoolExecutor
@@ -79,6 +85,33 @@ def gevp(Abar, B, rank_reveal):
     W = W / np.sqrt(mu)[None, :]            # b(w, w) = v^T C v / mu = 1
     lam = 1.0 / mu - 1.0
     return lam, W
+
+
+def gevp_regularised(Abar, B, sigma, tau):
+    """All finite eigenpairs of the generating-system pencil of a coarse
+    level (Section 4.2, Eq. evp_reg), ascending.
+
+    The paper factors the pencil's matrix as L D L^T and replaces the zero
+    pivots by 0 < eps << 1; the vectors that pass through the regularised
+    pivots then have eigenvalues near eps (lambda ~ 0, kernel directions)
+    or belong to ker B (lambda = infinity).  Reading, in the limit
+    eps^{-1} -> 0 and with the shift of the spectral transformation: the
+    matrix factored is K = Abar + sigma B, in generator order, and a pivot
+    d_k <= tau K_kk is a null pivot, which drops generator k as dependent on
+    the earlier ones in K-energy.  The pencil is then solved completely on
+    the kept directions V = L^{-T}[:, kept] (span of the generating system
+    less those dependencies) by gevp().  Returns (lam, W), W = V W_r with
+    W^T B W = I, and the number of null pivots."""
+    K = Abar + sigma * B
+    L, d, null = linalg.ldlt_null(K, tau)
+    keep = ~null
+    n = Abar.shape[0]
+    E = np.eye(n)[:, keep]
+    V = linalg.backward(L, E)                  # L^T V = E: V = L^{-T} E (L unit lower)
+    Ar = V.T @ Abar @ V
+    Br = V.T @ B @ V
+    lam, Wr = gevp(0.5 * (Ar + Ar.T), 0.5 * (Br + Br.T), rank_reveal=False)
+    return lam, V @ Wr, int(null.sum())
 
 
 def normalise_sign(W):
@@ -152,11 +185,15 @@ class Hierarchy:
     """Result of the oracle set-up: all levels, spaces and factors."""
 
     def __init__(self, mesh, coeff, parts, overlap, levels, group, nev_max, eta,
-                 keep_local=False, blf=1):
+                 keep_local=False, blf=1, sigma=1e-2, reg_tol=None):
         self.mesh = mesh
         self.nev_max = nev_max
         self.eta = eta
         self.blf = blf
+        # coarse-level generating systems (Section 4.2): shift and null-pivot
+        # threshold of the regularised LDL^T (readings; 1e-10 in 2D, 1e-6 in 3D)
+        self.sigma = sigma
+        self.reg_tol = reg_tol if reg_tol is not None else (1e-10 if mesh.dim == 2 else 1e-6)
         self.A = fem.assemble_system(mesh, coeff)
         self.n = self.A.shape[0]
         self.dec = Decomposition(mesh, parts, overlap, levels, group)
@@ -250,12 +287,12 @@ class Hierarchy:
             Abar = 0.5 * (Abar + Abar.T)
             x = np.concatenate([np.ones(len(own_cols)), np.zeros(len(nbr_cols))])
             B = x[:, None] * Abar * x[None, :]
-            lam, W = gevp(Abar, B, rank_reveal=True)
+            lam, W, nnull = gevp_regularised(Abar, B, self.sigma, self.reg_tol)
             m = select_count(lam, self.nev_max, self.eta)
             Wm = normalise_sign(W[:, :m])
             Ai = Al[np.ix_(own_cols, own_cols)]
             Li = linalg.cholesky(Ai) if len(own_cols) else None
-            return dict(own=own, nbr=nbr, own_cols=own_cols, gen=gen,
+            return dict(own=own, nbr=nbr, own_cols=own_cols, gen=gen, null_pivots=nnull,
                         Abar=Abar if keep_local else None, B=B if keep_local else None,
                         lam=lam, m=m, W=Wm, Ai=Ai if keep_local else None, Li=Li)
 

@@ -23,7 +23,11 @@ same pencil by an independent route and check what Section 3.3 fixes:
   * brute force: scipy's LAPACK symmetric-definite solver on the
     rank-reduced, spectrally transformed pencil;
   * the projection stability estimates (Lemma gevp_properties) for the
-    oracle's eigenvectors on random vectors.
+    oracle's eigenvectors on random vectors;
+  * the regularised LDL^T route of Section 4.2 (Eq. evp_reg) that the
+    oracle takes on coarse levels: on generators with exact dependencies it
+    drops exactly those (null pivots = dim ker A cap ker B) and yields the
+    pencil's eigenvalues on the span, whatever the generators' scaling.
 """
 import numpy as np
 import pytest
@@ -192,3 +196,60 @@ def test_coarse_projection_stability(fixture, request):
                 if m >= r and m < len(lam):
                     d = v - Pv
                     assert bn2(d) <= an(d) ** 2 / lam[m] * (1 + 1e-7) + 1e-12
+
+
+def _dependent_pencil(rng, scales=None):
+    """A = G^T Sa G, B = G^T Sb G on generators G (columns) with exact
+    dependencies: ker A cap ker B = ker G."""
+    m, k = 30, 12
+    G = rng.standard_normal((m, k))
+    G = np.concatenate([G, G[:, [0]] + G[:, [1]], 3.0 * G[:, [4]], G[:, [2]] - 0.5 * G[:, [7]]], axis=1)
+    M = rng.standard_normal((m, m))
+    Sa = M @ M.T + m * np.eye(m)
+    mask = np.zeros(m)
+    mask[: m // 2] = 1.0
+    Sb = mask[:, None] * Sa * mask[None, :]
+    A, B = G.T @ Sa @ G, G.T @ Sb @ G
+    if scales is not None:
+        A = scales[:, None] * A * scales[None, :]
+        B = scales[:, None] * B * scales[None, :]
+        G = G * scales[None, :]
+    return G, Sa, Sb, A, B
+
+
+def test_regularised_gevp_equals_pencil_on_the_span():
+    """Section 4.2: with dependent generators the regularised LDL^T drops
+    exactly the dependencies (3 null pivots here), and the eigenvalues are
+    those of the pencil on span(G) (orthonormal basis by SVD, scipy's
+    symmetric-definite solver); a rescaling of the generators changes
+    nothing."""
+    rng = np.random.default_rng(3)
+    G, Sa, Sb, A, B = _dependent_pencil(rng)
+    U, s, _ = np.linalg.svd(G, full_matrices=False)
+    Q = U[:, s > 1e-10 * s[0]]
+    ref = sla.eigh(Q.T @ Sa @ Q, Q.T @ (Sa + Sb) @ Q, eigvals_only=True)   # mu-type: a = nu (a + b)
+    nu = np.sort(ref)
+    mu_b = 1.0 - nu                                # b = (1 - nu)(a + b)
+    fin = mu_b > 1e-12
+    lam_ref = np.sort(nu[fin] / mu_b[fin])
+    lam, W, nnull = method.gevp_regularised(A, B, 1e-2, 1e-10)
+    assert nnull == G.shape[1] - Q.shape[1] == 3
+    assert len(lam) == len(lam_ref)
+    assert np.allclose(lam, lam_ref, rtol=1e-8, atol=1e-10)
+    assert np.allclose(W.T @ B @ W, np.eye(len(lam)), atol=1e-8)
+    assert np.allclose(A @ W, (B @ W) * lam[None, :], atol=1e-7 * np.abs(A).max())
+    scales = np.exp(rng.uniform(np.log(1e-6), np.log(1e3), G.shape[1]))
+    _, _, _, As, Bs = _dependent_pencil(np.random.default_rng(3), scales)
+    lam_s, _, nnull_s = method.gevp_regularised(As, Bs, 1e-2, 1e-10)
+    assert nnull_s == 3 and np.allclose(lam_s, lam, rtol=1e-7, atol=1e-10)
+
+
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level"])
+def test_null_pivots_are_the_common_kernel(fixture, request):
+    """On these cases every null pivot is an exact dependency: their number
+    is dim(ker A cap ker B) = n - rank(A + B)."""
+    mesh, kap, H = request.getfixturevalue(fixture)
+    for s in H.levels[1].subs:
+        A, B = s["Abar"], s["B"]
+        rAB, _ = _rank(A + B)
+        assert s["null_pivots"] == A.shape[0] - rAB

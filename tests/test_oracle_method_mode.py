@@ -8,8 +8,9 @@ the fine level) against the dense oracle and against brute force.
     dense GEVP solution: eigenvalues, b-orthonormality, residuals;
   * the whole method-mode hierarchy against the dense oracle on the 64 x 64
     channel workload (two levels) and a three-level case: selected counts
-    and coarse dimensions exact, eigenvalues to 1e-8 relative, the
-    preconditioner application and the PCG iterates to 1e-8;
+    and coarse dimensions exact, eigenvalues to 1e-8 relative (1e-7 on the
+    middle level), the preconditioner application and the PCG iterates to
+    1e-8;
   * worker processes give the same result as the in-process loop.
 """
 import numpy as np
@@ -106,7 +107,9 @@ def test_method_mode_matches_dense_oracle(name):
             assert a["m"] == b["m"]
             k = a["m"]
             err = np.abs(a["lam"][:k] - b["lam"][:k]) / np.maximum(np.abs(a["lam"][:k]), 1e-3 * c["eta"])
-            assert err.max() < 1e-8, (l, err)
+            # middle level: its pencil is built from the fine eigenvectors,
+            # whose errors (residual 1e-10 over the gaps) enter at first order
+            assert err.max() < (1e-8 if l == D.L else 1e-7), (l, err)
     assert D.coarse_dims() == M.coarse_dims()
     rng = np.random.default_rng(2)
     r = rng.standard_normal(D.n)
