@@ -185,3 +185,51 @@ class MethodModeHierarchy(method.Hierarchy):
 
     def _fine_solve(self, s, r):
         return linalg.band_solve(s["Li"], r)
+
+
+# ---- a bounded sample of the fine level (for workloads too large for a
+# full oracle run on the host): workers build only what the sampled
+# subdomains need (their element matrices, the partition of unity)
+def _sample_init(n, dirichlet_faces, coeff, parts, overlap, levels, group, opts):
+    mesh = fem.Mesh(n, dirichlet_faces)
+    dec = Decomposition(mesh, parts, overlap, levels, group)
+    chis, counts = dec.partition_of_unity()
+    _W.update(mesh=mesh, dec=dec, chis=chis, coeff=np.asarray(coeff), en=mesh.element_nodes(), opts=opts)
+
+
+def _sample_local(i):
+    mesh, dec, o = _W["mesh"], _W["dec"], _W["opts"]
+    s = dec.fine[i]
+    nn = s.neumann_nodes()
+    chi = _W["chis"][i]
+    mask = s.element_mask
+    Ke = fem.element_matrices(mesh, _W["coeff"][mask])
+    idx = np.nonzero(mask)[0]
+    full_mask = np.ones(len(idx), dtype=bool)
+    Abar = local_neumann(Ke, _W["en"][idx], full_mask, nn, mesh.num_nodes)
+    X = sp.diags(chi)
+    B = (X @ Abar @ X).tocsr()
+    K = (Abar + o["sigma"] * B).tocsr()
+    KL = linalg.band_cholesky(linalg.to_band(K, linalg.half_bandwidth(K)))
+    rng = np.random.default_rng([o["seed"], i])
+    theta, Xr, its = subspace_iteration(Abar, B, KL, o["nev_max"], o["eta"], o["nev_max"] + o["extra"], o["tol"],
+                                        o["maxit"], rng)
+    return dict(lam=theta, m=method.select_count(theta, o["nev_max"], o["eta"]), eig_iterations=its)
+
+
+def fine_level_sample(n, dirichlet_faces, coeff, parts, overlap, levels, group, nev_max, eta, sample, processes,
+                      sigma=1e-2, tol=1e-8, extra=8, maxit=400, seed=0):
+    """Method-mode fine-level eigenpairs (Ritz values, selected counts) of the
+    fine subdomains listed in `sample`, in `processes` spawned workers."""
+    opts = dict(sigma=sigma, tol=tol, extra=extra, maxit=maxit, seed=seed, nev_max=nev_max, eta=eta)
+    args = (tuple(n), dirichlet_faces, np.asarray(coeff), tuple(parts), overlap, levels, tuple(group), opts)
+    if processes > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(min(processes, len(sample)), mp_context=mp.get_context("spawn"),
+                                 initializer=_sample_init, initargs=args) as ex:
+            return list(ex.map(_sample_local, sample))
+    _sample_init(*args)
+    out = [_sample_local(i) for i in sample]
+    _W.clear()
+    return out

@@ -1027,14 +1027,8 @@ __global__ void __launch_bounds__(8 * CG) k_tile_solve_band(
     cp_async_wait_n<0>();
 }
 
-// ---- the FP32 band solve with TMA tile loads
-// Same steps as k_tile_solve_band<float, 1, 16> (16 right-hand sides per
-// CTA; NT = 128, 256 or 512 threads hold 4, 2 or 1 rows of a tile row each,
-// so more threads shorten each step's dependent chain); the tiles of a step and D^{-1} are
-// fetched by one thread with cp.async.bulk(.tensor) into 128-byte-swizzled
-// shared tiles (16-byte chunk g of row r at g ^ (r & 7)), completion tracked
-// by one mbarrier per stage.  Every mbarrier wait is bounded: on timeout the
-// CTA sets *err, waits (bounded) for its copies in flight and returns.
+// ---- TMA / mbarrier helpers of the FP32 band solve.  Every mbarrier wait is
+// bounded; a kernel whose wait runs out records it in g_wait_timeouts.
 __device__ int g_wait_timeouts;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -1072,213 +1066,266 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
-__device__ __forceinline__ void tma_load4(const float* tile, int r, int g, float (&v)[4]) {
-    const float4 x = *reinterpret_cast<const float4*>(tile + r * NB + ((g ^ (r & 7)) << 2));
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
-// N = 1, 2 or 4 consecutive entries of row r from column c (c a multiple of N)
-template <int N>
-__device__ __forceinline__ void tma_loadn(const float* tile, int r, int c, float (&v)[N]) {
-    const float* q = tile + r * NB + (((c >> 2) ^ (r & 7)) << 2) + (c & 3);
-    if constexpr (N == 4) {
-        const float4 x = *reinterpret_cast<const float4*>(q);
+// ---- the FP32 band solve with TMA tile loads, warp-specialised (kb <= 2)
+// The steps and expressions of k_tile_solve_band<float> (forward z_R = T_R
+// (x_R - sum_J L_RJ z_J), backward x_R = T_R^T (D_R^{-1} z_R - sum_I L_IR^T
+// x_I), products summed in the same order), arranged so that no block
+// barrier sits on the sweeps' chain: each
+// of W consumer warps owns C right-hand-side columns and all 32 rows of a
+// tile row (lane = row), so a step's data exchange is warp-internal
+// (__syncwarp); a producer warp streams the tiles of each step and D^{-1}
+// with TMA into an NST-stage ring ("full" mbarriers completed by the copies'
+// byte counts, "empty" mbarriers released by each consumer warp after its
+// last read of the stage).  Each lane prefetches its own row of the
+// right-hand sides with cp.async, XD steps ahead.  Column k of tile
+// L_{R,R-d} can be nonzero only where 32 d + r - k <= b (the band), so the
+// forward products start at k = 32 d - b and the backward ones stop at
+// k = b - 32 d + 31.  Every wait is bounded; on a timeout the CTA records it
+// (g_wait_timeouts), the producer waits (bounded) for the copies it still
+// has in flight, and the CTA returns.
+template <int C>
+__device__ __forceinline__ void ws_ld(const float* p, float (&v)[C]) {
+    if constexpr (C == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
         v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-    } else if constexpr (N == 2) {
-        const float2 x = *reinterpret_cast<const float2*>(q);
+    } else if constexpr (C == 2) {
+        const float2 x = *reinterpret_cast<const float2*>(p);
         v[0] = x.x; v[1] = x.y;
     } else {
-        v[0] = *q;
+        v[0] = *p;
+    }
+}
+template <int C>
+__device__ __forceinline__ void ws_st(float* p, const float (&v)[C]) {
+    if constexpr (C == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else if constexpr (C == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    else *p = v[0];
+}
+// element (row, col) of a 128-byte-swizzled 32 x 32 FP32 tile
+__device__ __forceinline__ int swz(int row, int col) { return row * NB + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3); }
+
+// acc[c] += SIGN * sum_{K0 <= k < K1} tile[lane][k] V[k][c]  (row access of a
+// swizzled tile; V: [32][C] floats, read by broadcast).  Fully unrolled so
+// that all loads issue ahead of the products.
+template <int C, int K0, int K1, int SIGN>
+__device__ __forceinline__ void ws_row_product(const float* tile, const float* V, int lane, float (&acc)[C]) {
+    float l[K1 - K0];
+#pragma unroll
+    for (int g = K0 / 4; g < K1 / 4; ++g) {
+        const float4 x = *reinterpret_cast<const float4*>(tile + lane * NB + ((g ^ (lane & 7)) << 2));
+        l[4 * g - K0] = x.x; l[4 * g - K0 + 1] = x.y; l[4 * g - K0 + 2] = x.z; l[4 * g - K0 + 3] = x.w;
+    }
+#pragma unroll
+    for (int k = K0; k < K1; ++k) {
+        float v[C];
+        ws_ld<C>(V + k * C, v);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            if (SIGN > 0) acc[c] += l[k - K0] * v[c];
+            else acc[c] -= l[k - K0] * v[c];
+        }
+    }
+}
+// acc[c] += SIGN * sum_{0 <= k < K1} tile[k][lane] V[k][c]  (column access)
+template <int C, int K1, int SIGN>
+__device__ __forceinline__ void ws_col_product(const float* tile, const float* V, int lane, float (&acc)[C]) {
+    float l[K1];
+#pragma unroll
+    for (int k = 0; k < K1; ++k) l[k] = tile[swz(k, lane)];
+#pragma unroll
+    for (int k = 0; k < K1; ++k) {
+        float v[C];
+        ws_ld<C>(V + k * C, v);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            if (SIGN > 0) acc[c] += l[k] * v[c];
+            else acc[c] -= l[k] * v[c];
+        }
     }
 }
 
-constexpr int BT_NT = 256, BT_CG = 16, BT_ZLD = 16, BT_NST = 3;
-constexpr size_t band_tma_smem_bytes() {
-    return 1024 + sizeof(float) * ((size_t)BT_NST * BAND_SLOTS * NB2) + sizeof(double) * (size_t)BT_NST * NB * BT_ZLD +
-           sizeof(float) * ((size_t)BT_NST * NB + (size_t)(BAND_SLOTS + 1) * NB * BT_ZLD) + 8 * BT_NST;
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// NT threads: a row group of BT_CG threads holds the BT_CG columns of RPT rows.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_tile_solve_band_tma(
+template <int W, int C, int NST, int XD>
+struct BandWs {
+    static constexpr int NT = 32 * (W + 1);
+    static constexpr int COLS = W * C;
+    static constexpr size_t stage_bytes = (size_t)BAND_SLOTS * NB2 * sizeof(float);
+    static constexpr size_t warp_bytes =
+        sizeof(float) * ((size_t)BAND_SLOTS * NB * C + (size_t)NB * C) + sizeof(double) * (size_t)XD * NB * C;
+    static constexpr size_t smem_bytes =
+        1024 + (size_t)NST * stage_bytes + (size_t)NST * NB * sizeof(float) + 16 * (size_t)NST + (size_t)W * warp_bytes;
+};
+
+template <int W, int C, int NST, int XD>
+__global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
     const __grid_constant__ CUtensorMap tmt, const float* __restrict__ dinv, const int* __restrict__ kb_,
-    const int* __restrict__ K_, const long long* __restrict__ toff_, const long long* __restrict__ roff_,
-    double* __restrict__ Xall, int ldx, int ncols_all, const int* __restrict__ skip, const int* __restrict__ gdone)
+    const int* __restrict__ K_, const int* __restrict__ b_, const long long* __restrict__ toff_,
+    const long long* __restrict__ roff_, double* __restrict__ Xall, int ldx, int ncols_all,
+    const int* __restrict__ skip, const int* __restrict__ gdone)
 {
-    constexpr int NST = BT_NST, ZLD = BT_ZLD, RPT = NB * BT_CG / NT;
-    static_assert(RPT == 1 || RPT == 2 || RPT == 4, "4, 2 or 1 rows per thread");
+    using Cfg = BandWs<W, C, NST, XD>;
+    static_assert(C == 1 || C == 2 || C == 4, "1, 2 or 4 columns per warp");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    float* St = reinterpret_cast<float*>(base);                               // [NST][SLOTS][32*32]
-    double* Sx = reinterpret_cast<double*>(St + (size_t)NST * BAND_SLOTS * NB2); // [NST][32][ZLD]
-    float* Sd = reinterpret_cast<float*>(Sx + (size_t)NST * NB * ZLD);         // [NST][32]
-    float* Zr = Sd + (size_t)NST * NB;                                         // [SLOTS][32][ZLD]
-    float* Acc = Zr + (size_t)BAND_SLOTS * NB * ZLD;                           // [32][ZLD]
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(Acc + (size_t)NB * ZLD);
+    float* St = reinterpret_cast<float*>(base);                                        // [NST][SLOTS][32*32]
+    float* Sd = St + (size_t)NST * BAND_SLOTS * NB2;                                   // [NST][32]
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(Sd + (size_t)NST * NB);
+    unsigned long long* empty = full + NST;
+    unsigned char* wbase = reinterpret_cast<unsigned char*>(empty + NST);
+    __shared__ int s_abort;
+
     const int i = blockIdx.x;
     if (skip && skip[i]) return;
     if (gdone && *gdone) return;
-    const int cbase = blockIdx.y * ZLD;
-    const int ncols = min(ZLD, ncols_all - cbase);
-    double* __restrict__ X = Xall + cbase;
-    const int cpr = (ncols + 1) / 2;                    // 16-byte chunks of a staged X row
-    const int kb = kb_[i], K = K_[i];
+    const int kb = kb_[i], K = K_[i], bw = b_[i];
     const long long toff = toff_[i], roff = roff_[i];
-    const int t = threadIdx.x;
-    const int rg = t / BT_CG, c0 = t % BT_CG, warp = t >> 5;
-    const int r0 = RPT * rg;
-    constexpr int WROWS = RPT * 32 / BT_CG;                  // rows of one warp
-    const int wrow_lo = WROWS * warp, wgrp_hi = (WROWS * warp + WROWS - 1) >> 2;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (t == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        s_abort = 0;
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W);
+        }
         fence_mbar_init();
-        fence_async_smem();
     }
     __syncthreads();
-    unsigned phase = 0, pending = 0;                   // per-stage parity; stages with copies in flight (thread 0)
     auto stile = [&](int st, int slot) { return St + (size_t)(st * BAND_SLOTS + slot) * NB2; };
-    auto issue = [&](int st, int R, bool fwd) {
-        if (R >= 0 && R < K) {
-            if (t == 0) {
-                fence_async_smem();
+    auto give_up = [&]() {
+        if (atomicExch(&s_abort, 1) == 0) atomicAdd(&g_wait_timeouts, 1);
+    };
+    const int total = 2 * K;                         // steps of both sweeps
+
+    if (warp == W) {
+        // ---------------- producer: one lane issues every copy
+        if (lane == 0) {
+            unsigned pending = 0, par = 0;           // stages with copies in flight, their phase parity
+            for (int it = 0; it < total; ++it) {
+                const int st = it % NST;
+                if (it >= NST) {
+                    if (!mbar_wait_bounded(&empty[st], ((it / NST) - 1) & 1u)) { give_up(); break; }
+                    pending &= ~(1u << st);
+                }
+                if (*(volatile int*)&s_abort) break;
+                const bool fwd = it < K;
+                const int R = fwd ? it : total - 1 - it;
                 int nt = 1;
                 for (int d = 1; d <= kb; ++d) {
                     const int o = fwd ? R - d : R + d;
                     if (o >= 0 && o < K) ++nt;
                 }
-                mbar_expect_tx(&bars[st], nt * NB2 * 4 + (fwd ? 0 : NB * 4));
-                tma_load_tile(stile(st, 0), &tmt, (int)(tile_index(toff, kb, R, R) / NB), &bars[st]);
+                mbar_expect_tx(&full[st], nt * NB2 * 4 + (fwd ? 0 : NB * 4));
+                tma_load_tile(stile(st, 0), &tmt, (int)(tile_index(toff, kb, R, R) / NB), &full[st]);
                 for (int d = 1; d <= kb; ++d) {
                     const int o = fwd ? R - d : R + d;
                     if (o < 0 || o >= K) continue;
                     const long long ti = fwd ? tile_index(toff, kb, R, o) : tile_index(toff, kb, o, R);
-                    tma_load_tile(stile(st, d), &tmt, (int)(ti / NB), &bars[st]);
+                    tma_load_tile(stile(st, d), &tmt, (int)(ti / NB), &full[st]);
                 }
-                if (!fwd) bulk_load(Sd + st * NB, dinv + roff + (long long)R * NB, NB * 4, &bars[st]);
+                if (!fwd) bulk_load(Sd + st * NB, dinv + roff + (long long)R * NB, NB * 4, &full[st]);
                 pending |= 1u << st;
+                par = (par & ~(1u << st)) | (((unsigned)(it / NST) & 1u) << st);
             }
-            const double* src = X + (roff + (long long)R * NB) * ldx;
-            double* dst = Sx + (size_t)st * NB * ZLD;
-            for (int ch = t; ch < NB * cpr; ch += NT) {
-                const int r = ch / cpr, c = (ch % cpr) * 2;
-                cp_async16(dst + r * ZLD + c, src + (long long)r * ldx + c);
+            // after an abort, copies still in flight must land before the CTA exits
+            if (*(volatile int*)&s_abort)
+                for (int s = 0; s < NST; ++s)
+                    if (pending & (1u << s)) mbar_wait_bounded(&full[s], (par >> s) & 1u);
+        }
+        return;
+    }
+
+    // ---------------- consumer warp: columns [c_lo, c_lo + nc)
+    const int c_lo = blockIdx.y * Cfg::COLS + warp * C;
+    const int nc = max(0, min(C, ncols_all - c_lo));
+    float* Zr = reinterpret_cast<float*>(wbase + (size_t)warp * Cfg::warp_bytes);     // [SLOTS][32][C]
+    float* Acc = Zr + (size_t)BAND_SLOTS * NB * C;                                      // [32][C]
+    double* Xs = reinterpret_cast<double*>(Acc + (size_t)NB * C);                      // [XD][32][C]
+    double* X = Xall + c_lo;
+    // loads of this lane's row: index q < K: forward step q (row q); q >= K:
+    // backward row K - 4 - (q - K) (backward steps s >= 3; rows K-1..K-3 are
+    // still in the Zr ring when the backward sweep starts)
+    const int nload = K + max(0, K - 3);
+    auto issue_load = [&](int q) {
+        if (q < nload && nc > 0) {
+            if (q >= K) __threadfence_block();       // rows written by this lane in the forward sweep
+            const int R = q < K ? q : K - 4 - (q - K);
+            const double* src = X + (roff + (long long)R * NB + lane) * ldx;
+            double* dst = Xs + ((size_t)(q % XD) * NB + lane) * C;
+            if constexpr (C == 1) {
+                // one double: an 8-byte copy
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+            } else {
+                cp_async16(dst, src);
+                if (C == 4 && nc > 2) cp_async16(dst + 2, src + 2);
             }
         }
         cp_async_commit();
     };
-    // wait for stage st (TMA part: bounded); false if any thread gave up
-    auto wait_stage = [&](int st) -> bool {
-        cp_async_wait_n<NST - 2>();
-        const bool ok = mbar_wait_bounded(&bars[st], (phase >> st) & 1u);
-        phase ^= 1u << st;
-        if (t == 0) pending &= ~(1u << st);
-        return !__syncthreads_or(!ok);
-    };
-    auto abort_cta = [&]() {
-        if (t == 0) {
-            atomicAdd(&g_wait_timeouts, 1);
-            for (int s = 0; s < NST; ++s)
-                if (pending & (1u << s)) mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
-        }
-        cp_async_wait_n<0>();
-        __syncthreads();
-    };
-    auto finish = [&](float (&acc)[RPT], int R, const float* Tt, bool fwd) {
-#pragma unroll
-        for (int a = 0; a < RPT; ++a) Acc[(r0 + a) * ZLD + c0] = acc[a];
-        __syncthreads();
-        float out[RPT];
-#pragma unroll
-        for (int a = 0; a < RPT; ++a) out[a] = 0.f;
-        if (fwd) {
-#pragma unroll 4
-            for (int g = 0; g <= wgrp_hi; ++g) {
-                float l[RPT][4];
-#pragma unroll
-                for (int a = 0; a < RPT; ++a) tma_load4(Tt, r0 + a, g, l[a]);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const float zv = Acc[(4 * g + kk) * ZLD + c0];
-#pragma unroll
-                    for (int a = 0; a < RPT; ++a) out[a] += l[a][kk] * zv;
-                }
-            }
-        } else {
-#pragma unroll 4
-            for (int k = wrow_lo; k < NB; ++k) {
-                float l[RPT];
-                tma_loadn<RPT>(Tt, k, r0, l);
-                const float zv = Acc[k * ZLD + c0];
-#pragma unroll
-                for (int a = 0; a < RPT; ++a) out[a] += l[a] * zv;
-            }
-        }
-        float* Zw = Zr + (size_t)(R % BAND_SLOTS) * NB * ZLD;
-#pragma unroll
-        for (int a = 0; a < RPT; ++a) {
-            Zw[(r0 + a) * ZLD + c0] = out[a];
-            if (c0 < ncols) X[(roff + (long long)R * NB + r0 + a) * ldx + c0] = f32_to_f64(out[a]);
-        }
-    };
-
-    // forward: z_R = T_R (x_R - sum_J L_RJ z_J)
-    for (int k = 0; k < NST - 1; ++k) issue(k, k, true);
-    for (int R = 0; R < K; ++R) {
-        const int st = R % NST;
-        if (!wait_stage(st)) { abort_cta(); return; }
-        issue((R + NST - 1) % NST, R + NST - 1, true);
-        float acc[RPT];
-        const double* xs = Sx + (size_t)st * NB * ZLD;
-#pragma unroll
-        for (int a = 0; a < RPT; ++a) acc[a] = c0 < ncols ? f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
-        for (int d = 1; d <= kb; ++d) {
-            if (R - d < 0) break;
-            const float* L = stile(st, d);
-            const float* Z = Zr + (size_t)((R - d) % BAND_SLOTS) * NB * ZLD;
-#pragma unroll
-            for (int g = 0; g < NB / 4; ++g) {
-                float l[RPT][4];
-#pragma unroll
-                for (int a = 0; a < RPT; ++a) tma_load4(L, r0 + a, g, l[a]);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const float zv = Z[(4 * g + kk) * ZLD + c0];
-#pragma unroll
-                    for (int a = 0; a < RPT; ++a) acc[a] -= l[a][kk] * zv;
-                }
-            }
-        }
-        finish(acc, R, stile(st, 0), true);
-    }
-    cp_async_wait_n<0>();
-    __syncthreads();
-    // backward: x_R = T_R^T (D_R^{-1} z_R - sum_I L_IR^T x_I)
-    for (int k = 0; k < NST - 1; ++k) issue(k, K - 1 - k, false);
-    for (int R = K - 1, it = 0; R >= 0; --R, ++it) {
+    for (int q = 0; q < XD - 1; ++q) issue_load(q);
+    int q_next = XD - 1, q_use = 0;
+    for (int it = 0; it < total; ++it) {
         const int st = it % NST;
-        if (!wait_stage(st)) { abort_cta(); return; }
-        issue((it + NST - 1) % NST, R - (NST - 1), false);
-        float acc[RPT];
-        const double* xs = Sx + (size_t)st * NB * ZLD;
-        const float* dv = Sd + st * NB;
+        const bool fwd = it < K;
+        const int R = fwd ? it : total - 1 - it;
+        float acc[C];
+        // right-hand side of this step (own row)
+        if (fwd || (it - K) >= 3) {
+            issue_load(q_next++);
+            cp_async_wait_n<XD - 1>();
+            const double* xs = Xs + ((size_t)(q_use % XD) * NB + lane) * C;
 #pragma unroll
-        for (int a = 0; a < RPT; ++a) acc[a] = c0 < ncols ? dv[r0 + a] * f64_to_f32(xs[(r0 + a) * ZLD + c0]) : 0.f;
-        for (int d = 1; d <= kb; ++d) {
-            if (R + d >= K) break;
-            const float* L = stile(st, d);
-            const float* Z = Zr + (size_t)((R + d) % BAND_SLOTS) * NB * ZLD;
-#pragma unroll 8
-            for (int k = 0; k < NB; ++k) {
-                float l[RPT];
-                tma_loadn<RPT>(L, k, r0, l);
-                const float zv = Z[k * ZLD + c0];
-#pragma unroll
-                for (int a = 0; a < RPT; ++a) acc[a] -= l[a] * zv;
-            }
+            for (int c = 0; c < C; ++c) acc[c] = c < nc ? f64_to_f32(xs[c]) : 0.f;
+            ++q_use;
+        } else {
+            ws_ld<C>(Zr + ((size_t)(R % BAND_SLOTS) * NB + lane) * C, acc);
         }
-        finish(acc, R, stile(st, 0), false);
+        if (!mbar_wait_bounded(&full[st], (it / NST) & 1u)) { give_up(); break; }
+        if (nc > 0) {
+            if (!fwd) {
+                const float dr = Sd[st * NB + lane];
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] *= dr;
+            }
+            for (int d = 1; d <= kb; ++d) {
+                const int o = fwd ? R - d : R + d;
+                if (o < 0 || o >= K) continue;
+                const float* L = stile(st, d);
+                const float* Z = Zr + (size_t)(o % BAND_SLOTS) * NB * C;
+                if (fwd) {
+                    // acc -= L_{R,o}[lane][k] z_o[k]; nonzero only for k >= 32 d - b
+                    const int k0 = NB * d - bw;
+                    if (k0 >= 24) ws_row_product<C, 24, 32, -1>(L, Z, lane, acc);
+                    else if (k0 >= 16) ws_row_product<C, 16, 32, -1>(L, Z, lane, acc);
+                    else ws_row_product<C, 0, 32, -1>(L, Z, lane, acc);
+                } else {
+                    // acc -= L_{o,R}[k][lane] x_o[k]; nonzero only for k <= b - 32 d + 31
+                    const int kend = bw - NB * d + NB;
+                    if (kend <= 8) ws_col_product<C, 8, -1>(L, Z, lane, acc);
+                    else if (kend <= 16) ws_col_product<C, 16, -1>(L, Z, lane, acc);
+                    else ws_col_product<C, 32, -1>(L, Z, lane, acc);
+                }
+            }
+            ws_st<C>(Acc + lane * C, acc);
+            __syncwarp();
+            const float* T = stile(st, 0);
+            float out[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) out[c] = 0.f;
+            if (fwd) ws_row_product<C, 0, 32, 1>(T, Acc, lane, out);
+            else ws_col_product<C, 32, 1>(T, Acc, lane, out);
+            __syncwarp();                                   // Acc reads done before the next step's writes
+            ws_st<C>(Zr + ((size_t)(R % BAND_SLOTS) * NB + lane) * C, out);
+            double* xw = X + (roff + (long long)R * NB + lane) * ldx;
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                if (c < nc) xw[c] = f32_to_f64(out[c]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
     }
     cp_async_wait_n<0>();
 }
@@ -1564,10 +1611,11 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
     if (band_ok) {
         const CUtensorMap* tm = tile_tensor_map(tb);
         if (tm) {
-            const size_t b = band_tma_smem_bytes();
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_band_tma<BT_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-            k_tile_solve_band_tma<BT_NT><<<dim3(tb.P, (ncols + BT_ZLD - 1) / BT_ZLD), BT_NT, b, s>>>(
-                *tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
+            using Cfg = BandWs<4, 4, 6, 4>;
+            auto kern = k_tile_solve_band_ws<4, 4, 6, 4>;
+            MSDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes));
+            kern<<<dim3(tb.P, (ncols + Cfg::COLS - 1) / Cfg::COLS), Cfg::NT, Cfg::smem_bytes, s>>>(
+                *tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_b.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
             MSDD_LAUNCH_CHECK();
         } else if (tb.prec) {
             launch_band_cols<float>(tb, tb.tiles_f.p, tb.dinv_f.p, X, ldx, ncols, skip, s, gdone);
