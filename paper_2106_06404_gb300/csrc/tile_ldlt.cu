@@ -1150,30 +1150,37 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int W, int C, int NST, int XD>
+template <int KBP, int W, int C, int NST, int XD>
 struct BandWs {
+    static constexpr int SLOTS = KBP + 1;            // tiles per step; also the solution ring per warp
     static constexpr int NT = 32 * (W + 1);
     static constexpr int COLS = W * C;
-    static constexpr size_t stage_bytes = (size_t)BAND_SLOTS * NB2 * sizeof(float);
+    static constexpr size_t stage_bytes = (size_t)SLOTS * NB2 * sizeof(float);
     static constexpr size_t warp_bytes =
-        sizeof(float) * ((size_t)BAND_SLOTS * NB * C + (size_t)NB * C) + sizeof(double) * (size_t)XD * NB * C;
+        sizeof(float) * ((size_t)SLOTS * NB * C + (size_t)NB * C) + sizeof(double) * (size_t)XD * NB * C;
     static constexpr size_t smem_bytes =
         1024 + (size_t)NST * stage_bytes + (size_t)NST * NB * sizeof(float) + 16 * (size_t)NST + (size_t)W * warp_bytes;
 };
 
-template <int W, int C, int NST, int XD>
+// Half-bandwidth b at most KBP tiles (kb <= KBP); a step needs the diagonal
+// tile and kb off-diagonal tiles, and z_{R-1} .. z_{R-kb} (forward) or
+// x_{R+1} .. x_{R+kb} (backward) from the warp's ring of KBP + 1 solution
+// blocks.  When the backward sweep starts, the ring still holds z_R for the
+// last KBP + 1 rows, so only the rows before those are read back from X.
+template <int KBP, int W, int C, int NST, int XD>
 __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
     const __grid_constant__ CUtensorMap tmt, const float* __restrict__ dinv, const int* __restrict__ kb_,
     const int* __restrict__ K_, const int* __restrict__ b_, const long long* __restrict__ toff_,
     const long long* __restrict__ roff_, double* __restrict__ Xall, int ldx, int ncols_all,
     const int* __restrict__ skip, const int* __restrict__ gdone)
 {
-    using Cfg = BandWs<W, C, NST, XD>;
+    using Cfg = BandWs<KBP, W, C, NST, XD>;
+    constexpr int S = Cfg::SLOTS;
     static_assert(C == 1 || C == 2 || C == 4, "1, 2 or 4 columns per warp");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    float* St = reinterpret_cast<float*>(base);                                        // [NST][SLOTS][32*32]
-    float* Sd = St + (size_t)NST * BAND_SLOTS * NB2;                                   // [NST][32]
+    float* St = reinterpret_cast<float*>(base);                                        // [NST][S][32*32]
+    float* Sd = St + (size_t)NST * S * NB2;                                            // [NST][32]
     unsigned long long* full = reinterpret_cast<unsigned long long*>(Sd + (size_t)NST * NB);
     unsigned long long* empty = full + NST;
     unsigned char* wbase = reinterpret_cast<unsigned char*>(empty + NST);
@@ -1183,6 +1190,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
     if (skip && skip[i]) return;
     if (gdone && *gdone) return;
     const int kb = kb_[i], K = K_[i], bw = b_[i];
+    if (kb > KBP) return;                            // never launched so (host dispatch)
     const long long toff = toff_[i], roff = roff_[i];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (t == 0) {
@@ -1194,7 +1202,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
         fence_mbar_init();
     }
     __syncthreads();
-    auto stile = [&](int st, int slot) { return St + (size_t)(st * BAND_SLOTS + slot) * NB2; };
+    auto stile = [&](int st, int slot) { return St + (size_t)(st * S + slot) * NB2; };
     auto give_up = [&]() {
         if (atomicExch(&s_abort, 1) == 0) atomicAdd(&g_wait_timeouts, 1);
     };
@@ -1241,22 +1249,20 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
     // ---------------- consumer warp: columns [c_lo, c_lo + nc)
     const int c_lo = blockIdx.y * Cfg::COLS + warp * C;
     const int nc = max(0, min(C, ncols_all - c_lo));
-    float* Zr = reinterpret_cast<float*>(wbase + (size_t)warp * Cfg::warp_bytes);     // [SLOTS][32][C]
-    float* Acc = Zr + (size_t)BAND_SLOTS * NB * C;                                      // [32][C]
+    float* Zr = reinterpret_cast<float*>(wbase + (size_t)warp * Cfg::warp_bytes);     // [S][32][C]
+    float* Acc = Zr + (size_t)S * NB * C;                                               // [32][C]
     double* Xs = reinterpret_cast<double*>(Acc + (size_t)NB * C);                      // [XD][32][C]
     double* X = Xall + c_lo;
     // loads of this lane's row: index q < K: forward step q (row q); q >= K:
-    // backward row K - 4 - (q - K) (backward steps s >= 3; rows K-1..K-3 are
-    // still in the Zr ring when the backward sweep starts)
-    const int nload = K + max(0, K - 3);
+    // backward row K - 1 - S - (q - K) (backward steps s >= S)
+    const int nload = K + max(0, K - S);
     auto issue_load = [&](int q) {
         if (q < nload && nc > 0) {
             if (q >= K) __threadfence_block();       // rows written by this lane in the forward sweep
-            const int R = q < K ? q : K - 4 - (q - K);
+            const int R = q < K ? q : K - 1 - S - (q - K);
             const double* src = X + (roff + (long long)R * NB + lane) * ldx;
             double* dst = Xs + ((size_t)(q % XD) * NB + lane) * C;
             if constexpr (C == 1) {
-                // one double: an 8-byte copy
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
             } else {
                 cp_async16(dst, src);
@@ -1273,7 +1279,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
         const int R = fwd ? it : total - 1 - it;
         float acc[C];
         // right-hand side of this step (own row)
-        if (fwd || (it - K) >= 3) {
+        if (fwd || (it - K) >= S) {
             issue_load(q_next++);
             cp_async_wait_n<XD - 1>();
             const double* xs = Xs + ((size_t)(q_use % XD) * NB + lane) * C;
@@ -1281,7 +1287,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
             for (int c = 0; c < C; ++c) acc[c] = c < nc ? f64_to_f32(xs[c]) : 0.f;
             ++q_use;
         } else {
-            ws_ld<C>(Zr + ((size_t)(R % BAND_SLOTS) * NB + lane) * C, acc);
+            ws_ld<C>(Zr + ((size_t)(R % S) * NB + lane) * C, acc);
         }
         if (!mbar_wait_bounded(&full[st], (it / NST) & 1u)) { give_up(); break; }
         if (nc > 0) {
@@ -1294,7 +1300,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
                 const int o = fwd ? R - d : R + d;
                 if (o < 0 || o >= K) continue;
                 const float* L = stile(st, d);
-                const float* Z = Zr + (size_t)(o % BAND_SLOTS) * NB * C;
+                const float* Z = Zr + (size_t)(o % S) * NB * C;
                 if (fwd) {
                     // acc -= L_{R,o}[lane][k] z_o[k]; nonzero only for k >= 32 d - b
                     const int k0 = NB * d - bw;
@@ -1318,7 +1324,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
             if (fwd) ws_row_product<C, 0, 32, 1>(T, Acc, lane, out);
             else ws_col_product<C, 32, 1>(T, Acc, lane, out);
             __syncwarp();                                   // Acc reads done before the next step's writes
-            ws_st<C>(Zr + ((size_t)(R % BAND_SLOTS) * NB + lane) * C, out);
+            ws_st<C>(Zr + ((size_t)(R % S) * NB + lane) * C, out);
             double* xw = X + (roff + (long long)R * NB + lane) * ldx;
 #pragma unroll
             for (int c = 0; c < C; ++c)
@@ -1328,6 +1334,19 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
         if (lane == 0) mbar_arrive(&empty[st]);
     }
     cp_async_wait_n<0>();
+}
+
+// Launch of k_tile_solve_band_ws for one configuration.
+template <int KBP, int W, int C, int NST, int XD>
+void launch_band_ws(const TileBatch& tb, const CUtensorMap& tm, double* X, int ldx, int ncols, const int* skip,
+                    cudaStream_t s, const int* gdone) {
+    using Cfg = BandWs<KBP, W, C, NST, XD>;
+    static_assert(Cfg::smem_bytes <= 227 * 1024, "shared memory per CTA");
+    auto kern = k_tile_solve_band_ws<KBP, W, C, NST, XD>;
+    MSDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes));
+    kern<<<dim3(tb.P, (ncols + Cfg::COLS - 1) / Cfg::COLS), Cfg::NT, Cfg::smem_bytes, s>>>(
+        tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_b.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
+    MSDD_LAUNCH_CHECK();
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1593,6 +1612,15 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
             MSDD_LAUNCH_CHECK();
             return;
         }
+        if (tb.prec && maxkb > 2 && maxkb <= 12) {
+            // wide bands, one right-hand side (PCG local solves of 3D boxes):
+            // one consumer warp, two stages of 13 tiles, 8-byte copies of X
+            const CUtensorMap* tm = tile_tensor_map(tb);
+            if (tm) {
+                launch_band_ws<12, 1, 1, 2, 4>(tb, *tm, X, 1, 1, nullptr, s, gdone);
+                return;
+            }
+        }
         if (maxkb > 2 && zbytes <= 160 * 1024) {
             if (zbytes > 48 * 1024) {
                 MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
@@ -1606,22 +1634,21 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
     }
     int maxkb = 0;
     for (int v : tb.kb) maxkb = std::max(maxkb, v);
-    // the band kernel stages blocks of X with 16-byte copies
-    const bool band_ok = maxkb <= 2 && ncols <= NB && ldx % 2 == 0 && ((uintptr_t)X % 16) == 0;
-    if (band_ok) {
-        const CUtensorMap* tm = tile_tensor_map(tb);
-        if (tm) {
-            using Cfg = BandWs<4, 4, 6, 4>;
-            auto kern = k_tile_solve_band_ws<4, 4, 6, 4>;
-            MSDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes));
-            kern<<<dim3(tb.P, (ncols + Cfg::COLS - 1) / Cfg::COLS), Cfg::NT, Cfg::smem_bytes, s>>>(
-                *tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_b.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
-            MSDD_LAUNCH_CHECK();
-        } else if (tb.prec) {
-            launch_band_cols<float>(tb, tb.tiles_f.p, tb.dinv_f.p, X, ldx, ncols, skip, s, gdone);
-        } else {
-            launch_band_cols<double>(tb, tb.tiles_d.p, tb.dinv_d.p, X, ldx, ncols, skip, s, gdone);
-        }
+    // the band kernels stage blocks of X with 16-byte copies
+    const bool aligned = ldx % 2 == 0 && ((uintptr_t)X % 16) == 0;
+    const CUtensorMap* tm = tb.prec && aligned && ncols <= NB ? tile_tensor_map(tb) : nullptr;
+    if (tm && maxkb <= 2) {
+        launch_band_ws<2, 4, 4, 6, 4>(tb, *tm, X, ldx, ncols, skip, s, gdone);
+        return;
+    }
+    if (tm && maxkb <= 12) {
+        // wide bands (3D boxes): 20 columns per CTA in 5 warps, 3 stages of 13 tiles
+        launch_band_ws<12, 5, 4, 3, 4>(tb, *tm, X, ldx, ncols, skip, s, gdone);
+        return;
+    }
+    if (maxkb <= 2 && ncols <= NB && aligned) {
+        if (tb.prec) launch_band_cols<float>(tb, tb.tiles_f.p, tb.dinv_f.p, X, ldx, ncols, skip, s, gdone);
+        else launch_band_cols<double>(tb, tb.tiles_d.p, tb.dinv_d.p, X, ldx, ncols, skip, s, gdone);
         return;
     }
     const dim3 grid(tb.P, (ncols + NB - 1) / NB);
