@@ -1068,6 +1068,391 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
+// ---- FP32 band LDL^T with the panel updates on the tensor cores (3 <= kb <= 12)
+// Left-looking by tile column C, one CTA (one warpgroup) per matrix.  The
+// update of column C,
+//   U_R = sum_{J} L_RJ D_J L_CJ^T,  R = C .. min(C + kb, K - 1),
+//   J = max(C - kb, R - kb) .. C - 1,
+// is a product D = A B^T with A = [L_RJ] (tile rows R stacked, 128-row
+// blocks of four tile rows, tiles outside the band zero) and
+// B = [L_CJ D_J] (32 x 32 per J), done by tcgen05.mma kind::tf32 into a
+// TMEM accumulator (four 128 x 32 FP32 blocks).  FP32 accuracy from TF32
+// operands by the three-product split x = hi + lo, hi = x with the low 13
+// mantissa bits cleared: A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo * lo
+// term is below FP32 rounding).  The tensor cores of this GPU take a
+// kind::tf32 operand as its top 19 bits (truncation, measured), so the FP32
+// L tiles themselves serve as hi parts, and lo = x - hi of each L tile is
+// written once, when the tile is computed, to a scratch array.  The A
+// operands (hi from the tiles, lo from the scratch) are streamed by TMA
+// (3-stage ring, one pair (block, J) per stage, tiles outside the band read
+// as zeros from out-of-range coordinates); the B operands are scaled by D_J
+// and split in shared memory.  Then, as in
+// k_tile_factor: W_RC = A_RC - U_R, the diagonal tile is factored and
+// inverted by warp 0 in registers (null pivots as there), and
+// L_RC = W_RC T_C^T D_C^{-1}.  Operands are K-major with the 128-byte
+// swizzle (row r of a tile at 128 r bytes, 16-byte chunk g at g ^ (r & 7)),
+// descriptors: start >> 4, stride between 8-row groups 1024 B, the K step
+// of 8 elements advances the start by 32 B.
+constexpr int TF_NT = 128, TF_KBM = 12, TF_NS = 3;
+constexpr int TF_MAXPAIRS = TF_KBM * ((TF_KBM + 1 + 3) / 4);
+constexpr size_t tf_smem_bytes() {
+    return 1024 + (size_t)TF_NS * 8 * NB2 * 4            // A stages: 4 hi + 4 lo tiles
+           + (size_t)TF_KBM * 2 * NB2 * 4                // B_J hi and lo
+           + (size_t)NB2 * 4 + NB * 4                    // T_C, D_C^{-1}
+           + (size_t)TF_KBM * NB * 4                     // D_J of the B operands
+           + 64 * (TF_NS * 2 + 3) + TF_MAXPAIRS * 4 + 64;
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+__device__ __forceinline__ uint64_t umma_desc_sw128(unsigned saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                             // leading byte offset (unused: K-major, 128 B rows)
+    d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                             // descriptor version
+    d |= (uint64_t)2 << 61;                             // 128-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void umma_tf32(unsigned tmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+
+// lo: E floats (E = total tile elements), lo parts of the L tiles in the tile layout;
+// tm_hi / tm_lo: [E / 32][32] tensor maps of the tiles and of lo
+__global__ void __launch_bounds__(TF_NT) k_tile_factor_tc(
+    const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, float* __restrict__ tiles,
+    float* __restrict__ lo, long long total_elems, float* __restrict__ dinv, const int* __restrict__ n_, const int* __restrict__ kb_,
+    const int* __restrict__ K_, const long long* __restrict__ toff_, const long long* __restrict__ roff_,
+    int* __restrict__ status, int* __restrict__ nreg, double reg_tol)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    float* Ast = reinterpret_cast<float*>(base);                                   // [NS][8][1024]
+    float* Bst = Ast + (size_t)TF_NS * 8 * NB2;                                     // [KBM][2][1024]
+    float* Tc = Bst + (size_t)TF_KBM * 2 * NB2;                                     // [32][32]
+    float* Dc = Tc + NB2;                                                           // [32]
+    float* Dj = Dc + NB;                                                            // [KBM][32]
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(Dj + TF_KBM * NB);  // full[NS], empty[NS], acc, b
+    unsigned long long* full = bars;
+    unsigned long long* empty = bars + TF_NS;
+    unsigned long long* accb = bars + 2 * TF_NS;
+    unsigned long long* bfull = bars + 2 * TF_NS + 1;
+    int* pairs = reinterpret_cast<int*>(bars + 2 * TF_NS + 3);                     // (J << 8) | mb
+    __shared__ unsigned s_tmem;
+    __shared__ int s_status, s_nreg, s_abort, s_npairs, s_used;
+
+    const int i = blockIdx.x;
+    const int n = n_[i], kb = kb_[i], K = K_[i];
+    const long long toff = toff_[i], roff = roff_[i];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (kb > TF_KBM) {                                  // never launched so (host dispatch)
+        if (t == 0) status[i] = -1;
+        return;
+    }
+    const int oob_row = (int)(total_elems / NB);        // first row beyond both tensors: zero fill
+    if (t == 0) {
+        s_status = 0; s_nreg = 0; s_abort = 0;
+        for (int s = 0; s < TF_NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(accb, 1);
+        mbar_init(bfull, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(&s_tmem)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = s_tmem;
+    // D f32, A and B tf32, both K-major, N = 32, M = 128
+    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    // parity bits: ph_full (product thread), ph_empty and par_issued (copy
+    // thread), ph_acc (all threads); pair_base counts the ring's pairs so far
+    unsigned ph_full = 0, ph_empty = 0, ph_acc = 0, par_issued = 0, ph_b = 0;
+    int pair_base = 0;
+
+    auto issue_pair = [&](int C, int Rend, int pr, int stage) {
+        // A operand tiles of pair (J, mb): hi into slots 0..3, lo into 4..7
+        const int J = pr >> 8, mb = pr & 0xff;
+        float* dst = Ast + (size_t)stage * 8 * NB2;
+        mbar_expect_tx(&full[stage], 8 * NB2 * 4);
+        for (int q = 0; q < 4; ++q) {
+            const int R = C + 4 * mb + q;
+            const bool valid = R <= Rend && R - J <= kb;
+            const long long ti = valid ? tile_index(toff, kb, R, J) : 0;
+            const int row = valid ? (int)(ti / NB) : oob_row;
+            tma_load_tile(dst + (size_t)q * NB2, &tm_hi, row, &full[stage]);
+            tma_load_tile(dst + (size_t)(4 + q) * NB2, &tm_lo, row, &full[stage]);
+        }
+    };
+
+    for (int C = 0; C < K && !s_abort; ++C) {
+        const int Rend = min(C + kb, K - 1);
+        const int J0 = max(0, C - kb);
+        const int nJ = C - J0;
+        const int nmb = (Rend - C + 1 + 3) / 4;
+        // ---- pair list and B operands: B_J[n][j] = L_CJ[n][j] * D_J[j], split
+        if (t == 0) {
+            int np = 0, used = 0;
+            for (int J = J0; J < C; ++J)
+                for (int mb = 0; mb < nmb; ++mb) {
+                    const int R0 = C + 4 * mb;
+                    if (R0 <= Rend && R0 - J <= kb) {       // the block's first row has the most J's
+                        pairs[np++] = (J << 8) | mb;
+                        used |= 1 << mb;
+                    }
+                }
+            s_npairs = np;
+            s_used = used;
+        }
+        // raw tiles L_CJ by TMA into the lo slots, D_J into shared memory
+        if (t == 32 && nJ > 0) {
+            mbar_expect_tx(bfull, nJ * NB2 * 4);
+            for (int jj = 0; jj < nJ; ++jj)
+                tma_load_tile(Bst + (size_t)(2 * jj + 1) * NB2, &tm_hi,
+                              (int)(tile_index(toff, kb, C, J0 + jj) / NB), bfull);
+        }
+        for (int e = t; e < nJ * NB; e += TF_NT) {
+            const float di = dinv[roff + (long long)J0 * NB + e];
+            Dj[e] = di != 0.f ? 1.f / di : 0.f;
+        }
+        __syncthreads();
+        if (nJ > 0) {
+            if (!mbar_wait_bounded(bfull, ph_b & 1u)) {
+                if (atomicExch(&s_abort, 1) == 0) atomicAdd(&g_wait_timeouts, 1);
+            } else {
+                ph_b ^= 1u;
+            }
+        }
+        for (int e = t; e < nJ * NB2; e += TF_NT) {
+            // element (r, c) of tile jj; the same swizzled position in both slots
+            const int jj = e / NB2, w = e % NB2, r = w / NB, c = w % NB;
+            const int sidx = r * NB + ((((c >> 2) ^ (r & 7))) << 2) + (c & 3);
+            float* lo_slot = Bst + (size_t)(2 * jj + 1) * NB2;
+            const float b = lo_slot[sidx] * Dj[jj * NB + c];
+            const float hi = tf32_hi(b);
+            Bst[(size_t)(2 * jj) * NB2 + sidx] = hi;
+            lo_slot[sidx] = b - hi;
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int np = s_npairs, used = s_used;
+        // ---- tensor-core update: lane 0 of warp 1 streams the A operands into the
+        // ring, lane 0 of warp 0 issues the products (each side waits only for
+        // the other: "full" when a stage's copies landed, "empty" when the
+        // products that read a stage are done)
+        if (t == 32 && np > 0) {
+            for (int p = 0; p < np; ++p) {
+                const int g = pair_base + p, st = g % TF_NS;
+                if (g >= TF_NS) {
+                    if (!mbar_wait_bounded(&empty[st], (ph_empty >> st) & 1u)) {
+                        if (atomicExch(&s_abort, 1) == 0) atomicAdd(&g_wait_timeouts, 1);
+                        break;
+                    }
+                    ph_empty ^= 1u << st;
+                }
+                if (*(volatile int*)&s_abort) break;
+                issue_pair(C, Rend, pairs[p], st);
+                par_issued = (par_issued & ~(1u << st)) | ((unsigned)((g / TF_NS) & 1) << st);
+            }
+        }
+        if (t == 0 && np > 0) {
+            unsigned started = 0;                       // M-blocks whose accumulator has been started
+            for (int p = 0; p < np; ++p) {
+                const int g = pair_base + p, st = g % TF_NS;
+                if (!mbar_wait_bounded(&full[st], (ph_full >> st) & 1u)) {
+                    if (atomicExch(&s_abort, 1) == 0) atomicAdd(&g_wait_timeouts, 1);
+                    break;
+                }
+                ph_full ^= 1u << st;
+                tc_fence_after();
+                const int J = pairs[p] >> 8, mb = pairs[p] & 0xff, jj = J - J0;
+                const unsigned a_hi = smem_u32(Ast + (size_t)st * 8 * NB2), a_lo = a_hi + 4 * NB2 * 4;
+                const unsigned b_hi = smem_u32(Bst + (size_t)(2 * jj) * NB2), b_lo = b_hi + NB2 * 4;
+                const unsigned d = tmem + 32u * mb;
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned ko = 32u * k;
+                    const unsigned acc = (started >> mb) & 1u;
+                    umma_tf32(d, umma_desc_sw128(a_hi + ko), umma_desc_sw128(b_hi + ko), idesc, acc);
+                    started |= 1u << mb;
+                    umma_tf32(d, umma_desc_sw128(a_hi + ko), umma_desc_sw128(b_lo + ko), idesc, 1u);
+                    umma_tf32(d, umma_desc_sw128(a_lo + ko), umma_desc_sw128(b_hi + ko), idesc, 1u);
+                }
+                umma_commit(&empty[st]);                // the stage is free once these products are done
+            }
+            umma_commit(accb);
+        }
+        pair_base += np;
+        __syncthreads();
+        if (s_abort) break;
+        // ---- W_RC = A_RC - U_R for the rows of this thread: tile row C + 4 mb + warp, row lane
+        if (np > 0) {
+            if (!mbar_wait_bounded(accb, ph_acc & 1u)) {
+                if (atomicExch(&s_abort, 1) == 0) atomicAdd(&g_wait_timeouts, 1);
+            } else {
+                ph_acc ^= 1u;                           // (on a timeout the phase stays pending)
+            }
+        }
+        tc_fence_after();
+        __syncthreads();
+        if (s_abort) break;
+        float w[4][NB];
+#pragma unroll
+        for (int mb = 0; mb < 4; ++mb) {
+            const int R = C + 4 * mb + warp;
+            if (mb < nmb && ((used >> mb) & 1)) {
+                float u[NB];
+                tmem_ld32(tmem + ((unsigned)(32 * warp) << 16) + 32u * mb, u);
+                if (R <= Rend) {
+                    const float* a = tiles + tile_index(toff, kb, R, C) + lane * NB;
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) w[mb][c] = a[c] - u[c];
+                }
+            } else if (mb < nmb && R <= Rend) {
+                const float* a = tiles + tile_index(toff, kb, R, C) + lane * NB;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) w[mb][c] = a[c];
+            }
+        }
+        tc_fence_before();
+        // ---- diagonal tile (warp 0, mb 0: R = C): L D L^T in registers, T_C = L_CC^{-1}
+        if (warp == 0) {
+            const int rows_valid = n - C * NB;
+            // original diagonal entry of this row (null-pivot reference)
+            const float od_l = tiles[tile_index(toff, kb, C, C) + lane * NB + lane];
+            float row[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) row[b] = w[0][b];
+            float dl = 0.f;
+            int nr = 0, stc = 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const float d = __shfl_sync(0xffffffffu, row[k], k);
+                const float odk = __shfl_sync(0xffffffffu, od_l, k);
+                float dinv_k;
+                if (k >= rows_valid) {
+                    dinv_k = 1.f;
+                } else if (reg_tol > 0.0 && !(d > (float)reg_tol * odk)) {
+                    dinv_k = 0.f;
+                    ++nr;
+                } else if (!(d > 0.f)) {
+                    dinv_k = 0.f;
+                    if (stc == 0) stc = C * NB + k + 1;
+                } else {
+                    dinv_k = 1.f / d;
+                }
+                if (lane == k) dl = dinv_k;
+                const float wak = row[k];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    if (b > k) {
+                        const float wbk = __shfl_sync(0xffffffffu, wak, b);
+                        if (lane >= b) row[b] -= wak * wbk * dinv_k;
+                    }
+                }
+                if (lane > k) row[k] = (k >= rows_valid || lane >= rows_valid) ? 0.f : wak * dinv_k;
+            }
+            float tr[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) tr[b] = (b == lane) ? 1.f : 0.f;
+#pragma unroll
+            for (int k = 0; k < NB - 1; ++k) {
+                const float lak = row[k];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    if (b <= k) {
+                        const float tkb = __shfl_sync(0xffffffffu, tr[b], k);
+                        if (lane > k) tr[b] -= lak * tkb;
+                    }
+                }
+            }
+            float* dst = tiles + tile_index(toff, kb, C, C) + lane * NB;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                Tc[lane * NB + b] = tr[b];
+                dst[b] = tr[b];
+            }
+            Dc[lane] = dl;
+            dinv[roff + (long long)C * NB + lane] = dl;
+            if (lane == 0) {
+                s_nreg += nr;
+                if (s_status == 0 && stc != 0) s_status = stc;
+            }
+        }
+        __syncthreads();
+        // ---- panel: L_RC = W_RC T_C^T D_C^{-1}, stored with its hi / lo parts for later columns
+#pragma unroll
+        for (int mb = 0; mb < 4; ++mb) {
+            const int R = C + 4 * mb + warp;
+            if (mb >= nmb || R <= C || R > Rend) continue;
+            float out[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) {
+                float s = 0.f;
+#pragma unroll
+                for (int g = 0; g < NB / 4; ++g) {
+                    const float4 tv = *reinterpret_cast<const float4*>(Tc + c * NB + 4 * g);
+                    s += w[mb][4 * g] * tv.x;
+                    s += w[mb][4 * g + 1] * tv.y;
+                    s += w[mb][4 * g + 2] * tv.z;
+                    s += w[mb][4 * g + 3] * tv.w;
+                }
+                out[c] = s * Dc[c];
+            }
+            const long long ti = tile_index(toff, kb, R, C) + lane * NB;
+#pragma unroll
+            for (int c = 0; c < NB; ++c) {
+                tiles[ti + c] = out[c];
+                lo[ti + c] = out[c] - tf32_hi(out[c]);
+            }
+        }
+        fence_proxy_async_global();                     // the next columns read these by TMA
+        __syncthreads();
+    }
+    // ---- end: wait (bounded) for copies and products still in flight, free TMEM
+    if (s_abort) {
+        // copies still in flight land, and the products issued complete, before the CTA exits
+        if (t == 32)
+            for (int s = 0; s < TF_NS && s < pair_base; ++s) mbar_wait_bounded(&full[s], (par_issued >> s) & 1u);
+        if (t == 0) mbar_wait_bounded(accb, ph_acc & 1u);  // a column's products, if their wait gave up
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
+    if (t == 0) { status[i] = s_status; nreg[i] = s_nreg; }
+}
+
 // ---- the FP32 band solve with TMA tile loads, warp-specialised (kb <= 2)
 // The steps and expressions of k_tile_solve_band<float> (forward z_R = T_R
 // (x_R - sum_J L_RJ z_J), backward x_R = T_R^T (D_R^{-1} z_R - sum_I L_IR^T
@@ -1365,21 +1750,25 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
+// [elems / 32][32] FP32 view of a tile array, 32 x 32 boxes, 128-byte swizzle.
+bool encode_tile_map(const float* base, long long elems, CUtensorMap* m) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || !base || elems <= 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)NB, (cuuint64_t)(elems / NB)};
+    const cuuint64_t strides[1] = {(cuuint64_t)NB * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)NB, (cuuint32_t)NB};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The tile descriptor of an FP32 batch (built once per tiles_f allocation).
 const CUtensorMap* tile_tensor_map(const TileBatch& tb) {
     if (!tb.prec || !tb.tiles_f.p || tb.total_tile_elems <= 0) return nullptr;
     if (tb.tmap_base == tb.tiles_f.p) return reinterpret_cast<const CUtensorMap*>(tb.tmap_tiles);
-    EncodeTiledFn enc = encode_tiled();
-    if (!enc) return nullptr;
-    const cuuint64_t dims[2] = {(cuuint64_t)NB, (cuuint64_t)(tb.total_tile_elems / NB)};
-    const cuuint64_t strides[1] = {(cuuint64_t)NB * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)NB, (cuuint32_t)NB};
-    const cuuint32_t estr[2] = {1, 1};
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(tb.tmap_tiles);
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)tb.tiles_f.p, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return nullptr;
+    if (!encode_tile_map(tb.tiles_f.p, tb.total_tile_elems, m)) return nullptr;
     tb.tmap_base = tb.tiles_f.p;
     return m;
 }
@@ -1568,6 +1957,21 @@ void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
                                                   tb.d_toff.p, tb.d_roff.p, tb.d_status.p, tb.d_nreg.p, reg_tol);
         MSDD_LAUNCH_CHECK();
         return;
+    }
+    if (tb.prec && maxkb <= TF_KBM) {
+        // 3 <= kb <= 12: panel updates on the tensor cores (lo parts of the factor in scratch)
+        const CUtensorMap* thi = tile_tensor_map(tb);
+        DevBuf<float> lo(tb.total_tile_elems);
+        alignas(64) CUtensorMap tlo;
+        if (thi && encode_tile_map(lo.p, tb.total_tile_elems, &tlo)) {
+            const size_t b = tf_smem_bytes();
+            MSDD_CUDA(cudaFuncSetAttribute(k_tile_factor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            k_tile_factor_tc<<<tb.P, TF_NT, b, s>>>(*thi, tlo, tb.tiles_f.p, lo.p, tb.total_tile_elems, tb.dinv_f.p,
+                                                   tb.d_n.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p,
+                                                   tb.d_status.p, tb.d_nreg.p, reg_tol);
+            MSDD_LAUNCH_CHECK();
+            return;
+        }
     }
     if (tb.prec)
         k_tile_factor<float><<<tb.P, TPB, 0, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,

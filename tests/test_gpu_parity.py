@@ -68,11 +68,15 @@ def _eig_close(theta, lam, eta, m):
 
 # ---------------------------------------------------------------- band solver
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
-@pytest.mark.parametrize("nrhs", [1, 5])
-def test_band_solver_matches_oracle(precision, tol, nrhs):
+@pytest.mark.parametrize("nrhs", [1, 5, 20])
+@pytest.mark.parametrize("bw", [40, 150, 381])
+def test_band_solver_matches_oracle(precision, tol, nrhs, bw):
+    """Half-bandwidths of 2, 5 and 12 tiles: the band kernels of the 2D boxes,
+    and for the wide bands of 3D boxes the tensor-core factorisation (FP32)
+    with the wide warp-specialised solves."""
     rng = np.random.default_rng(7)
-    sizes = [1, 31, 32, 33, 100, 157]            # ragged tails and several tiles
-    nmax, bw = max(sizes), 40
+    sizes = [1, 31, 32, 33, 100, 157] + ([450, 700] if bw > 40 else [])   # ragged tails, several tiles
+    nmax = max(sizes)
     A = np.zeros((len(sizes), nmax, nmax))
     for i, n in enumerate(sizes):
         M = rng.standard_normal((n, n))
