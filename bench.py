@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["grf512", "channels64", "composite128"], default="grf512")
+    ap.add_argument("--workload", choices=["grf512", "channels64", "composite128", "composite96", "batch256"],
+                    default="grf512")
+    ap.add_argument("--batch-count", type=int, default=256, help="batch256: number of problems")
     ap.add_argument("--oracle-sample", type=int, default=16,
                     help="3D workload: fine subdomains in the CPU oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true",
@@ -118,7 +120,8 @@ def solver_leg(H, b, steps, warmup, sync):
 
 def workload(name, seed):
     import synthetic_inputs as si
-    return {"grf512": si.grf512, "channels64": si.channels64, "composite128": si.composite128}[name](seed=seed)
+    return {"grf512": si.grf512, "channels64": si.channels64, "composite128": si.composite128,
+            "composite96": si.composite96}[name](seed=seed)
 
 
 def full_oracle_step(wname):
@@ -126,7 +129,7 @@ def full_oracle_step(wname):
     host (512 band factorisations of order 6859, half-bandwidth 381, with
     their subspace iterations: minutes on 16 cores); it gets a bounded
     sample instead."""
-    return wname != "composite128"
+    return wname not in ("composite128", "composite96")
 
 
 # ------------------------------------------------------------------ CPU oracle step
@@ -599,6 +602,70 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batch of problems
+def run_batch(args):
+    """The multi-problem workload: the batch256 recipe (256 independent 2D
+    problems of uneven size) set up and solved with msdd_batch_run; a step is
+    the whole batch.  The worker count is picked by a timing sweep on the
+    first 32 problems (the batch's own tuner)."""
+    import numpy as np
+    import torch
+    import synthetic_inputs as si
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2106_06404_gb300 as pkg
+    ws = si.batch256(count=args.batch_count)
+    probs = []
+    for w in ws:
+        probs.append(dict(n=w.n, kappa=torch.tensor(w.coefficient(), device="cuda"), parts=w.parts,
+                          overlap=w.overlap, levels=w.levels, group=w.group, b=pkg.assemble_rhs(w.n)))
+    torch.cuda.synchronize()
+
+    def run(sub, precision, nworkers):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = pkg.batch_run(sub, ws[0].nev_max, ws[0].eta, tol=TOL, precision=precision, nworkers=nworkers)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    tune = {}
+    for nw in (4, 8, 16, 32):
+        run(probs[:32], 1, nw)
+        tune[nw] = run(probs[:32], 1, nw)[0]
+    best = min(tune, key=tune.get)
+    res = {}
+    for prec in (1, 0):
+        for _ in range(args.warmup):
+            run(probs, prec, best)
+        times, out = [], None
+        for _ in range(args.steps):
+            t, out = run(probs, prec, best)
+            times.append(t)
+        res[prec] = (times, out)
+    t1, (xs, it, rel, st, sms, pms) = res[1]
+    t0 = res[0][0]
+    n_unknowns = int(sum(x.numel() for x in xs))
+    line = {
+        "metric": METRIC, "value": round(statistics.mean(t1), 6), "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t1), 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 fine factors",
+        "data": "synthetic (batch recipe: seeded sides 128-384, 4x4-12x12 subdomains, log-normal x channels 1e4-1e6)",
+        "config": {"workload": "batch2d_%dproblems" % len(ws), "problems": len(ws), "unknowns": n_unknowns,
+                   "levels": 2, "nev_max": ws[0].nev_max, "eta": ws[0].eta, "tol": TOL, "form": "chosen (precision=1)",
+                   "parallelism": "single GPU, %d host workers" % best},
+        "step_seconds": [round(t, 6) for t in t1],
+        "plain_fp64": {"value": round(statistics.mean(t0), 6), "unit": "s"},
+        "speedup_chosen_vs_plain": round(statistics.mean(t0) / statistics.mean(t1), 3),
+        "workers_sweep_s": {str(k): round(v, 4) for k, v in tune.items()},
+        "iterations": {"min": int(it.min()), "max": int(it.max()), "mean": round(float(it.mean()), 2)},
+        "statuses_ok": int(np.sum(st == 0)),
+        "sum_setup_ms": round(float(sms.sum()), 1), "sum_solve_ms": round(float(pms.sum()), 1),
+        "note": "value = wall seconds for set-up and PCG of every problem of the batch (inputs resident in HBM); "
+                "sum_* are the per-problem times, which overlap on the GPU",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -606,6 +673,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.oracle_leg is not None:
         oracle_leg(args)
+    elif args.workload == "batch256" and args.impl == "ours":
+        if rank == 0:
+            run_batch(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -65,8 +65,8 @@ typedef struct msdd_coeff {
     int kind;            /* 0: scalar, one double per element;
                             1: tensor, per element (kxx, kyy, kxy) in 2D or
                                (kxx, kyy, kzz, kyz, kxz, kxy) in 3D */
-    const double* data;  /* device, element-major; read during msdd_setup and
-                            by every solve (must stay valid while the hierarchy lives) */
+    const double* data;  /* device, element-major, caller-owned; read during
+                            msdd_setup only (the hierarchy keeps its own copy) */
 } msdd_coeff;
 
 /* Hierarchical box decomposition (Section 2.2).  The fine level splits the
@@ -286,7 +286,8 @@ void msdd_destroy(msdd_hierarchy* h);
  * cudaFree each: a buffer released inside a call (or by msdd_destroy /
  * msdd_band_destroy) is parked, and at the end of that call the device is
  * synchronised once and parked blocks become reusable by later allocations
- * of the same rounded size (512 bytes).  A sequence of set-ups of the same
+ * of the same size class (multiples of 512 bytes up to 1 MiB, above that
+ * four classes per octave, at most 25% slack).  A sequence of set-ups of the same
  * size thus allocates nothing after the first, and no block is reused while
  * a kernel launched before its release can still read it.  The cache keeps
  * its memory until msdd_release_cache, which synchronises the device and
@@ -297,7 +298,9 @@ msdd_status msdd_release_cache(void);
 long long msdd_cached_bytes(void);
 
 /* Number of CUDA kernels this library has launched in the process so far
- * (a replayed CUDA graph counts the kernels it holds).  Not thread-safe. */
+ * (a replayed CUDA graph counts the kernels it holds): the kernels launched
+ * from the calling thread plus those of the worker threads of finished
+ * msdd_batch_run calls. */
 long long msdd_kernel_launches(void);
 
 /* Message of the last failure on the calling thread ("" if none; most entry
@@ -379,6 +382,42 @@ msdd_status msdd_band_solve_noalloc(const msdd_band_batch* bb, int nrhs, double*
 #define MSDD_NN_OUT (MSDD_NN_NVEC * MSDD_NN_GRID * MSDD_NN_GRID)
 #define MSDD_NN_NPARAM (MSDD_NN_HIDDEN * MSDD_NN_IN + MSDD_NN_HIDDEN + MSDD_NN_HIDDEN * MSDD_NN_HIDDEN + \
                         MSDD_NN_HIDDEN + MSDD_NN_OUT * MSDD_NN_HIDDEN + MSDD_NN_OUT)
+
+/* ---- batches of independent problems: set-up and solve ---------------------
+ * msdd_batch_run sets up the hierarchy of each of nprob independent problems
+ * and solves A_p x_p = b_p with PCG to tol (as msdd_setup and msdd_solve),
+ * on one GPU.  The paper solves one problem at a time; Section 5 reports the
+ * wide spread of per-subdomain costs that a work queue evens out.  A host work
+ * queue hands the problems, largest first (sum of n (b + 1) over the fine
+ * subdomains), to nworkers worker threads, each with its own non-blocking
+ * CUDA streams, so the kernels of different problems run side by side.
+ *  - meshes, coeffs, decomps: nprob entries each (host arrays); spectral and
+ *    options are shared (options->stream is ignored); every problem's
+ *    arguments are checked before any device work (MSDD_ERR_INVALID_ARG /
+ *    MSDD_ERR_UNSUPPORTED naming the problem).  All meshes must have
+ *    elements of one shape (equal n[d] / n[0] ratios): the element reference
+ *    matrices, which depend on the shape alone, live in constant memory that
+ *    all problems share (uploaded once, before the workers start);
+ *    MSDD_ERR_UNSUPPORTED otherwise.
+ *  - b[p], x[p]: device pointers to the right-hand side and the solution of
+ *    problem p (x^0 = 0); coefficient arrays are read during the call only.
+ *  - status (nprob ints, required), iterations, rel_residual, setup_ms,
+ *    solve_ms (nprob each, may be NULL): per-problem results; a failing
+ *    problem does not stop the others.  The in-kernel wait limit is counted
+ *    in one process-wide counter, so a wait that runs out is reported
+ *    (MSDD_ERR_TIMEOUT) for the problem whose worker reads the counter
+ *    first, which may be another problem than the one that timed out.
+ * Device memory: each worker's problem releases its buffers to the device
+ * cache when it is done, and they serve the next problems at once (the
+ * worker's streams are idle by then), so the batch holds about nworkers
+ * problems' worth of buffers, not nprob.
+ * Returns MSDD_OK when every problem succeeded, else the status of the
+ * first failing problem in queue order (msdd_last_error names it).
+ * Synchronous: returns when all problems are done. */
+msdd_status msdd_batch_run(int nprob, const msdd_mesh* meshes, const msdd_coeff* coeffs, const msdd_decomp* decomps,
+                           const msdd_spectral* spectral, const msdd_options* options, const double* const* b,
+                           double tol, int maxit, double* const* x, int nworkers, int* iterations,
+                           double* rel_residual, int* status, double* setup_ms, double* solve_ms);
 
 /* ---- batches of independent problems --------------------------------------
  * Work items of a batch of problems for one persistent launch: every fine

@@ -1,5 +1,6 @@
 // C ABI of the msdd library (declarations and contracts in include/msdd.h).
 #include <algorithm>
+#include <atomic>
 #include <functional>
 #include <queue>
 #include <cstring>
@@ -11,10 +12,18 @@
 #include "warmstart.cuh"
 
 namespace msdd {
-long long& kernel_launch_counter() {
-    static long long counter = 0;
-    return counter;
+// launches counted per host thread (graph capture subtracts what it captured);
+// worker threads of a batch add theirs to the process total when they end
+namespace {
+std::atomic<long long> g_launch_total{0};
+thread_local long long t_launches = 0;
+}  // namespace
+long long& kernel_launch_counter() { return t_launches; }
+void kernel_launch_flush() {
+    g_launch_total += t_launches;
+    t_launches = 0;
 }
+long long kernel_launch_total() { return g_launch_total.load() + t_launches; }
 }  // namespace msdd
 
 namespace {
@@ -107,6 +116,44 @@ std::vector<msdd::ProbBox> warm_boxes(const msdd_mesh* mesh, const msdd_decomp* 
 
 }  // namespace
 
+msdd_status msdd::check_setup_args(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp,
+                                   const msdd_spectral* spectral, const msdd_options* options, msdd_options* opt_out,
+                                   std::string* msg) {
+    auto bad = [&](msdd_status st, const char* m) {
+        *msg = m;
+        return st;
+    };
+    if (!mesh_ok(mesh)) return bad(MSDD_ERR_INVALID_ARG, "invalid mesh (dim, sizes or Dirichlet faces)");
+    if (!coeff || !coeff->data || (coeff->kind != 0 && coeff->kind != 1))
+        return bad(MSDD_ERR_INVALID_ARG, "invalid coefficient");
+    if (!decomp || !spectral) return bad(MSDD_ERR_INVALID_ARG, "decomposition or spectral options NULL");
+    if (decomp->levels < 2) return bad(MSDD_ERR_INVALID_ARG, "levels must be >= 2");
+    if (decomp->levels > 3) return bad(MSDD_ERR_UNSUPPORTED, "this build supports 2 or 3 levels");
+    if (decomp->overlap < 1) return bad(MSDD_ERR_INVALID_ARG, "overlap must be >= 1 (partition of unity)");
+    for (int d = 0; d < mesh->dim; ++d) {
+        if (decomp->parts[d] < 1 || decomp->parts[d] > mesh->n[d])
+            return bad(MSDD_ERR_INVALID_ARG, "parts must be in 1..n per axis");
+        if (decomp->levels == 3 && decomp->group[d] < 1) return bad(MSDD_ERR_INVALID_ARG, "group must be >= 1 per axis");
+    }
+    if (spectral->nev_max < 1 || spectral->nev_max > 24 || !(spectral->eta > 0.0))
+        return bad(MSDD_ERR_INVALID_ARG, "nev_max must be in 1..24 and eta > 0");
+    if (spectral->blf < 0 || spectral->blf > 3) return bad(MSDD_ERR_INVALID_ARG, "blf must be 1, 2 or 3");
+    msdd_options opt;
+    msdd_default_options(&opt);
+    if (options) opt = *options;
+    if (opt.precision != 0 && opt.precision != 1) return bad(MSDD_ERR_INVALID_ARG, "precision must be 0 or 1");
+    if (opt.block_p < 0 || opt.block_p > msdd::PMAX) return bad(MSDD_ERR_INVALID_ARG, "block_p out of range");
+    if (opt.block_p > 0 && opt.block_p <= spectral->nev_max)
+        return bad(MSDD_ERR_INVALID_ARG, "block_p must exceed nev_max");
+    if (!(opt.sigma > 0.0) || !(opt.eig_tol > 0.0) || opt.eig_maxit < 1 || !(opt.reg_tol < 1.0) ||
+        opt.fp32_start_iters < 0 || opt.fp32_start_iters > 1000)
+        return bad(MSDD_ERR_INVALID_ARG, "invalid eigensolver options");
+    if (opt.warm_start && (opt.warm_cols < 1 || opt.warm_cols > msdd::PMAX))
+        return bad(MSDD_ERR_INVALID_ARG, "warm_cols must be in 1..32 with warm_start");
+    *opt_out = opt;
+    return MSDD_OK;
+}
+
 extern "C" {
 
 const char* msdd_last_error(void) { return g_last_error.c_str(); }
@@ -138,34 +185,10 @@ msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msd
     return guarded([&]() -> msdd_status {
         if (!out) return fail(MSDD_ERR_INVALID_ARG, "out is NULL");
         *out = nullptr;
-        if (!mesh_ok(mesh)) return fail(MSDD_ERR_INVALID_ARG, "invalid mesh (dim, sizes or Dirichlet faces)");
-        if (!coeff || !coeff->data || (coeff->kind != 0 && coeff->kind != 1))
-            return fail(MSDD_ERR_INVALID_ARG, "invalid coefficient");
-        if (!decomp || !spectral) return fail(MSDD_ERR_INVALID_ARG, "decomposition or spectral options NULL");
-        if (decomp->levels < 2) return fail(MSDD_ERR_INVALID_ARG, "levels must be >= 2");
-        if (decomp->levels > 3) return fail(MSDD_ERR_UNSUPPORTED, "this build supports 2 or 3 levels");
-        if (decomp->overlap < 1) return fail(MSDD_ERR_INVALID_ARG, "overlap must be >= 1 (partition of unity)");
-        for (int d = 0; d < mesh->dim; ++d) {
-            if (decomp->parts[d] < 1 || decomp->parts[d] > mesh->n[d])
-                return fail(MSDD_ERR_INVALID_ARG, "parts must be in 1..n per axis");
-            if (decomp->levels == 3 && decomp->group[d] < 1)
-                return fail(MSDD_ERR_INVALID_ARG, "group must be >= 1 per axis");
-        }
-        if (spectral->nev_max < 1 || spectral->nev_max > 24 || !(spectral->eta > 0.0))
-            return fail(MSDD_ERR_INVALID_ARG, "nev_max must be in 1..24 and eta > 0");
-        if (spectral->blf < 0 || spectral->blf > 3) return fail(MSDD_ERR_INVALID_ARG, "blf must be 1, 2 or 3");
         msdd_options opt;
-        msdd_default_options(&opt);
-        if (options) opt = *options;
-        if (opt.precision != 0 && opt.precision != 1) return fail(MSDD_ERR_INVALID_ARG, "precision must be 0 or 1");
-        if (opt.block_p < 0 || opt.block_p > msdd::PMAX) return fail(MSDD_ERR_INVALID_ARG, "block_p out of range");
-        if (opt.block_p > 0 && opt.block_p <= spectral->nev_max)
-            return fail(MSDD_ERR_INVALID_ARG, "block_p must exceed nev_max");
-        if (!(opt.sigma > 0.0) || !(opt.eig_tol > 0.0) || opt.eig_maxit < 1 || !(opt.reg_tol < 1.0) ||
-            opt.fp32_start_iters < 0 || opt.fp32_start_iters > 1000)
-            return fail(MSDD_ERR_INVALID_ARG, "invalid eigensolver options");
-        if (opt.warm_start && (opt.warm_cols < 1 || opt.warm_cols > msdd::PMAX))
-            return fail(MSDD_ERR_INVALID_ARG, "warm_cols must be in 1..32 with warm_start");
+        std::string msg;
+        const msdd_status chk = msdd::check_setup_args(mesh, coeff, decomp, spectral, options, &opt, &msg);
+        if (chk != MSDD_OK) return fail(chk, msg);
         msdd_hierarchy* H = new msdd_hierarchy();
         H->h.opt = opt;
         H->h.spec = *spectral;
@@ -248,6 +271,7 @@ msdd_status msdd_solve_gmres(msdd_hierarchy* h, const double* b, double tol, int
 msdd_status msdd_apply_operator(msdd_hierarchy* h, const double* x, double* y) {
     return guarded([&]() -> msdd_status {
         if (!h || !x || !y) return fail(MSDD_ERR_INVALID_ARG, "NULL argument");
+        msdd::upload_reference(h->h.g);            // this hierarchy's element shape
         msdd::apply_global(h->h.g, x, y, h->h.st);
         MSDD_CUDA(cudaStreamSynchronize(h->h.st));
         return MSDD_OK;
@@ -359,7 +383,7 @@ msdd_status msdd_release_cache(void) {
 
 long long msdd_cached_bytes(void) { return (long long)msdd::dev_cache_bytes(); }
 
-long long msdd_kernel_launches(void) { return msdd::kernel_launch_counter(); }
+long long msdd_kernel_launches(void) { return msdd::kernel_launch_total(); }
 
 msdd_status msdd_band_factor(int batch, const int* n, int nmax, int bw, const double* A, int precision,
                              double reg_tol, void* stream, msdd_band_batch** out, int* status) {

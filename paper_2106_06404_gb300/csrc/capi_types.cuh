@@ -25,4 +25,9 @@ msdd_status set_last_error(msdd_status s, const std::string& msg);
 // wait that gave up -> MSDD_ERR_TIMEOUT, MsddError -> its own status, any
 // other failure -> MSDD_ERR_CUDA).  Allocates nothing itself.
 msdd_status classified_call(msdd_status (*f)(void*), void* ctx);
+// The argument checks of msdd_setup (every field, before any device work):
+// MSDD_OK with the effective options in *opt, else the status and a message.
+msdd_status check_setup_args(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp,
+                             const msdd_spectral* spectral, const msdd_options* options, msdd_options* opt,
+                             std::string* msg);
 }  // namespace msdd

@@ -37,15 +37,31 @@ struct WaitTimeout : std::runtime_error {
             throw ::msdd::CudaError(std::string(#call) + ": " + cudaGetErrorString(err__)); \
     } while (0)
 
-// Process-wide count of kernel launches issued by the library (a graph
-// launch adds the number of kernels it holds).
+// Count of kernel launches issued by the library from the calling host
+// thread (a graph launch adds the number of kernels it holds);
+// kernel_launch_flush adds a thread's count to the process total (batch
+// workers call it when they end), kernel_launch_total is that total plus the
+// calling thread's count.
 long long& kernel_launch_counter();
+void kernel_launch_flush();
+long long kernel_launch_total();
 
-#define MSDD_LAUNCH_CHECK()                 \
-    do {                                    \
-        ++::msdd::kernel_launch_counter();  \
-        MSDD_CUDA(cudaGetLastError());      \
+#define MSDD_LAUNCH_CHECK()                                                                      \
+    do {                                                                                         \
+        ++::msdd::kernel_launch_counter();                                                       \
+        const cudaError_t err__ = cudaGetLastError();                                            \
+        if (err__ != cudaSuccess)                                                                \
+            throw ::msdd::CudaError(std::string("kernel launch (") + ::msdd::base_name(__FILE__) + \
+                                    ":" + std::to_string(__LINE__) + "): " + cudaGetErrorString(err__)); \
     } while (0)
+
+// file name without its directories (for messages)
+inline const char* base_name(const char* path) {
+    const char* b = path;
+    for (const char* c = path; *c; ++c)
+        if (*c == '/' || *c == '\\') b = c + 1;
+    return b;
+}
 
 // Caching device allocator (devcache.cu): dev_cache_release parks a block
 // until the next dev_cache_collect, which synchronises the device once and
@@ -55,6 +71,10 @@ long long& kernel_launch_counter();
 void* dev_cache_alloc(size_t bytes);
 void dev_cache_release(void* p, size_t bytes);
 void dev_cache_collect();
+// Make the blocks that the calling thread released reusable without a device
+// synchronisation.  Only for a thread that has synchronised every stream on
+// which work using those blocks was issued (a batch worker between problems).
+void dev_cache_collect_thread();
 void dev_cache_trim();
 size_t dev_cache_bytes();
 // pinned host blocks, same rules (released blocks reusable after a collect)
@@ -63,6 +83,15 @@ void pinned_cache_release(void* p, size_t bytes);
 // CUDA events with timing, reused (put back only after they completed)
 cudaEvent_t timing_event_get();
 void timing_event_put(cudaEvent_t e);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (the
+// limit is per function and device, shared by all host threads).  It is
+// only ever raised, under a lock, so a launch that another thread sized
+// for a smaller amount stays valid.
+void raise_smem_limit(const void* func, size_t bytes);
+template <class F>
+void raise_smem_limit(F* func, size_t bytes) {
+    raise_smem_limit(reinterpret_cast<const void*>(func), bytes);
+}
 
 // Device buffer (caching allocator above), move-only; borrow() makes a
 // non-owning view of another buffer's memory (never freed by the view).

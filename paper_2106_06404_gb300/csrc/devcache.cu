@@ -11,6 +11,7 @@
 
 #include <map>
 #include <mutex>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -18,14 +19,25 @@ namespace msdd {
 
 namespace {
 
+// A parked block with the release order number and the releasing thread:
+// a collect moves only blocks released before its device synchronisation
+// began, so a block that another thread parks meanwhile (its kernels may
+// still run) stays parked.
+struct Parked {
+    int device;          // -1 for pinned host blocks
+    size_t bytes;        // rounded
+    void* p;
+    unsigned long long seq;
+    std::thread::id owner;
+};
+
 struct Cache {
     std::mutex mu;
     std::map<std::pair<int, size_t>, std::vector<void*>> free_blocks;   // (device, rounded bytes)
-    std::vector<std::pair<std::pair<int, size_t>, void*>> pending;
-    size_t held = 0;                                                     // bytes in both lists
-    // pinned host blocks: same rules (device -1)
-    std::map<size_t, std::vector<void*>> free_host;
-    std::vector<std::pair<size_t, void*>> pending_host;
+    std::map<size_t, std::vector<void*>> free_host;                      // pinned host blocks
+    std::vector<Parked> pending;
+    unsigned long long seq = 0;
+    size_t held = 0;                                                     // device bytes, free + parked
     std::vector<cudaEvent_t> events;                                     // completed timing events
 };
 
@@ -34,7 +46,16 @@ Cache& cache() {
     return *c;
 }
 
-size_t rounded(size_t bytes) { return (bytes + 511) & ~size_t(511); }
+// Size classes: multiples of 512 bytes up to 1 MiB; above that a quarter of
+// the size's octave (1, 1.25, 1.5, 1.75 times a power of two), so that the
+// buffers of problems of different sizes share blocks (at most 25% slack).
+size_t rounded(size_t bytes) {
+    if (bytes <= (size_t(1) << 20)) return (bytes + 511) & ~size_t(511);
+    int top = 63;
+    while (!((bytes >> top) & 1)) --top;
+    const size_t step = size_t(1) << (top - 2);
+    return (bytes + step - 1) & ~(step - 1);
+}
 
 int current_device() {
     int d = 0;
@@ -72,9 +93,10 @@ void* dev_cache_alloc(size_t bytes) {
 void dev_cache_release(void* p, size_t bytes) {
     if (!p) return;
     Cache& c = cache();
+    const int dev = current_device();
     std::lock_guard<std::mutex> lk(c.mu);
     const size_t r = rounded(bytes);
-    c.pending.push_back({{current_device(), r}, p});
+    c.pending.push_back({dev, r, p, c.seq++, std::this_thread::get_id()});
     c.held += r;
 }
 
@@ -100,35 +122,67 @@ void pinned_cache_release(void* p, size_t bytes) {
     if (!p) return;
     Cache& c = cache();
     std::lock_guard<std::mutex> lk(c.mu);
-    c.pending_host.push_back({rounded(bytes), p});
+    c.pending.push_back({-1, rounded(bytes), p, c.seq++, std::this_thread::get_id()});
 }
+
+namespace {
+
+// move the parked blocks that `take` selects to the free lists (lock held)
+template <class Pred>
+void unpark(Cache& c, Pred take) {
+    size_t keep = 0;
+    for (size_t i = 0; i < c.pending.size(); ++i) {
+        const Parked& e = c.pending[i];
+        if (!take(e)) {
+            c.pending[keep++] = e;
+            continue;
+        }
+        if (e.device < 0) c.free_host[e.bytes].push_back(e.p);
+        else c.free_blocks[{e.device, e.bytes}].push_back(e.p);
+    }
+    c.pending.resize(keep);
+}
+
+}  // namespace
 
 void dev_cache_collect() {
     Cache& c = cache();
+    unsigned long long upto;
     {
         std::lock_guard<std::mutex> lk(c.mu);
-        if (c.pending.empty() && c.pending_host.empty()) return;
+        if (c.pending.empty()) return;
+        upto = c.seq;
     }
     cudaDeviceSynchronize();
     std::lock_guard<std::mutex> lk(c.mu);
-    for (auto& e : c.pending) c.free_blocks[e.first].push_back(e.second);
-    c.pending.clear();
-    for (auto& e : c.pending_host) c.free_host[e.first].push_back(e.second);
-    c.pending_host.clear();
+    unpark(c, [&](const Parked& e) { return e.seq < upto; });
+}
+
+void dev_cache_collect_thread() {
+    Cache& c = cache();
+    const std::thread::id me = std::this_thread::get_id();
+    std::lock_guard<std::mutex> lk(c.mu);
+    unpark(c, [&](const Parked& e) { return e.owner == me; });
 }
 
 void dev_cache_trim() {
-    cudaDeviceSynchronize();
     Cache& c = cache();
+    unsigned long long upto;
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        upto = c.seq;
+    }
+    cudaDeviceSynchronize();
     std::lock_guard<std::mutex> lk(c.mu);
-    for (auto& e : c.pending) c.free_blocks[e.first].push_back(e.second);
-    c.pending.clear();
+    unpark(c, [&](const Parked& e) { return e.seq < upto; });
+    size_t freed = 0;
     for (auto& kv : c.free_blocks)
-        for (void* p : kv.second) cudaFree(p);
+        for (void* p : kv.second) {
+            cudaFree(p);
+            freed += kv.first.second;
+        }
     c.free_blocks.clear();
-    c.held = 0;
-    for (auto& e : c.pending_host) c.free_host[e.first].push_back(e.second);
-    c.pending_host.clear();
+    c.held -= freed;
     for (auto& kv : c.free_host)
         for (void* p : kv.second) cudaFreeHost(p);
     c.free_host.clear();
@@ -156,6 +210,17 @@ void timing_event_put(cudaEvent_t e) {
     Cache& c = cache();
     std::lock_guard<std::mutex> lk(c.mu);
     c.events.push_back(e);
+}
+
+void raise_smem_limit(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[std::make_pair(current_device(), func)];
+    if (bytes <= cur) return;
+    if (bytes > 48 * 1024)
+        MSDD_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
 }
 
 size_t dev_cache_bytes() {

@@ -317,6 +317,7 @@ Geom make_geom(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     g.coeff_kind = coeff.kind;
     g.ncomp = coeff.kind == 0 ? 1 : (mesh.dim == 2 ? 3 : 6);
     g.coeff = coeff.data;
+    g.rscale = mesh.dim == 3 ? 1.0 / g.n[0] : 1.0;
     return g;
 }
 
@@ -365,7 +366,7 @@ size_t Hierarchy::device_bytes() const {
     b += (mge.X.n + mge.AX.n + mge.BX.n + mge.Y.n + mge.AY.n + mge.BY.n + mge.W.n) * 8;
     b += (Phi.n + A1.n + Abar_m.n + K_m.n + Zb.n + Tm.n + A0.n + frhs.n + v1.n + r0buf.n) * 8;
     b += (Minv.n + A0inv.n + y0buf.n + z1t.n) * 8;
-    b += (x.n + r.n + p.n + q.n + z.n + stencil.n) * 8;
+    b += (x.n + r.n + p.n + q.n + z.n + stencil.n + coeff_own.n) * 8;
     b += (fst.a.n + fst.b.n) * 8 + fst.b32.n * 4;
     return b;
 }
@@ -391,6 +392,14 @@ void Hierarchy::setup(const msdd_mesh& mesh, const msdd_coeff& coeff) {
     prof.on = opt.profile != 0;
     prof.solves_only = opt.profile == 2;
     g = make_geom(mesh, coeff);
+    {
+        // the caller's coefficient array is read here only: later set-up work
+        // and msdd_apply_operator use the hierarchy's own copy
+        const long long ne = (long long)g.n[0] * g.n[1] * g.n[2] * g.ncomp;
+        coeff_own.alloc((size_t)ne);
+        MSDD_CUDA(cudaMemcpyAsync(coeff_own.p, coeff.data, (size_t)ne * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        g.coeff = coeff_own.p;
+    }
     nun = (long long)g.ushape[0] * g.ushape[1] * g.ushape[2];
     // node coordinates in the combine kernel use 32-bit divisions
     if (nun >= (1LL << 31)) throw MsddError(MSDD_ERR_UNSUPPORTED, "more than 2^31 unknowns");

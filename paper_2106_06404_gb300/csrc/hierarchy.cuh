@@ -152,6 +152,7 @@ struct Hierarchy {
     // ---- CG
     DevBuf<double> x, r, p, q, z, partial;
     DevBuf<double> stencil;         // stored 3^d-point global operator
+    DevBuf<double> coeff_own;       // the hierarchy's copy of the element coefficients
     DevBuf<PcgScalars> sc;
     int nblocks = 1;
     cudaGraphExec_t graph = nullptr;

@@ -1,12 +1,19 @@
 // Q1 assembly and matrix-free operators on the structured mesh.
 #include "q1.cuh"
 
+#include <cstring>
+#include <mutex>
+
 #include <cmath>
 
 namespace msdd {
 
-// R[d][e][a][b] = int_tau d_d phi_a d_e phi_b (tau of size h), and the
-// scalar-coefficient sum S[a][b] = sum_d R[d][d][a][b].
+// R[d][e][a][b] = int_tau d_d phi_a d_e phi_b on the element tau scaled to
+// x-edge 1 (edges 1, h_y / h_x, h_z / h_x), and the scalar-coefficient sum
+// S[a][b] = sum_d R[d][d][a][b].  On the element of the mesh (edges h_x,
+// h_y, h_z) the integrals are h_x^(dim-2) times these (Geom::rscale), so the
+// constants depend on the element's shape only and are the same, bit for
+// bit, for every mesh whose elements have that shape.
 __constant__ double c_R[3][3][8][8];
 __constant__ double c_S[8][8];
 
@@ -16,7 +23,8 @@ void upload_reference(const Geom& g) {
     memset(R, 0, sizeof(R));
     memset(S, 0, sizeof(S));
     const int dim = g.dim, nloc = 1 << dim;
-    double h[3] = {1.0 / g.n[0], 1.0 / g.n[1], dim == 3 ? 1.0 / g.n[2] : 1.0};
+    // h_d / h_x = n_x / n_d, a correctly rounded quotient: equal for equal shapes
+    double h[3] = {1.0, (double)g.n[0] / g.n[1], dim == 3 ? (double)g.n[0] / g.n[2] : 1.0};
     // 2-point Gauss-Legendre on [0,1] per axis integrates the (bi/tri)quadratic
     // integrand exactly.
     const double gp[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
@@ -45,14 +53,25 @@ void upload_reference(const Geom& g) {
     for (int d = 0; d < dim; ++d)
         for (int a = 0; a < nloc; ++a)
             for (int b = 0; b < nloc; ++b) S[a][b] += R[d][d][a][b];
+    // the reference matrices live in constant memory shared by every
+    // hierarchy of the process: upload only when they change (hierarchies
+    // whose elements have the same shape share them)
+    static std::mutex mu;
+    static double last_R[3][3][8][8], last_S[8][8];
+    static bool have = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (have && memcmp(last_R, R, sizeof(R)) == 0 && memcmp(last_S, S, sizeof(S)) == 0) return;
     MSDD_CUDA(cudaMemcpyToSymbol(c_R, R, sizeof(R)));
     MSDD_CUDA(cudaMemcpyToSymbol(c_S, S, sizeof(S)));
+    memcpy(last_R, R, sizeof(R));
+    memcpy(last_S, S, sizeof(S));
+    have = true;
 }
 
 namespace {
 
 __device__ __forceinline__ double elem_entry(const Geom& g, long long e, int a, int b) {
-    if (g.coeff_kind == 0) return g.coeff[e] * c_S[a][b];
+    if (g.coeff_kind == 0) return g.coeff[e] * (c_S[a][b] * g.rscale);
     const double* k = g.coeff + e * g.ncomp;
     double K[3][3];
     if (g.dim == 2) {
@@ -66,7 +85,7 @@ __device__ __forceinline__ double elem_entry(const Geom& g, long long e, int a, 
     double v = 0.0;
     for (int d = 0; d < g.dim; ++d)
         for (int f = 0; f < g.dim; ++f) v += K[d][f] * c_R[d][f][a][b];
-    return v;
+    return v * g.rscale;
 }
 
 // sum over elements tau of the element box containing nodes x and x + o of
@@ -209,7 +228,7 @@ __global__ void k_apply_neumann(Geom g, const ProbBox* __restrict__ boxes, const
 // FP32 versions of the element entries and stencil coefficients (used only
 // by the FP32 start phase of the eigensolver).
 __device__ __forceinline__ float elem_entry_f(const Geom& g, long long e, int a, int b) {
-    if (g.coeff_kind == 0) return (float)g.coeff[e] * (float)c_S[a][b];
+    if (g.coeff_kind == 0) return (float)g.coeff[e] * (float)(c_S[a][b] * g.rscale);
     return (float)elem_entry(g, e, a, b);
 }
 
@@ -850,7 +869,7 @@ void patch_gram(const Geom& g, const ProbBox* d_fine, const double* Phi, const l
                 const int* d_m, const GramItem* d_items, int nitems, double* G, cudaStream_t s) {
     if (nitems == 0) return;
     size_t smem = (size_t)3 * GCH * (1 << g.dim) * ldphi * sizeof(double);
-    if (smem > 48 * 1024) MSDD_CUDA(cudaFuncSetAttribute(k_patch_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) raise_smem_limit(k_patch_gram, smem);
     k_patch_gram<<<nitems, 256, smem, s>>>(g, d_fine, Phi, d_phioff, ldphi, d_m, d_items, G);
     MSDD_LAUNCH_CHECK();
 }

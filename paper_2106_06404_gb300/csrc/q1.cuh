@@ -20,6 +20,7 @@ struct Geom {
     const double* coeff;
     int blf;           // fine GEVP right-hand side b^1, b^2 or b^3 (Section 3.4)
     const int* ecov[3];// b^2: per axis, fine element boxes holding each element index (device)
+    double rscale;     // h_x^(dim-2): the element matrices are rscale times the reference matrices
 };
 
 // One local problem on the fine level: its overlapping element box

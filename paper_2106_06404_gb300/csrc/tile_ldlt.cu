@@ -1728,7 +1728,7 @@ void launch_band_ws(const TileBatch& tb, const CUtensorMap& tm, double* X, int l
     using Cfg = BandWs<KBP, W, C, NST, XD>;
     static_assert(Cfg::smem_bytes <= 227 * 1024, "shared memory per CTA");
     auto kern = k_tile_solve_band_ws<KBP, W, C, NST, XD>;
-    MSDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes));
+    raise_smem_limit(kern, Cfg::smem_bytes);
     kern<<<dim3(tb.P, (ncols + Cfg::COLS - 1) / Cfg::COLS), Cfg::NT, Cfg::smem_bytes, s>>>(
         tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_b.p, tb.d_toff.p, tb.d_roff.p, X, ldx, ncols, skip, gdone);
     MSDD_LAUNCH_CHECK();
@@ -1779,7 +1779,7 @@ void launch_band(const TileBatch& tb, const T* tiles, const T* dinv, double* X, 
     constexpr int ZLD = BandSmem<T, CPT, CG>::ZLD;
     const int chunks = (ncols + ZLD - 1) / ZLD;
     const size_t b = BandSmem<T, CPT, CG>::bytes(((std::min(ncols, ZLD) + 1) / 2) * 2);
-    MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve_band<T, CPT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+    raise_smem_limit(k_tile_solve_band<T, CPT, CG>, b);
     k_tile_solve_band<T, CPT, CG><<<dim3(tb.P, chunks), 8 * CG, b, s>>>(tiles, dinv, tb.d_kb.p, tb.d_K.p, tb.d_toff.p,
                                                                          tb.d_roff.p, X, ldx, ncols, skip, gdone);
     MSDD_LAUNCH_CHECK();
@@ -1952,7 +1952,7 @@ void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
     }
     if (tb.prec && maxkb <= 2) {
         const size_t b = factor_band32_smem();
-        MSDD_CUDA(cudaFuncSetAttribute(k_tile_factor_band32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+        raise_smem_limit(k_tile_factor_band32, b);
         k_tile_factor_band32<<<tb.P, FB_T, b, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_n.p, tb.d_kb.p, tb.d_K.p,
                                                   tb.d_toff.p, tb.d_roff.p, tb.d_status.p, tb.d_nreg.p, reg_tol);
         MSDD_LAUNCH_CHECK();
@@ -1965,7 +1965,7 @@ void tile_factor(TileBatch& tb, double reg_tol, cudaStream_t s) {
         alignas(64) CUtensorMap tlo;
         if (thi && encode_tile_map(lo.p, tb.total_tile_elems, &tlo)) {
             const size_t b = tf_smem_bytes();
-            MSDD_CUDA(cudaFuncSetAttribute(k_tile_factor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            raise_smem_limit(k_tile_factor_tc, b);
             k_tile_factor_tc<<<tb.P, TF_NT, b, s>>>(*thi, tlo, tb.tiles_f.p, lo.p, tb.total_tile_elems, tb.dinv_f.p,
                                                    tb.d_n.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p,
                                                    tb.d_status.p, tb.d_nreg.p, reg_tol);
@@ -2006,11 +2006,11 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
         if (maxkb <= 2 && ring_bytes <= 200 * 1024) {
             if (tb.prec) {
                 auto k = maxkb <= 1 ? k_tile_solve1<float, 1> : k_tile_solve1<float, 2>;
-                MSDD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_bytes));
+                raise_smem_limit(k, ring_bytes);
                 k<<<tb.P, S1T, ring_bytes, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
             } else {
                 auto k = maxkb <= 1 ? k_tile_solve1<double, 1> : k_tile_solve1<double, 2>;
-                MSDD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_bytes));
+                raise_smem_limit(k, ring_bytes);
                 k<<<tb.P, S1T, ring_bytes, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
             }
             MSDD_LAUNCH_CHECK();
@@ -2027,8 +2027,8 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
         }
         if (maxkb > 2 && zbytes <= 160 * 1024) {
             if (zbytes > 48 * 1024) {
-                MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
-                MSDD_CUDA(cudaFuncSetAttribute(k_tile_solve1_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes));
+                raise_smem_limit(k_tile_solve1_dense<float>, zbytes);
+                raise_smem_limit(k_tile_solve1_dense<double>, zbytes);
             }
             if (tb.prec) k_tile_solve1_dense<float><<<tb.P, S1T, zbytes, s>>>(tb.tiles_f.p, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);
             else k_tile_solve1_dense<double><<<tb.P, S1T, zbytes, s>>>(tb.tiles_d.p, tb.dinv_d.p, tb.d_kb.p, tb.d_K.p, tb.d_toff.p, tb.d_roff.p, X, gdone);

@@ -77,7 +77,7 @@ EXPORTED = [
     "msdd_band_factor", "msdd_band_solve", "msdd_band_destroy", "msdd_band_solve_noalloc", "msdd_kernel_launches",
     "msdd_fine_layout", "msdd_nn_patches", "msdd_nn_workspace_bytes", "msdd_nn_forward", "msdd_nn_loss_grad",
     "msdd_nn_adam", "msdd_nn_start_vectors", "msdd_nn_targets", "msdd_release_cache", "msdd_cached_bytes",
-    "msdd_apply_hybrid_preconditioner", "msdd_solve_gmres", "msdd_batch_plan",
+    "msdd_apply_hybrid_preconditioner", "msdd_solve_gmres", "msdd_batch_plan", "msdd_batch_run",
 ]
 
 # learned warm start (include/msdd.h, MSDD_NN_*)
@@ -130,6 +130,8 @@ def load(path=LIB_PATH):
     lib.msdd_fine_layout.argtypes = [P(Mesh), P(Decomp), ip, ctypes.c_int, ip]
     lib.msdd_batch_plan.argtypes = [ctypes.c_int, P(Mesh), P(Decomp), ctypes.c_int, ip, dp, ctypes.c_longlong,
                                     P(ctypes.c_longlong), dp, dp]
+    lib.msdd_batch_run.argtypes = [ctypes.c_int, P(Mesh), P(Coeff), P(Decomp), P(Spectral), P(Options), P(vp),
+                                   ctypes.c_double, ctypes.c_int, P(vp), ctypes.c_int, ip, dp, ip, dp, dp]
     lib.msdd_nn_patches.argtypes = [P(Mesh), P(Coeff), P(Decomp), vp, vp]
     lib.msdd_nn_workspace_bytes.argtypes = [ctypes.c_int]
     lib.msdd_nn_workspace_bytes.restype = ctypes.c_size_t
@@ -221,7 +223,7 @@ class Hierarchy:
         self._lib = lib
         self.mesh = make_mesh(n, dirichlet_faces)
         coeff = coeff.to(device="cuda", dtype=torch.float64).contiguous()
-        self._coeff = coeff                      # the library reads it during solves
+        self._coeff = coeff                      # alive until msdd_setup has copied it
         c = Coeff()
         c.kind = 0 if coeff.dim() == 1 else 1
         c.data = coeff.data_ptr()
@@ -440,6 +442,59 @@ def batch_plan(problems, nworkers):
                                cost.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt.value, ctypes.byref(cnt),
                                ctypes.byref(mk), ctypes.byref(lb)))
     return items.reshape(-1, 2), cost, mk.value, lb.value
+
+
+def batch_run(problems, nev_max, eta, tol=1e-8, maxit=1000, precision=1, nworkers=8, allow_fail=False, **opts):
+    """msdd_batch_run: set up and solve independent problems on the GPU.
+
+    problems: list of dicts with n, kappa (CUDA float64 tensor), parts, overlap,
+    levels, group, b (CUDA float64 right-hand side) and optionally
+    dirichlet_faces.  Returns (xs, iterations, rel_residuals, statuses,
+    setup_ms, solve_ms) with one entry per problem (xs: CUDA tensors)."""
+    torch = _torch()
+    lib = load()
+    k = len(problems)
+    meshes, coeffs, decs = (Mesh * k)(), (Coeff * k)(), (Decomp * k)()
+    keep, xs = [], []
+    bp, xp = (ctypes.c_void_p * k)(), (ctypes.c_void_p * k)()
+    for i, pr in enumerate(problems):
+        meshes[i] = make_mesh(pr["n"], pr.get("dirichlet_faces", 0b1))
+        kap = pr["kappa"].to(device="cuda", dtype=torch.float64).contiguous()
+        b = pr["b"].to(device="cuda", dtype=torch.float64).contiguous()
+        keep += [kap, b]
+        coeffs[i].kind = 0 if kap.dim() == 1 else 1
+        coeffs[i].data = kap.data_ptr()
+        d = Decomp()
+        for a in range(3):
+            d.parts[a] = int(pr["parts"][a]) if a < len(pr["parts"]) else 1
+            g = pr.get("group", (1, 1, 1))
+            d.group[a] = int(g[a]) if a < len(g) else 1
+        d.overlap = int(pr["overlap"])
+        d.levels = int(pr.get("levels", 2))
+        decs[i] = d
+        x = torch.zeros_like(b)
+        xs.append(x)
+        bp[i], xp[i] = b.data_ptr(), x.data_ptr()
+    s = Spectral()
+    s.nev_max, s.eta, s.blf = int(nev_max), float(eta), 1
+    o = default_options()
+    o.precision = int(precision)
+    for key, val in opts.items():
+        setattr(o, key, val)
+    it = np.zeros(k, dtype=np.int32)
+    rel = np.zeros(k)
+    st = np.zeros(k, dtype=np.int32)
+    sms = np.zeros(k)
+    pms = np.zeros(k)
+    torch.cuda.synchronize()
+    P = ctypes.POINTER
+    status = lib.msdd_batch_run(k, meshes, coeffs, decs, ctypes.byref(s), ctypes.byref(o), bp, float(tol), int(maxit),
+                                xp, int(nworkers), it.ctypes.data_as(P(ctypes.c_int)),
+                                rel.ctypes.data_as(P(ctypes.c_double)), st.ctypes.data_as(P(ctypes.c_int)),
+                                sms.ctypes.data_as(P(ctypes.c_double)), pms.ctypes.data_as(P(ctypes.c_double)))
+    if not allow_fail:
+        _check(status)
+    return xs, it, rel, st, sms, pms
 
 
 def fine_layout(n, parts, overlap, dirichlet_faces=0b1):

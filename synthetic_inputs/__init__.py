@@ -151,6 +151,14 @@ def composite128(seed=0):
                     seed=seed, kind="composite")
 
 
+def composite96(seed=0):
+    """3D, 96^3 Q1, the layered composite of composite128 at 6^3 subdomains, overlap 1, three levels,
+    nev <= 16: the same box shapes as the 128^3 workload's Dirichlet matrices (16^3 elements per
+    subdomain) at a size small enough for a full ncu capture."""
+    return Workload("composite3d_96_6x6x6_3lvl", (96, 96, 96), (6, 6, 6), 1, 3, (2, 2, 2), 16, 0.3,
+                    seed=seed, kind="composite")
+
+
 def batch256(seed=0, count=256):
     """Batch of independent 2D problems of uneven size: per problem, from one
     PCG64(seed) stream in this order, the side N ~ U{128..384} elements, the
