@@ -212,25 +212,6 @@ __global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ 
     }
 }
 
-// H, M = sums of the split partials (fixed order)
-__global__ void k_gram_sum(const double* __restrict__ Hp, const double* __restrict__ Mp, double* __restrict__ H,
-                           double* __restrict__ M, const int* __restrict__ p_, const int* __restrict__ done,
-                           int gsplit) {
-    const int i = blockIdx.x;
-    if (done[i]) return;
-    const int p = p_[i];
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        const int a = e / p, b = e % p;
-        double hs = 0.0, ms = 0.0;
-        for (int s = 0; s < gsplit; ++s) {
-            const long long o = ((long long)i * gsplit + s) * PMAX * PMAX + a * PMAX + b;
-            hs += Hp[o];
-            ms += Mp[o];
-        }
-        H[(long long)i * PMAX * PMAX + a * PMAX + b] = hs;
-        M[(long long)i * PMAX * PMAX + a * PMAX + b] = ms;
-    }
-}
 
 // ---- block-wide symmetric eigen-solver (parallel cyclic Jacobi, round robin)
 // FP64 divisions and square roots are long instruction sequences on the
@@ -638,7 +619,10 @@ __device__ bool rr_fast(double (*S)[LD], double (*V)[LD], double (*L)[LD], doubl
 // positive definite), eigen-decomposition of the reduced standard problem.
 // C = D L^{-T} V with theta ascending; columns of dropped (dependent)
 // directions get theta = +inf and zero columns of C.
-__global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict__ H, const double* __restrict__ M,
+// H and M are first summed from the split partials of k_gram_split (in
+// split order) and stored; the kernel then reads them back.
+__global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict__ Hp, const double* __restrict__ Mp,
+                                                       int gsplit, double* __restrict__ H, double* __restrict__ M,
                                                        double* __restrict__ C, double* __restrict__ theta,
                                                        const int* __restrict__ p_, int* __restrict__ rank,
                                                        const int* __restrict__ done) {
@@ -651,8 +635,21 @@ __global__ void __launch_bounds__(TPB) k_rayleigh_ritz(const double* __restrict_
     const int p = p_[i];
     const int q = p + (p & 1);
     const int t = threadIdx.x;
-    const double* Hi = H + (long long)i * PMAX * PMAX;
-    const double* Mi = M + (long long)i * PMAX * PMAX;
+    double* Hw = H + (long long)i * PMAX * PMAX;
+    double* Mw = M + (long long)i * PMAX * PMAX;
+    for (int e = t; e < p * p; e += TPB) {
+        const int a = e / p, b = e % p;
+        double hs = 0.0, ms = 0.0;
+        for (int sp = 0; sp < gsplit; ++sp) {
+            const long long o = ((long long)i * gsplit + sp) * PMAX * PMAX + a * PMAX + b;
+            hs += Hp[o];
+            ms += Mp[o];
+        }
+        Hw[a * PMAX + b] = hs;
+        Mw[a * PMAX + b] = ms;
+    }
+    const double* Hi = Hw;
+    const double* Mi = Mw;
     if (t == 0) s_zero = 0;
     __syncthreads();
     if (t < PMAX) {
@@ -1313,12 +1310,11 @@ void eig_gram(GevpBatch& g, cudaStream_t s) {
     k_gram_split<<<dim3(g.P, g.gsplit), GR_T, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.Hp.p, g.Mp.p, g.K.d_n.p, g.K.d_roff.p,
                                                      g.d_p.p, g.ldx, g.done.p, g.gsplit);
     MSDD_LAUNCH_CHECK();
-    k_gram_sum<<<g.P, 256, 0, s>>>(g.Hp.p, g.Mp.p, g.H.p, g.M.p, g.d_p.p, g.done.p, g.gsplit);
-    MSDD_LAUNCH_CHECK();
 }
 
 void eig_rayleigh_ritz(GevpBatch& g, cudaStream_t s) {
-    k_rayleigh_ritz<<<g.P, TPB, 0, s>>>(g.H.p, g.M.p, g.C.p, g.theta.p, g.d_p.p, g.rank.p, g.done.p);
+    k_rayleigh_ritz<<<g.P, TPB, 0, s>>>(g.Hp.p, g.Mp.p, g.gsplit, g.H.p, g.M.p, g.C.p, g.theta.p, g.d_p.p, g.rank.p,
+                                        g.done.p);
     MSDD_LAUNCH_CHECK();
 }
 
