@@ -14,6 +14,8 @@ preconditioner and PCG (method.py).
 
 Pins: every function is checked in tests/test_oracle_*.py against closed forms,
 invariants and brute force, never against the CUDA path.  Parity pinned for
-all functions except where a test module says "parity unpinned".
+all functions except where a test module says "parity unpinned", and except
+method.normalise_sign: parity unpinned (a sign convention for exported
+eigenvectors; every comparison goes through spans or Ritz values).
 """
 from . import fem, linalg, decomposition, method  # noqa: F401

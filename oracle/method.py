@@ -115,7 +115,10 @@ def gevp_regularised(Abar, B, sigma, tau):
 
 
 def normalise_sign(W):
-    """Flip each column so that its entry of largest magnitude is positive."""
+    """Flip each column so that its entry of largest magnitude is positive.
+
+    Parity unpinned: a sign convention, not part of the method; no comparison
+    with the CUDA path depends on it (spans and Ritz values are compared)."""
     W = W.copy()
     for k in range(W.shape[1]):
         i = int(np.argmax(np.abs(W[:, k])))
