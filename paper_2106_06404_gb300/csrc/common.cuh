@@ -217,6 +217,48 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     if (e == 0xffu) { hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x00080000u : 0u); lo = m << 29; }
     return __hiloint2double((int)hi, (int)lo);
 }
+// ---- double-float arithmetic on the FP32 pipes (Dekker's error-free product
+// via FMA, Knuth's two-sum).  A value is the unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= 2^-23 |hi|, about 47 significant bits: enough for
+// sums of products whose FP64 results only need ~1e-13 relative accuracy, at a
+// dozen FP32 operations per multiply-add instead of one FP64 operation on the
+// narrow FP64 pipe.  The _rn intrinsics keep the compiler from contracting
+// the error-free steps into FMAs.
+//
+// FP64 x -> (hi, lo) from the bit fields: hi keeps the leading 24 significand
+// bits (truncated, exact in FP32), lo is the remaining 29 bits rounded to FP32,
+// so |x - hi - lo| <= 2^-47 |x|.  Exponents outside [2^-60, 2^100] fall back
+// to (f64_to_f32(x), 0).
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned uh = (unsigned)(u >> 32), ul = (unsigned)u;
+    const unsigned sign = uh & 0x80000000u;
+    const int e = (int)((uh >> 20) & 0x7ffu);
+    if (e < 1023 - 60 || e > 1023 + 100) {
+        hi = f64_to_f32(x);
+        lo = 0.f;
+        return;
+    }
+    hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | ((uh & 0x000fffffu) << 3) | (ul >> 29));
+    // lo = r 2^(e - 1075) with r the 29 dropped bits; the scale is a normal FP32 power of two here
+    const float r = __uint2float_rn(ul & 0x1fffffffu);
+    lo = __uint_as_float(__float_as_uint(__fmul_rn(r, __uint_as_float((unsigned)(e - 1075 + 127) << 23))) | sign);
+}
+// (sh, sl) += (ah + al)(bh + bl): the product of the leading parts exactly
+// (p + e), the cross terms into e, p into sh by two-sum, the rest into sl
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float s = __fadd_rn(sh, p);
+    const float bb = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+__device__ __forceinline__ double df_to_f64(float hi, float lo) { return f32_to_f64(hi) + f32_to_f64(lo); }
+
 // load a double as T / store a T as double
 template <typename T> __device__ __forceinline__ T from_f64(double x);
 template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }

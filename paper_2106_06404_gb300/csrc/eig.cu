@@ -1,6 +1,8 @@
 // Batched subspace iteration with Rayleigh-Ritz (see eig.cuh).
 #include "eig.cuh"
 
+#include <type_traits>
+
 #include <cmath>
 
 namespace msdd {
@@ -132,17 +134,23 @@ __global__ void __launch_bounds__(TPB) k_form_y_knorm(double* __restrict__ Y, co
     }
 }
 
-// H = Y^T AY, M = Y^T BY (symmetric, FP64), one CTA per problem.
 // H = Y^T AY, M = Y^T BY as partial sums over `gsplit` row ranges of each
 // problem (grid: problems x splits); each thread owns 2 x 2 blocks (bi <= bj)
-// of the upper block triangle, read as double2 from shared row chunks.
+// of the upper block triangle, read as pairs from shared row chunks.
+// DF = false: FP64 arithmetic.  DF = true: the rows are split into FP32
+// (hi, lo) pairs as they are staged and the products are accumulated in
+// double-float (split_f64, df_fma), off the narrow FP64 pipe; the partials
+// are stored as FP64.
 constexpr int GR_T = 64, GR_ROWS = 32, GR_LD = 34;
+template <bool DF>
 __global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ Y, const double* __restrict__ AY,
                                                      const double* __restrict__ BY, double* __restrict__ Hp,
                                                      double* __restrict__ Mp, const int* __restrict__ n_,
                                                      const long long* __restrict__ roff_, const int* __restrict__ p_,
                                                      int ldx, const int* __restrict__ done, int gsplit) {
-    __shared__ __align__(16) double sY[GR_ROWS][GR_LD], sA[GR_ROWS][GR_LD], sB[GR_ROWS][GR_LD];
+    using V = std::conditional_t<DF, float, double>;
+    constexpr int NA = DF ? 2 : 1;                       // FP64: value; DF: hi, lo
+    __shared__ __align__(16) V sY[NA][GR_ROWS][GR_LD], sA[NA][GR_ROWS][GR_LD], sB[NA][GR_ROWS][GR_LD];
     const int i = blockIdx.x, sp = blockIdx.y, t = threadIdx.x;
     if (done[i]) return;
     const int n = n_[i], p = p_[i], q = p + (p & 1), nb = q / 2;
@@ -152,7 +160,7 @@ __global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ 
     const int nblk = nb * (nb + 1) / 2;
     constexpr int KMAX = (PMAX / 2 * (PMAX / 2 + 1) / 2 + GR_T - 1) / GR_T;
     int ba[KMAX], bb[KMAX];
-    double h[KMAX][4], m[KMAX][4];
+    V h[KMAX][NA][4], m[KMAX][NA][4];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         const int e = t + k * GR_T;
@@ -165,7 +173,9 @@ __global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ 
             bb[k] = a + rem;
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) { h[k][c] = 0.0; m[k][c] = 0.0; }
+        for (int z = 0; z < NA; ++z)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { h[k][z][c] = V(0); m[k][z][c] = V(0); }
     }
     for (int r0 = r_lo; r0 < r_hi; r0 += GR_ROWS) {
         __syncthreads();
@@ -173,9 +183,16 @@ __global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ 
             const int rr = e / q, c = e % q, r = r0 + rr;
             const bool ok = r < r_hi && c < p;
             const long long idx = (roff + r) * ldx + c;
-            sY[rr][c] = ok ? Y[idx] : 0.0;
-            sA[rr][c] = ok ? AY[idx] : 0.0;
-            sB[rr][c] = ok ? BY[idx] : 0.0;
+            const double y = ok ? Y[idx] : 0.0, av = ok ? AY[idx] : 0.0, bv = ok ? BY[idx] : 0.0;
+            if constexpr (DF) {
+                split_f64(y, sY[0][rr][c], sY[1][rr][c]);
+                split_f64(av, sA[0][rr][c], sA[1][rr][c]);
+                split_f64(bv, sB[0][rr][c], sB[1][rr][c]);
+            } else {
+                sY[0][rr][c] = y;
+                sA[0][rr][c] = av;
+                sB[0][rr][c] = bv;
+            }
         }
         __syncthreads();
         const int nr = min(GR_ROWS, r_hi - r0);
@@ -184,11 +201,28 @@ __global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ 
             if (ba[k] < 0) continue;
             const int a0 = 2 * ba[k], b0 = 2 * bb[k];
             for (int rr = 0; rr < nr; ++rr) {
-                const double2 y = *reinterpret_cast<const double2*>(&sY[rr][a0]);
-                const double2 av = *reinterpret_cast<const double2*>(&sA[rr][b0]);
-                const double2 bv = *reinterpret_cast<const double2*>(&sB[rr][b0]);
-                h[k][0] += y.x * av.x; h[k][1] += y.x * av.y; h[k][2] += y.y * av.x; h[k][3] += y.y * av.y;
-                m[k][0] += y.x * bv.x; m[k][1] += y.x * bv.y; m[k][2] += y.y * bv.x; m[k][3] += y.y * bv.y;
+                if constexpr (DF) {
+                    const float2 yh = *reinterpret_cast<const float2*>(&sY[0][rr][a0]);
+                    const float2 yl = *reinterpret_cast<const float2*>(&sY[1][rr][a0]);
+                    const float2 ah = *reinterpret_cast<const float2*>(&sA[0][rr][b0]);
+                    const float2 al = *reinterpret_cast<const float2*>(&sA[1][rr][b0]);
+                    const float2 bh = *reinterpret_cast<const float2*>(&sB[0][rr][b0]);
+                    const float2 bl = *reinterpret_cast<const float2*>(&sB[1][rr][b0]);
+                    df_fma(h[k][0][0], h[k][1][0], yh.x, yl.x, ah.x, al.x);
+                    df_fma(h[k][0][1], h[k][1][1], yh.x, yl.x, ah.y, al.y);
+                    df_fma(h[k][0][2], h[k][1][2], yh.y, yl.y, ah.x, al.x);
+                    df_fma(h[k][0][3], h[k][1][3], yh.y, yl.y, ah.y, al.y);
+                    df_fma(m[k][0][0], m[k][1][0], yh.x, yl.x, bh.x, bl.x);
+                    df_fma(m[k][0][1], m[k][1][1], yh.x, yl.x, bh.y, bl.y);
+                    df_fma(m[k][0][2], m[k][1][2], yh.y, yl.y, bh.x, bl.x);
+                    df_fma(m[k][0][3], m[k][1][3], yh.y, yl.y, bh.y, bl.y);
+                } else {
+                    const double2 y = *reinterpret_cast<const double2*>(&sY[0][rr][a0]);
+                    const double2 av = *reinterpret_cast<const double2*>(&sA[0][rr][b0]);
+                    const double2 bv = *reinterpret_cast<const double2*>(&sB[0][rr][b0]);
+                    h[k][0][0] += y.x * av.x; h[k][0][1] += y.x * av.y; h[k][0][2] += y.y * av.x; h[k][0][3] += y.y * av.y;
+                    m[k][0][0] += y.x * bv.x; m[k][0][1] += y.x * bv.y; m[k][0][2] += y.y * bv.x; m[k][0][3] += y.y * bv.y;
+                }
             }
         }
     }
@@ -202,16 +236,23 @@ __global__ void __launch_bounds__(GR_T) k_gram_split(const double* __restrict__ 
         for (int c = 0; c < 4; ++c) {
             const int a = a0 + (c >> 1), b = b0 + (c & 1);
             if (a >= p || b >= p) continue;
-            Hs[a * PMAX + b] = h[k][c];
-            Ms[a * PMAX + b] = m[k][c];
+            double hv, mv;
+            if constexpr (DF) {
+                hv = df_to_f64(h[k][0][c], h[k][1][c]);
+                mv = df_to_f64(m[k][0][c], m[k][1][c]);
+            } else {
+                hv = h[k][0][c];
+                mv = m[k][0][c];
+            }
+            Hs[a * PMAX + b] = hv;
+            Ms[a * PMAX + b] = mv;
             if (a0 != b0) {                                 // mirror off-diagonal blocks
-                Hs[b * PMAX + a] = h[k][c];
-                Ms[b * PMAX + a] = m[k][c];
+                Hs[b * PMAX + a] = hv;
+                Ms[b * PMAX + a] = mv;
             }
         }
     }
 }
-
 
 // ---- block-wide symmetric eigen-solver (parallel cyclic Jacobi, round robin)
 // FP64 divisions and square roots are long instruction sequences on the
@@ -794,7 +835,9 @@ sorted_output:
 // X = Y C, AX = AY C, BX = BY C on a block of 32 rows; residual partial sums.
 // Outputs (row, column < p) are spread over the threads, at most 4 each.
 // FULL = false: X = Y C only (AX, BX, partial untouched).
-template <bool FULL>
+// DF (with FULL = false, the chosen form's X-only update): the products in
+// double-float (split_f64 while staging, df_fma), X stored as FP64.
+template <bool FULL, bool DF = false>
 __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, const double* __restrict__ AY,
                                                 const double* __restrict__ BY, double* __restrict__ X,
                                                 double* __restrict__ AX, double* __restrict__ BX,
@@ -812,6 +855,31 @@ __global__ void __launch_bounds__(TPB) k_update(const double* __restrict__ Y, co
     if (r0 >= rows) return;
     const long long roff = roff_[i];
     const int t = threadIdx.x;
+    if constexpr (DF && !FULL) {
+        // hi and lo halves of C and of the row block, as FP32 in the FP64 arrays' space
+        float (*cH)[LD] = reinterpret_cast<float (*)[LD]>(&sC[0][0]);
+        float (*cL)[LD] = cH + PMAX;
+        float (*yH)[LD] = reinterpret_cast<float (*)[LD]>(&sY[0][0]);
+        float (*yL)[LD] = yH + ROWBLK;
+        for (int e = t; e < p * p; e += TPB)
+            split_f64(C[(long long)i * PMAX * PMAX + (e / p) * PMAX + e % p], cH[e / p][e % p], cL[e / p][e % p]);
+        for (int e = t; e < ROWBLK * p; e += TPB) {
+            const int rr = e / p, c = e % p, r = r0 + rr;
+            split_f64(r < n ? Y[(roff + r) * ldx + c] : 0.0, yH[rr][c], yL[rr][c]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = t + k * TPB;
+            if (e >= ROWBLK * p) break;
+            const int rr = e / p, c = e % p;
+            float xh = 0.f, xl = 0.f;
+            for (int j = 0; j < p; ++j) df_fma(xh, xl, yH[rr][j], yL[rr][j], cH[j][c], cL[j][c]);
+            const int r = r0 + rr;
+            if (r < rows) X[(roff + r) * ldx + c] = df_to_f64(xh, xl);
+        }
+        return;
+    }
     for (int e = t; e < p * p; e += TPB) sC[e / p][e % p] = C[(long long)i * PMAX * PMAX + (e / p) * PMAX + e % p];
     for (int e = t; e < ROWBLK * p; e += TPB) {
         int rr = e / p, c = e % p;
@@ -1307,8 +1375,13 @@ void eig_cholqr32(GevpBatch& g, cudaStream_t s) {
 }
 
 void eig_gram(GevpBatch& g, cudaStream_t s) {
-    k_gram_split<<<dim3(g.P, g.gsplit), GR_T, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.Hp.p, g.Mp.p, g.K.d_n.p, g.K.d_roff.p,
-                                                     g.d_p.p, g.ldx, g.done.p, g.gsplit);
+    // the chosen form (FP32 fine factors) takes the double-float products
+    if (g.K.prec)
+        k_gram_split<true><<<dim3(g.P, g.gsplit), GR_T, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.Hp.p, g.Mp.p, g.K.d_n.p,
+                                                                g.K.d_roff.p, g.d_p.p, g.ldx, g.done.p, g.gsplit);
+    else
+        k_gram_split<false><<<dim3(g.P, g.gsplit), GR_T, 0, s>>>(g.Y.p, g.AY.p, g.BY.p, g.Hp.p, g.Mp.p, g.K.d_n.p,
+                                                                 g.K.d_roff.p, g.d_p.p, g.ldx, g.done.p, g.gsplit);
     MSDD_LAUNCH_CHECK();
 }
 
@@ -1327,9 +1400,14 @@ void eig_update(GevpBatch& g, cudaStream_t s) {
 
 void eig_update_x(GevpBatch& g, cudaStream_t s) {
     dim3 grid(g.nblk_max, g.P);
-    k_update<false><<<grid, TPB, 0, s>>>(g.Y.p, nullptr, nullptr, g.X.p, nullptr, nullptr, g.C.p, g.theta.p,
-                                         g.K.d_n.p, g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx, nullptr, g.nblk_max,
-                                         g.done.p);
+    if (g.K.prec)
+        k_update<false, true><<<grid, TPB, 0, s>>>(g.Y.p, nullptr, nullptr, g.X.p, nullptr, nullptr, g.C.p, g.theta.p,
+                                                   g.K.d_n.p, g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx, nullptr,
+                                                   g.nblk_max, g.done.p);
+    else
+        k_update<false><<<grid, TPB, 0, s>>>(g.Y.p, nullptr, nullptr, g.X.p, nullptr, nullptr, g.C.p, g.theta.p,
+                                             g.K.d_n.p, g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx, nullptr, g.nblk_max,
+                                             g.done.p);
     MSDD_LAUNCH_CHECK();
 }
 

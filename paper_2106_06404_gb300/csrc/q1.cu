@@ -348,7 +348,9 @@ __device__ __forceinline__ int nbr_offset(int oi, int w0, int w1, int dim) {
 }
 
 // One thread per (row, chunk of 8 columns).  A zero coefficient marks a
-// neighbour outside the box (its row is not read).
+// neighbour outside the box (its row is not read).  DF: the products are
+// accumulated in double-float (split_f64, df_fma) on the FP32 pipes.
+template <bool DF>
 __global__ void __launch_bounds__(128) k_apply_local(const ProbBox* __restrict__ boxes, int dim,
                                                      const long long* __restrict__ roff_, const double* __restrict__ A,
                                                      const double* __restrict__ B, const double* __restrict__ X,
@@ -367,21 +369,40 @@ __global__ void __launch_bounds__(128) k_apply_local(const ProbBox* __restrict__
         const int r = (int)(w / nchunk), c0 = (int)(w % nchunk) * 8;
         const int c1 = min(ncols, c0 + 8);
         double ax[8], bx[8];
+        float axh[8], axl[8], bxh[8], bxl[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) { ax[c] = 0.0; bx[c] = 0.0; }
+        for (int c = 0; c < 8; ++c) { ax[c] = 0.0; bx[c] = 0.0; axh[c] = axl[c] = bxh[c] = bxl[c] = 0.f; }
         const double* ar = A + (roff + r) * noff;
         const double* br = B + (roff + r) * noff;
         for (int oi = 0; oi < noff; ++oi) {
             const double a = ar[oi], b = br[oi];
             if (a == 0.0 && b == 0.0) continue;
             const double* xr = X + (roff + r + nbr_offset(oi, w0, w1, dim)) * ldx;
+            if constexpr (DF) {
+                float ah, al, bh, bl;
+                split_f64(a, ah, al);
+                split_f64(b, bh, bl);
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (c0 + c < c1) {
-                    const double v = xr[c0 + c];
-                    ax[c] += a * v;
-                    bx[c] += b * v;
-                }
+                for (int c = 0; c < 8; ++c)
+                    if (c0 + c < c1) {
+                        float vh, vl;
+                        split_f64(xr[c0 + c], vh, vl);
+                        df_fma(axh[c], axl[c], ah, al, vh, vl);
+                        df_fma(bxh[c], bxl[c], bh, bl, vh, vl);
+                    }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c0 + c < c1) {
+                        const double v = xr[c0 + c];
+                        ax[c] += a * v;
+                        bx[c] += b * v;
+                    }
+            }
+        }
+        if constexpr (DF) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) { ax[c] = df_to_f64(axh[c], axl[c]); bx[c] = df_to_f64(bxh[c], bxl[c]); }
         }
         double* aw = AX + (roff + r) * ldx;
         double* bw = BX + (roff + r) * ldx;
@@ -400,7 +421,9 @@ __global__ void __launch_bounds__(128) k_apply_local(const ProbBox* __restrict__
 // Since BX - (AX + sigma BX) mu = -(AX - theta BX) mu, W is one product of
 // the residual R = AX - theta BX.  The squares are summed in FP32 (from
 // integer-pipe conversions): they only feed the relative residual test, and
-// the FP64 pipe is the bound of this kernel.
+// the FP64 pipe is the bound of this kernel.  DF: the stencil products in
+// double-float (split_f64, df_fma), R and W from their FP64 sums.
+template <bool DF>
 __global__ void __launch_bounds__(128) k_apply_rhs(const ProbBox* __restrict__ boxes, int dim,
                                                    const long long* __restrict__ roff_, const int* __restrict__ K_,
                                                    const double* __restrict__ A, const double* __restrict__ B,
@@ -433,19 +456,39 @@ __global__ void __launch_bounds__(128) k_apply_rhs(const ProbBox* __restrict__ b
     for (int cb = cg; cb < p; cb += 16) {
         double ax[4] = {0.0, 0.0, 0.0, 0.0}, bx[4] = {0.0, 0.0, 0.0, 0.0};
         if (r < n) {
+            float axh[4] = {0.f, 0.f, 0.f, 0.f}, axl[4] = {0.f, 0.f, 0.f, 0.f};
+            float bxh[4] = {0.f, 0.f, 0.f, 0.f}, bxl[4] = {0.f, 0.f, 0.f, 0.f};
             const double* ar = A + (roff + r) * noff;
             const double* br = B + (roff + r) * noff;
             for (int oi = 0; oi < noff; ++oi) {
                 const double a = ar[oi], b = br[oi];
                 if (a == 0.0 && b == 0.0) continue;
                 const double* xr = X + (roff + r + nbr_offset(oi, w0, w1, dim)) * ldx + cb;
+                if constexpr (DF) {
+                    float ah, al, bh, bl;
+                    split_f64(a, ah, al);
+                    split_f64(b, bh, bl);
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (cb + c < p) {
-                        const double v = xr[c];
-                        ax[c] += a * v;
-                        bx[c] += b * v;
-                    }
+                    for (int c = 0; c < 4; ++c)
+                        if (cb + c < p) {
+                            float vh, vl;
+                            split_f64(xr[c], vh, vl);
+                            df_fma(axh[c], axl[c], ah, al, vh, vl);
+                            df_fma(bxh[c], bxl[c], bh, bl, vh, vl);
+                        }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (cb + c < p) {
+                            const double v = xr[c];
+                            ax[c] += a * v;
+                            bx[c] += b * v;
+                        }
+                }
+            }
+            if constexpr (DF) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { ax[c] = df_to_f64(axh[c], axl[c]); bx[c] = df_to_f64(bxh[c], bxl[c]); }
             }
         }
         double* wr = W + (roff + r) * ldx + cb;
@@ -686,7 +729,13 @@ void apply_local(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const 
                  double* AX, double* BX, int ldx, int ncols, const int* skip, cudaStream_t s) {
     if (layout.P == 0) return;
     dim3 grid(64, layout.P);
-    k_apply_local<<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, ls.a.p, ls.b.p, X, AX, BX, ldx, ncols, skip);
+    // the chosen form (FP32 factors) takes the double-float products
+    if (layout.prec)
+        k_apply_local<true><<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, ls.a.p, ls.b.p, X, AX, BX, ldx, ncols,
+                                                 skip);
+    else
+        k_apply_local<false><<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, ls.a.p, ls.b.p, X, AX, BX, ldx, ncols,
+                                                  skip);
     MSDD_LAUNCH_CHECK();
 }
 
@@ -695,8 +744,12 @@ void apply_local_rhs(const LocalStencil& ls, const ProbBox* d_boxes, int dim, co
                      double* partial, int nblk_max, const int* done, cudaStream_t s) {
     if (layout.P == 0) return;
     dim3 grid(nblk_max, layout.P);
-    k_apply_rhs<<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, layout.d_K.p, ls.a.p, ls.b.p, X, W, ldx, d_p,
-                                     theta, sigma, partial, nblk_max, done);
+    if (layout.prec)
+        k_apply_rhs<true><<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, layout.d_K.p, ls.a.p, ls.b.p, X, W, ldx,
+                                               d_p, theta, sigma, partial, nblk_max, done);
+    else
+        k_apply_rhs<false><<<grid, 128, 0, s>>>(d_boxes, dim, layout.d_roff.p, layout.d_K.p, ls.a.p, ls.b.p, X, W, ldx,
+                                                d_p, theta, sigma, partial, nblk_max, done);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -111,6 +111,8 @@ struct LocalStencil {
 void build_local_stencil(const Geom& g, const ProbBox* d_boxes, const int* d_count, const TileBatch& layout,
                          LocalStencil& ls, cudaStream_t s);
 // AX = Abar X, BX = X Abar X from the stored stencils (same contract as apply_neumann).
+// With FP32 factors in `layout` (the chosen form) the products are accumulated
+// in double-float, as in apply_local_rhs.
 void apply_local(const LocalStencil& ls, const ProbBox* d_boxes, int dim, const TileBatch& layout, const double* X,
                  double* AX, double* BX, int ldx, int ncols, const int* skip, cudaStream_t s);
 // W = BX - (AX + sigma BX) diag(1 / (theta + sigma)) with AX, BX from the

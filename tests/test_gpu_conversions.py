@@ -4,7 +4,15 @@ bit for bit against CUDA's own conversions (__double2float_rn and the float
 to double widening) on edge values: signed zeros, infinities, NaN, rounding
 ties at every scale, the overflow threshold, the normal/subnormal boundary,
 subnormal results and inputs, and random bit patterns.  NaN results are
-compared as "both NaN"."""
+compared as "both NaN".
+
+Also the double-float helpers of the chosen form's Gram products: split_f64
+reconstructs x as hi + lo to 2^-47 relative (hi exact in FP32, |lo| <=
+2^-23 |hi|) inside its range and falls back to (f64_to_f32(x), 0) outside,
+and df_fma dot products of 1369 terms agree with the exact dot product (the
+products summed as fractions) to 1e-11 of the sum of |terms|: each step adds
+at most ~2^-46 of its product and the FP32 low-order sum grows by n 2^-24 of
+its size, so n 2^-47 ~ 1e-11 bounds the error (measured ~1e-13)."""
 import ctypes
 import os
 import subprocess
@@ -32,6 +40,9 @@ def probe(tmp_path_factory):
     lib = ctypes.CDLL(out)
     lib.conv_probe.restype = ctypes.c_int
     lib.conv_probe.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 4
+    lib.df_probe.restype = ctypes.c_int
+    lib.df_probe.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_int] * 2 + \
+        [ctypes.c_void_p]
     return lib
 
 
@@ -90,3 +101,34 @@ def test_conversions_match_cuda_bit_for_bit(probe):
     # the host's IEEE conversions agree as well (numpy rounds to nearest even)
     ref = xd.astype(np.float32)
     assert np.all((of.view(np.uint32) == ref.view(np.uint32)) | (np.isnan(of) & np.isnan(ref)))
+
+
+def test_double_float_split_and_dot(probe):
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    x = np.exp(rng.uniform(np.log(2.0 ** -59), np.log(2.0 ** 99), 20000)) * rng.choice([-1, 1], 20000)
+    x = np.concatenate([x, [0.0, -0.0, 1.0, -1.0, 2.0 ** -70, 3.0 ** 70, 1e-300, 1 + 2.0 ** -52]])
+    rows, L = 64, 1369
+    a = rng.standard_normal((rows, L)) * np.exp(rng.uniform(-20, 20, (rows, 1)))
+    b = rng.standard_normal((rows, L)) * np.exp(rng.uniform(-20, 20, (rows, 1)))
+    dev = "cuda"
+    tx, ta, tb = (torch.tensor(v, device=dev) for v in (x, a, b))
+    hi = torch.empty(len(x), dtype=torch.float32, device=dev)
+    lo = torch.empty(len(x), dtype=torch.float32, device=dev)
+    dot = torch.empty(rows, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    assert probe.df_probe(tx.data_ptr(), len(x), hi.data_ptr(), lo.data_ptr(), ta.data_ptr(), tb.data_ptr(), rows, L,
+                          dot.data_ptr()) == 0
+    hi, lo, dot = hi.cpu().numpy(), lo.cpu().numpy(), dot.cpu().numpy()
+    inside = (np.abs(x) >= 2.0 ** -60) & (np.abs(x) < 2.0 ** 101)
+    rec = hi.astype(np.float64) + lo.astype(np.float64)
+    assert np.all(np.abs(x - rec)[inside] <= 2.0 ** -47 * np.abs(x[inside]))
+    assert np.all(np.abs(lo[inside].astype(np.float64)) <= 2.0 ** -23 * np.abs(hi[inside].astype(np.float64)))
+    assert np.all(hi[~inside] == x[~inside].astype(np.float32)) and np.all(lo[~inside] == 0)
+    worst = 0.0
+    for r in range(rows):
+        exact = float(sum((Fraction(u) * Fraction(v) for u, v in zip(a[r], b[r])), Fraction(0)))
+        scale = float(np.sum(np.abs(a[r] * b[r])))
+        worst = max(worst, abs(dot[r] - exact) / scale)
+    print("double-float dot products: max error %.2e of the sum of |terms|" % worst)
+    assert worst <= 1e-11
