@@ -31,17 +31,18 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64, nominal (used only for "alu"-bound kernels)
 
 
-def measured_traffic(family):
+def measured_traffic(family, workload_name):
     """DRAM traffic of the family's kernel from the committed ncu summary
     (profiles/traffic.txt: key=value lines).  The figure holds only for the
-    kernel source it was captured from: null when that file's SHA-256 differs."""
+    workload and the kernel source it was captured from: absent for another
+    workload, null when the source file's SHA-256 differs."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
     except OSError:
         return {}
-    if kv.get("family") != family:
+    if kv.get("family") != family or kv.get("workload") != workload_name:
         return {}
     src = os.path.join(ROOT, kv.get("source", ""))
     try:
@@ -514,7 +515,7 @@ def run_ours(args, rank, world, local_rank):
                  "traffic": None,
                  # the family's time per timed step over the step's time
                  "share_of_step": round((pf["ms"] / 1e3 / args.steps) / (total / args.steps), 4)})
-    roof.update(measured_traffic(fam))
+    roof.update(measured_traffic(fam, w.name))
 
     # the CPU oracle: one full step on all host cores, after all GPU work
     cpu = None

@@ -1,5 +1,6 @@
 // Coarse-level assembly, batched small GEMMs and preconditioner vector kernels.
 #include "coarse.cuh"
+#include "pcg.cuh"
 
 namespace msdd {
 
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(COMBINE_NT, 1) k_fine_combine(
     const double* __restrict__ y, const double* __restrict__ Phi, const long long* __restrict__ phioff, int ldphi,
     const int* __restrict__ m_, const long long* __restrict__ c1off, const double* __restrict__ z1,
     double* __restrict__ z, const double* __restrict__ r, double* __restrict__ partial, long long nun,
-    const int* __restrict__ done, int mode) {
+    const int* __restrict__ done, int mode, PcgScalars* sc, int fin) {
     __shared__ double red[COMBINE_NT];
     if (done && *done) return;
     double part = 0.0;
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(COMBINE_NT, 1) k_fine_combine(
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (sc) pcg_last_block(sc, fin, partial);
 }
 
 __global__ void k_segment_copy(const long long* __restrict__ so, const long long* __restrict__ dof,
@@ -311,22 +313,23 @@ void fine_gather_restrict(const Geom& g, const ProbBox* d_fine, const long long*
 void fine_combine(const Geom& g, const CombineMaps& cm, const ProbBox* d_fine, const long long* d_droff,
                   const double* y, const double* Phi, const long long* d_phioff, int ldphi, const int* d_m,
                   const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
-                  int nblocks, const int* done, cudaStream_t s) {
+                  int nblocks, const int* done, cudaStream_t s, PcgScalars* sc, int fin) {
     fine_combine_mode(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off, z1, z, r, partial, nblocks, done,
-                      COMB_Y | COMB_COARSE, s);
+                      COMB_Y | COMB_COARSE, s, sc, fin);
 }
 
 void fine_combine_mode(const Geom& g, const CombineMaps& cm, const ProbBox* d_fine, const long long* d_droff,
                        const double* y, const double* Phi, const long long* d_phioff, int ldphi, const int* d_m,
                        const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
-                       int nblocks, const int* done, int mode, cudaStream_t s) {
+                       int nblocks, const int* done, int mode, cudaStream_t s, PcgScalars* sc, int fin) {
     long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
+    if (!partial) sc = nullptr;                      // no partials, nothing to finish
     if (g.dim == 3)
         k_fine_combine<3><<<nblocks, COMBINE_NT, 0, s>>>(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off,
-                                                         z1, z, r, partial, nun, done, mode);
+                                                         z1, z, r, partial, nun, done, mode, sc, fin);
     else
         k_fine_combine<2><<<nblocks, COMBINE_NT, 0, s>>>(g, cm, d_fine, d_droff, y, Phi, d_phioff, ldphi, d_m, d_c1off,
-                                                         z1, z, r, partial, nun, done, mode);
+                                                         z1, z, r, partial, nun, done, mode, sc, fin);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -58,7 +58,7 @@ struct CombineMaps {
 void fine_combine(const Geom& g, const CombineMaps& cm, const ProbBox* d_fine, const long long* d_droff,
                   const double* y, const double* Phi, const long long* d_phioff, int ldphi, const int* d_m,
                   const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
-                  int nblocks, const int* done, cudaStream_t s);
+                  int nblocks, const int* done, cudaStream_t s, struct PcgScalars* sc = nullptr, int fin = 0);
 // Modes of the combine: COMB_Y the fine local solutions, COMB_COARSE the
 // prolongation Phi z1, COMB_RAS the local solutions weighted by chi = 1/N(x)
 // (restricted additive Schwarz), COMB_ACC adds to z; partial (z . r per
@@ -67,7 +67,8 @@ constexpr int COMB_Y = 1, COMB_COARSE = 2, COMB_RAS = 4, COMB_ACC = 8;
 void fine_combine_mode(const Geom& g, const CombineMaps& cm, const ProbBox* d_fine, const long long* d_droff,
                        const double* y, const double* Phi, const long long* d_phioff, int ldphi, const int* d_m,
                        const long long* d_c1off, const double* z1, double* z, const double* r, double* partial,
-                       int nblocks, const int* done, int mode, cudaStream_t s);
+                       int nblocks, const int* done, int mode, cudaStream_t s, struct PcgScalars* sc = nullptr,
+                       int fin = 0);
 
 // out[dst_off[i] + k] (+)= in[src_off[i] + k] for k < len[i]; mode 0: copy, 1: add.
 void segment_copy(const long long* d_src_off, const long long* d_dst_off, const int* d_len, int P, int maxlen,

@@ -1101,7 +1101,9 @@ __global__ void k_cholqr(const double* __restrict__ Gp, int gsplit, double* __re
     const int p = p_[i];
     const int t = threadIdx.x;
     const double* Gi = Gp + (long long)i * gsplit * PMAX * PMAX;
-    for (int e = t; e < PMAX * PMAX; e += 32) {       // G = sum of the row-range partials
+    // G = sum of the row-range partials, by the whole block (their loads are
+    // the long part); the factorisation below is one warp's
+    for (int e = t; e < PMAX * PMAX; e += blockDim.x) {
         int a = e / PMAX, b = e % PMAX;
         float g = 0.f;
         if (a < p && b < p)
@@ -1109,7 +1111,8 @@ __global__ void k_cholqr(const double* __restrict__ Gp, int gsplit, double* __re
         R[a][b] = g;
         Ri[a][b] = 0.f;
     }
-    __syncwarp();
+    __syncthreads();
+    if (t >= 32) return;
     if (t < PMAX) {
         const float g = t < p ? R[t][t] : 0.f;
         d[t] = g > 0.f ? rsqrt_f32(g) : 0.f;
@@ -1275,8 +1278,9 @@ void GevpBatch::alloc(cudaStream_t s) {
     for (DevBuf<double>* b : {&X, &AX, &BX, &Y, &AY, &BY, &W}) { b->alloc(rows * ldx); b->zero(s); }
     H.alloc((size_t)P * PMAX * PMAX);
     M.alloc((size_t)P * PMAX * PMAX);
-    // row splits: about 1024 CTAs in total, at least 64 rows per split
-    gsplit = (int)std::max<long long>(1, std::min<long long>(ceil_div(1024, std::max(P, 1)),
+    // row splits: about 2048 CTAs in total, at least 64 rows per split (the
+    // double-float Gram waits on its staging loads: more CTAs hide that)
+    gsplit = (int)std::max<long long>(1, std::min<long long>(ceil_div(2048, std::max(P, 1)),
                                                                  ceil_div((long long)K.max_K * NB, 64)));
     Hp.alloc((size_t)P * gsplit * PMAX * PMAX);
     Mp.alloc((size_t)P * gsplit * PMAX * PMAX);
@@ -1367,7 +1371,7 @@ void eig_check_knorm(GevpBatch& g, const EigParams& ep, int it, cudaStream_t s) 
 void eig_cholqr32(GevpBatch& g, cudaStream_t s) {
     k_gram32<<<dim3(g.P, g.gsplit), TPB, 0, s>>>(g.W.p, g.Hp.p, g.K.d_n.p, g.K.d_roff.p, g.d_p.p, g.ldx, g.gsplit);
     MSDD_LAUNCH_CHECK();
-    k_cholqr<<<g.P, 32, 0, s>>>(g.Hp.p, g.gsplit, g.C.p, g.d_p.p);
+    k_cholqr<<<g.P, 256, 0, s>>>(g.Hp.p, g.gsplit, g.C.p, g.d_p.p);
     MSDD_LAUNCH_CHECK();
     dim3 grid(g.nblk_max, g.P);
     k_update32<<<grid, TPB, 0, s>>>(g.W.p, g.X.p, g.C.p, g.K.d_n.p, g.K.d_K.p, g.K.d_roff.p, g.d_p.p, g.ldx);

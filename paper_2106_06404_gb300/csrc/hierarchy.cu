@@ -1148,7 +1148,7 @@ void Hierarchy::build_coarse() {
     stats.phase_ms[6] = ms_since(t0);
 }
 
-void Hierarchy::apply_prec(const double* rr, double* zz, const int* gdone) {
+void Hierarchy::apply_prec(const double* rr, double* zz, const int* gdone, PcgScalars* fin_sc) {
     double* r1 = levels == 2 ? r0buf.p : v1.p;
     fine_gather_restrict(g, d_fboxes.p, fdir.d_roff.p, fdir.d_K.p, rr, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p,
                          d_c1off.p, r1, Pf, gdone, st);
@@ -1170,7 +1170,7 @@ void Hierarchy::apply_prec(const double* rr, double* zz, const int* gdone) {
     tile_solve(fdir, frhs.p, 1, 1, nullptr, st, gdone);
     MSDD_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
     fine_combine(g, cmaps, d_fboxes.p, fdir.d_roff.p, frhs.p, Phi.p, d_phioff.p, ldphi, d_fm.p, d_c1off.p, zc, zz,
-                 rr, partial.p, nblocks, gdone, st);
+                 rr, partial.p, nblocks, gdone, st, fin_sc, fin_sc ? PCG_FIN_BETA : PCG_FIN_NONE);
 }
 
 void Hierarchy::build_graph() {
@@ -1180,12 +1180,11 @@ void Hierarchy::build_graph() {
     MSDD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const int* gd = &sc.p->done;
     for (int k = 0; k < chunk; ++k) {
-        spmv_stencil_dot(g, stencil.p, p.p, q.p, partial.p, nblocks, gd, st);
-        pcg_fin_alpha(sc.p, partial.p, nblocks, st);
-        pcg_axpy(sc.p, x.p, r.p, p.p, q.p, nun, partial.p, nblocks, st);
-        pcg_fin_rr(sc.p, partial.p, nblocks, st);
-        apply_prec(r.p, z.p, gd);
-        pcg_fin_beta(sc.p, partial.p, nblocks, st);
+        // the finishing steps (alpha, the r.r test, beta) run in the last
+        // block of the kernel that produced their partial sums
+        spmv_stencil_dot(g, stencil.p, p.p, q.p, partial.p, nblocks, gd, st, sc.p, PCG_FIN_ALPHA);
+        pcg_axpy(sc.p, x.p, r.p, p.p, q.p, nun, partial.p, nblocks, st, true);
+        apply_prec(r.p, z.p, gd, sc.p);
         pcg_update_p(sc.p, z.p, p.p, nun, st);
     }
     MSDD_CUDA(cudaStreamEndCapture(st, &gr));

@@ -161,7 +161,8 @@ struct Hierarchy {
 
     ~Hierarchy();
     void setup(const msdd_mesh& mesh, const msdd_coeff& coeff);
-    void apply_prec(const double* rr, double* zz, const int* gdone);
+    // fin_sc: the CG scalars whose beta step the final combine applies (PCG)
+    void apply_prec(const double* rr, double* zz, const int* gdone, PcgScalars* fin_sc = nullptr);
     int solve(const double* b, double tol, int maxit, double* xout, double* relres);
     // hybrid form (multiplicative over levels, restricted additive Schwarz on
     // the fine level) and right-preconditioned GMRES with it (Section 5)

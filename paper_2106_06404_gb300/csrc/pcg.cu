@@ -58,16 +58,13 @@ __global__ void k_copy(const double* __restrict__ z, double* __restrict__ p, lon
 __global__ void k_fin_alpha(PcgScalars* sc, const double* __restrict__ partial, int nblocks) {
     if (sc->done) return;
     double v = sum_partials(partial, nblocks);
-    if (threadIdx.x == 0) {
-        sc->pq = v;
-        if (!(v > 0.0)) { sc->done = 3; sc->alpha = 0.0; }
-        else sc->alpha = sc->rho / v;
-    }
+    if (threadIdx.x == 0) pcg_fin_apply(sc, PCG_FIN_ALPHA, v);
 }
 
-__global__ void __launch_bounds__(1024) k_axpy(const PcgScalars* sc, double* __restrict__ x, double* __restrict__ r,
+// fin = PCG_FIN_RR: the last block applies the r.r test itself
+__global__ void __launch_bounds__(1024) k_axpy(PcgScalars* sc, double* __restrict__ x, double* __restrict__ r,
                        const double* __restrict__ p, const double* __restrict__ q, long long n,
-                       double* __restrict__ partial) {
+                       double* __restrict__ partial, int fin) {
     __shared__ double red[1024];
     if (sc->done) return;
     const double a = sc->alpha;
@@ -85,27 +82,19 @@ __global__ void __launch_bounds__(1024) k_axpy(const PcgScalars* sc, double* __r
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (fin) pcg_last_block(sc, fin, partial);
 }
 
 __global__ void k_fin_rr(PcgScalars* sc, const double* __restrict__ partial, int nblocks) {
     if (sc->done) return;
     double v = sum_partials(partial, nblocks);
-    if (threadIdx.x == 0) {
-        sc->rr = v;
-        sc->iters += 1;
-        if (v < sc->tol2 * sc->bb) sc->done = 1;
-        else if (sc->iters >= sc->maxit) sc->done = 2;
-    }
+    if (threadIdx.x == 0) pcg_fin_apply(sc, PCG_FIN_RR, v);
 }
 
 __global__ void k_fin_beta(PcgScalars* sc, const double* __restrict__ partial, int nblocks) {
     if (sc->done) return;
     double v = sum_partials(partial, nblocks);
-    if (threadIdx.x == 0) {
-        sc->rz = v;
-        sc->beta = v / sc->rho;
-        sc->rho = v;
-    }
+    if (threadIdx.x == 0) pcg_fin_apply(sc, PCG_FIN_BETA, v);
 }
 
 __global__ void k_update_p(const PcgScalars* sc, const double* __restrict__ z, double* __restrict__ p, long long n) {
@@ -270,8 +259,8 @@ void pcg_fin_alpha(PcgScalars* sc, const double* partial, int nblocks, cudaStrea
     MSDD_LAUNCH_CHECK();
 }
 void pcg_axpy(PcgScalars* sc, double* x, double* r, const double* p, const double* q, long long n, double* partial,
-              int nblocks, cudaStream_t s) {
-    k_axpy<<<nblocks, 1024, 0, s>>>(sc, x, r, p, q, n, partial);
+              int nblocks, cudaStream_t s, bool fuse_rr) {
+    k_axpy<<<nblocks, 1024, 0, s>>>(sc, x, r, p, q, n, partial, fuse_rr ? PCG_FIN_RR : PCG_FIN_NONE);
     MSDD_LAUNCH_CHECK();
 }
 void pcg_fin_rr(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s) {

@@ -15,7 +15,54 @@ struct PcgScalars {
     int iters;
     int maxit;
     int pad;
+    unsigned ticket;   // blocks of a fused producer kernel that stored their partial (reset by the last)
+    unsigned pad2;
 };
+
+// Finishing steps of a CG iteration that a producer kernel can apply itself
+// (its last block to finish sums the block partials): alpha = rho / p.q,
+// the r.r convergence test, beta = r.z / rho.
+enum PcgFin { PCG_FIN_NONE = 0, PCG_FIN_ALPHA = 1, PCG_FIN_RR = 2, PCG_FIN_BETA = 3 };
+
+#ifdef __CUDACC__
+// the scalar updates of the finishing steps, given the summed partials v
+__device__ __forceinline__ void pcg_fin_apply(PcgScalars* sc, int fin, double v) {
+    if (fin == PCG_FIN_ALPHA) {
+        sc->pq = v;
+        if (!(v > 0.0)) { sc->done = 3; sc->alpha = 0.0; }
+        else sc->alpha = sc->rho / v;
+    } else if (fin == PCG_FIN_RR) {
+        sc->rr = v;
+        sc->iters += 1;
+        if (v < sc->tol2 * sc->bb) sc->done = 1;
+        else if (sc->iters >= sc->maxit) sc->done = 2;
+    } else if (fin == PCG_FIN_BETA) {
+        sc->rz = v;
+        sc->beta = v / sc->rho;
+        sc->rho = v;
+    }
+}
+// Called by every thread of every block once thread 0 has stored
+// partial[blockIdx.x]: the last block to arrive sums the gridDim.x partials
+// (one warp, lane-strided then a fixed shuffle tree, the order of the
+// separate finishing kernels) and applies `fin`.
+__device__ __forceinline__ void pcg_last_block(PcgScalars* sc, int fin, const double* partial) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double v = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) v += __ldcg(partial + k);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+        pcg_fin_apply(sc, fin, v);
+        sc->ticket = 0u;
+    }
+}
+#endif
 
 // r = b, x = 0, partial sums of b.b
 void pcg_start(const double* b, double* x, double* r, long long n, double* partial, int nblocks, cudaStream_t s);
@@ -26,9 +73,10 @@ void pcg_fin_rho0(PcgScalars* sc, const double* partial, int nblocks, const doub
                   cudaStream_t s);
 // alpha = rho / sum(partial)
 void pcg_fin_alpha(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
-// x += alpha p, r -= alpha q, partial sums of r.r
+// x += alpha p, r -= alpha q, partial sums of r.r (fuse_rr: and the r.r
+// test of pcg_fin_rr, applied by the kernel's last block)
 void pcg_axpy(PcgScalars* sc, double* x, double* r, const double* p, const double* q, long long n, double* partial,
-              int nblocks, cudaStream_t s);
+              int nblocks, cudaStream_t s, bool fuse_rr = false);
 // rr = sum(partial); iters += 1; convergence / maxit test
 void pcg_fin_rr(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
 // beta = sum(partial) / rho; rho = sum(partial)

@@ -1,5 +1,6 @@
 // Q1 assembly and matrix-free operators on the structured mesh.
 #include "q1.cuh"
+#include "pcg.cuh"
 
 #include <cstring>
 #include <mutex>
@@ -587,7 +588,7 @@ template <int D>
 __global__ void __launch_bounds__(1024) k_spmv_stencil_dot(Geom g, const double* __restrict__ S,
                                                            const double* __restrict__ p, double* __restrict__ q,
                                                            long long nun, double* __restrict__ partial,
-                                                           const int* __restrict__ done) {
+                                                           const int* __restrict__ done, PcgScalars* sc, int fin) {
     __shared__ double red[1024];
     if (done && *done) return;
     constexpr int NOFF = D == 3 ? 27 : 9;
@@ -612,6 +613,7 @@ __global__ void __launch_bounds__(1024) k_spmv_stencil_dot(Geom g, const double*
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (sc) pcg_last_block(sc, fin, partial);
 }
 
 __global__ void k_apply_global(Geom g, const double* __restrict__ x, double* __restrict__ y, long long nun) {
@@ -769,12 +771,12 @@ void global_stencil(const Geom& g, double* S, cudaStream_t s) {
 }
 
 void spmv_stencil_dot(const Geom& g, const double* S, const double* p, double* q, double* partial, int nblocks,
-                      const int* done, cudaStream_t s) {
+                      const int* done, cudaStream_t s, PcgScalars* sc, int fin) {
     long long nun = (long long)g.ushape[0] * g.ushape[1] * (g.dim == 3 ? g.ushape[2] : 1);
     if (g.dim == 3)
-        k_spmv_stencil_dot<3><<<nblocks, 1024, 0, s>>>(g, S, p, q, nun, partial, done);
+        k_spmv_stencil_dot<3><<<nblocks, 1024, 0, s>>>(g, S, p, q, nun, partial, done, sc, fin);
     else
-        k_spmv_stencil_dot<2><<<nblocks, 1024, 0, s>>>(g, S, p, q, nun, partial, done);
+        k_spmv_stencil_dot<2><<<nblocks, 1024, 0, s>>>(g, S, p, q, nun, partial, done, sc, fin);
     MSDD_LAUNCH_CHECK();
 }
 

@@ -131,8 +131,10 @@ void apply_local_b32(const LocalStencil& ls, const ProbBox* d_boxes, int dim, co
 // not an unknown.  n * 3^d doubles.
 void global_stencil(const Geom& g, double* S, cudaStream_t s);
 // q = A p from the stored stencil and partial sums of p.q (nblocks CTAs).
+// (sc != NULL: the kernel's last block also applies the finishing step `fin`
+// of PcgFin to the summed partials, e.g. alpha = rho / p.q.)
 void spmv_stencil_dot(const Geom& g, const double* S, const double* p, double* q, double* partial, int nblocks,
-                      const int* done, cudaStream_t s);
+                      const int* done, cudaStream_t s, struct PcgScalars* sc = nullptr, int fin = 0);
 
 // y = A x on the unknowns (Dirichlet nodes eliminated).
 void apply_global(const Geom& g, const double* x, double* y, cudaStream_t s);
