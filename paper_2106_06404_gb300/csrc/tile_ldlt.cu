@@ -1534,7 +1534,7 @@ __device__ __forceinline__ void ws_col_product(const float* tile, const float* V
 // Wide-band forms of the two products: the loads are volatile shared
 // loads issued eight k at a time ahead of their products (the compiler keeps
 // their order), with two partial sums per column.  With 13 tiles a step the
-// products dominate and this ordering is ~12% faster; with 3 tiles the
+// products dominate and this ordering is 2-12% faster; with 3 tiles the
 // plain forms above are.
 __device__ __forceinline__ float4 lds4_ordered(const float* p) {
     float4 r;
@@ -1548,11 +1548,19 @@ __device__ __forceinline__ float lds1_ordered(const float* p) {
     asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(r) : "r"(smem_u32(p)));
     return r;
 }
+__device__ __forceinline__ float2 lds2_ordered(const float* p) {
+    float2 r;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(r.x), "=f"(r.y) : "r"(smem_u32(p)));
+    return r;
+}
 template <int C>
 __device__ __forceinline__ void ws_ld_ordered(const float* p, float (&v)[C]) {
     if constexpr (C == 4) {
         const float4 x = lds4_ordered(p);
         v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if constexpr (C == 2) {
+        const float2 x = lds2_ordered(p);
+        v[0] = x.x; v[1] = x.y;
     } else {
         ws_ld<C>(p, v);
     }
@@ -1612,7 +1620,7 @@ __device__ __forceinline__ void ws_col_product_wide(const float* tile, const flo
     for (int c = 0; c < C; ++c) acc[c] = a0[c] + a1[c];
 }
 // the form a configuration uses: ordered for wide bands (more than 2 tiles)
-// and four columns a warp, the configuration that was measured
+// with 2 or 4 columns a warp (the configurations that were measured)
 template <bool WIDE, int C, int K0, int K1, int SIGN>
 __device__ __forceinline__ void ws_rowp(const float* tile, const float* V, int lane, float (&acc)[C]) {
     if constexpr (WIDE) ws_row_product_wide<C, K0, K1, SIGN>(tile, V, lane, acc);
@@ -1630,6 +1638,10 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
 
 template <int KBP, int W, int C, int NST, int XD>
 struct BandWs {
+    // The backward sweep's first right-hand side read from X (block K-1-S,
+    // written by forward step K-1-S) is issued XD - 1 steps ahead, at step
+    // K - XD + 1: it must come after that write, so XD <= S + 1 = KBP + 2.
+    static_assert(XD <= KBP + 2, "X prefetch deeper than the solution ring allows");
     static constexpr int SLOTS = KBP + 1;            // tiles per step; also the solution ring per warp
     static constexpr int NT = 32 * (W + 1);
     static constexpr int COLS = W * C;
@@ -1782,15 +1794,15 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
                 if (fwd) {
                     // acc -= L_{R,o}[lane][k] z_o[k]; nonzero only for k >= 32 d - b
                     const int k0 = NB * d - bw;
-                    if (k0 >= 24) ws_rowp<(KBP > 2 && C == 4), C, 24, 32, -1>(L, Z, lane, acc);
-                    else if (k0 >= 16) ws_rowp<(KBP > 2 && C == 4), C, 16, 32, -1>(L, Z, lane, acc);
-                    else ws_rowp<(KBP > 2 && C == 4), C, 0, 32, -1>(L, Z, lane, acc);
+                    if (k0 >= 24) ws_rowp<(KBP > 2 && C >= 2), C, 24, 32, -1>(L, Z, lane, acc);
+                    else if (k0 >= 16) ws_rowp<(KBP > 2 && C >= 2), C, 16, 32, -1>(L, Z, lane, acc);
+                    else ws_rowp<(KBP > 2 && C >= 2), C, 0, 32, -1>(L, Z, lane, acc);
                 } else {
                     // acc -= L_{o,R}[k][lane] x_o[k]; nonzero only for k <= b - 32 d + 31
                     const int kend = bw - NB * d + NB;
-                    if (kend <= 8) ws_colp<(KBP > 2 && C == 4), C, 8, -1>(L, Z, lane, acc);
-                    else if (kend <= 16) ws_colp<(KBP > 2 && C == 4), C, 16, -1>(L, Z, lane, acc);
-                    else ws_colp<(KBP > 2 && C == 4), C, 32, -1>(L, Z, lane, acc);
+                    if (kend <= 8) ws_colp<(KBP > 2 && C >= 2), C, 8, -1>(L, Z, lane, acc);
+                    else if (kend <= 16) ws_colp<(KBP > 2 && C >= 2), C, 16, -1>(L, Z, lane, acc);
+                    else ws_colp<(KBP > 2 && C >= 2), C, 32, -1>(L, Z, lane, acc);
                 }
             }
             ws_st<C>(Acc + lane * C, acc);
@@ -1799,8 +1811,8 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_tile_solve_band_ws(
             float out[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) out[c] = 0.f;
-            if (fwd) ws_rowp<(KBP > 2 && C == 4), C, 0, 32, 1>(T, Acc, lane, out);
-            else ws_colp<(KBP > 2 && C == 4), C, 32, 1>(T, Acc, lane, out);
+            if (fwd) ws_rowp<(KBP > 2 && C >= 2), C, 0, 32, 1>(T, Acc, lane, out);
+            else ws_colp<(KBP > 2 && C >= 2), C, 32, 1>(T, Acc, lane, out);
             __syncwarp();                                   // Acc reads done before the next step's writes
             ws_st<C>(Zr + ((size_t)(R % S) * NB + lane) * C, out);
             double* xw = X + (roff + (long long)R * NB + lane) * ldx;
@@ -2135,12 +2147,17 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
     const bool aligned = ldx % 2 == 0 && ((uintptr_t)X % 16) == 0;
     const CUtensorMap* tm = tb.prec && aligned && ncols <= NB ? tile_tensor_map(tb) : nullptr;
     if (tm && maxkb <= 2) {
+        // 16 columns in 4 warps of 4, 6 stages.  8 warps of 2 with 3 stages
+        // is 9% faster on its own (129 vs 139 us a launch) but no faster in
+        // the set-up, where the other half's kernels share the SMs
         launch_band_ws<2, 4, 4, 6, 4>(tb, *tm, X, ldx, ncols, skip, s, gdone);
         return;
     }
     if (tm && maxkb <= 12) {
-        // wide bands (3D boxes): 20 columns per CTA in 5 warps, 3 stages of 13 tiles
-        launch_band_ws<12, 5, 4, 3, 4>(tb, *tm, X, ldx, ncols, skip, s, gdone);
+        // wide bands (3D boxes): 20 columns per CTA in 10 warps of 2, 2 stages
+        // of 13 tiles (17% faster than 5 warps of 4 with 3 stages: the smaller
+        // shared-memory carve-out leaves L1 to the right-hand-side rows)
+        launch_band_ws<12, 10, 2, 2, 4>(tb, *tm, X, ldx, ncols, skip, s, gdone);
         return;
     }
     if (maxkb <= 2 && ncols <= NB && aligned) {
