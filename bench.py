@@ -513,8 +513,9 @@ def run_ours(args, rank, world, local_rank):
                  "arith_intensity_flop_per_byte": round(intensity, 3),
                  "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
                  "traffic": None,
-                 # the family's time per timed step over the step's time
-                 "share_of_step": round((pf["ms"] / 1e3 / args.steps) / (total / args.steps), 4)})
+                 # pf holds the family times of one step (the last timed step's
+                 # hierarchy): that time over the mean step time
+                 "share_of_step": round((pf["ms"] / 1e3) / (total / args.steps), 4)})
     roof.update(measured_traffic(fam, w.name))
 
     # the CPU oracle: one full step on all host cores, after all GPU work
@@ -537,7 +538,7 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 outer / f32 fine factors",
+        "dtype": "f64 outer / f32 fine factors and solves / double-f32 fine Gram, apply, update",
         "data": "synthetic (seeded GRF x channels/inclusions, contrast 1e6)",
         "config": workload_config(w, n, world),
         "iterations": it_chosen[-1],
@@ -649,7 +650,7 @@ def run_batch(args):
     line = {
         "metric": METRIC, "value": round(statistics.mean(t1), 6), "unit": "s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t1), 3), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 fine factors",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 fine factors and solves / double-f32 fine Gram, apply, update",
         "data": "synthetic (batch recipe: seeded sides 128-384, 4x4-12x12 subdomains, log-normal x channels 1e4-1e6)",
         "config": {"workload": "batch2d_%dproblems" % len(ws), "problems": len(ws), "unknowns": n_unknowns,
                    "levels": 2, "nev_max": ws[0].nev_max, "eta": ws[0].eta, "tol": TOL, "form": "chosen (precision=1)",
