@@ -195,3 +195,34 @@ def test_status_names_match_header_enum():
     from paper_2106_06404_gb300 import msdd
     assert enum == msdd.STATUS_NAMES
     assert enum[-8] == "MSDD_ERR_TIMEOUT"
+
+
+def _batch_call(lib, msdd, meshes, coeffs, decs, spec, opt, nworkers=2, tol=1e-8, maxit=100, bptr=0x3000):
+    k = len(meshes)
+    M, C, D = (msdd.Mesh * k)(*meshes), (msdd.Coeff * k)(*coeffs), (msdd.Decomp * k)(*decs)
+    bp = (ctypes.c_void_p * k)(*([bptr] * k))
+    xp = (ctypes.c_void_p * k)(*([0x4000] * k))
+    st = (ctypes.c_int * k)()
+    return lib.msdd_batch_run(k, M, C, D, ctypes.byref(spec), ctypes.byref(opt), bp, tol, maxit, xp, nworkers, None,
+                              None, st, None, None)
+
+
+def test_batch_run_rejects_invalid_problems_before_device_work(lib):
+    """msdd_batch_run checks every problem (naming it) and the shared element
+    shape before it touches the device: these calls need no GPU."""
+    from paper_2106_06404_gb300 import msdd
+    mesh, coeff, dec, spec, opt = _setup_args(msdd)
+    # a problem whose decomposition is invalid: named by its index
+    bad = msdd.Decomp()
+    ctypes.memmove(ctypes.byref(bad), ctypes.byref(dec), ctypes.sizeof(dec))
+    bad.overlap = 0
+    assert _batch_call(lib, msdd, [mesh, mesh], [coeff, coeff], [dec, bad], spec, opt) == -1
+    assert b"problem 1" in lib.msdd_last_error() and b"overlap" in lib.msdd_last_error()
+    # elements of another shape (32 x 16 elements on the unit square) cannot share the reference matrices
+    other = msdd.make_mesh((32, 16), 0b1)
+    assert _batch_call(lib, msdd, [mesh, other], [coeff, coeff], [dec, dec], spec, opt) == -7
+    assert b"problem 1" in lib.msdd_last_error() and b"one shape" in lib.msdd_last_error()
+    # NULL right-hand side, no worker, a non-positive tolerance
+    assert _batch_call(lib, msdd, [mesh], [coeff], [dec], spec, opt, bptr=0) == -1
+    assert _batch_call(lib, msdd, [mesh], [coeff], [dec], spec, opt, nworkers=0) == -1
+    assert _batch_call(lib, msdd, [mesh], [coeff], [dec], spec, opt, tol=0.0) == -1
