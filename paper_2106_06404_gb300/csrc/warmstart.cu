@@ -57,19 +57,48 @@ __global__ void __launch_bounds__(256) k_nn_patch(Geom g, const ProbBox* __restr
 
 // ---- C[M][N] = epilogue(sum_k A(m,k) B(n,k)); A(m,k) = TA ? A[k lda + m] : A[m lda + k],
 // B(n,k) = TB ? B[k ldb + n] : B[n ldb + k]; RB rounds B to bfloat16 (weights);
-// EPI: 0 store, 1 add bias[n].  64 x 64 tile per CTA, 4 x 4 outputs per thread.
+// EPI: 0 store, 1 add bias[n].
+//
+// BF16 tensor cores (mma.m16n8k16, FP32 accumulate).  An FP32 operand is
+// split into three bfloat16 terms x = h + m + l (each the round-to-nearest
+// of what the previous ones leave; together the 24 significand bits), so a
+// product with a bfloat16 weight is formed exactly from three mma (h, m, l
+// against the weight) and the arithmetic is that of FP32 products with the
+// BF16-rounded weights.  Two FP32 operands (the weight gradients) take the
+// six terms with index sum <= 2 (the rest are below 2^-24 of the product).
+// 64 x 64 tile per CTA, 8 warps of 32 x 16 (2 x 2 mma tiles), k-steps of 16
+// staged in shared memory as FP32.
+__device__ __forceinline__ void bf16_split3(float x, unsigned (&t)[3]) {
+    const float h = bf16_rne(x);
+    const float r1 = __fsub_rn(x, h);
+    const float m = bf16_rne(r1);
+    const float l = bf16_rne(__fsub_rn(r1, m));
+    t[0] = __float_as_uint(h) >> 16;
+    t[1] = __float_as_uint(m) >> 16;
+    t[2] = __float_as_uint(l) >> 16;
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 template <bool TA, bool TB, bool RB, int EPI>
 __global__ void __launch_bounds__(256) k_nn_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
                                                  const float* __restrict__ B, int ldb, const float* __restrict__ bias,
                                                  float* __restrict__ C, int ldc) {
     __shared__ float As[16][65], Bs[16][65];
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    const int t = threadIdx.x, tm = t >> 4, tn = t & 15;
-    float acc[4][4];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
+    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 16;       // this warp's 32 x 16 block of the tile
+    float acc[2][2][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+    constexpr int NB_TERMS = RB ? 1 : 3;
     for (int k0 = 0; k0 < K; k0 += 16) {
         for (int e = t; e < 16 * 64; e += 256) {
             const int kk = TA ? e / 64 : e % 16, mm = TA ? e % 64 : e / 16;
@@ -81,33 +110,73 @@ __global__ void __launch_bounds__(256) k_nn_gemm(int M, int N, int K, const floa
             Bs[kb][nb] = RB ? bf16_rne(bv) : bv;
         }
         __syncthreads();
+        // fragments: A (16 x 16): (g, 2q..2q+1), (g + 8, ..), (g, 2q + 8..), (g + 8, 2q + 8..);
+        // B (16 x 8): k 2q..2q+1 and 2q + 8..2q + 9 of column g; two bfloat16 a register, low = first
+        unsigned af[2][3][4], bfr[2][3][2];
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float av[4], bv[4];
+        for (int i = 0; i < 2; ++i) {
+            const int r = wm + 16 * i + g;
+            const int rows[4] = {r, r + 8, r, r + 8}, ks[4] = {2 * q, 2 * q, 2 * q + 8, 2 * q + 8};
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][tm + 16 * a];
+            for (int v = 0; v < 4; ++v) {
+                unsigned lo[3], hi[3];
+                bf16_split3(As[ks[v]][rows[v]], lo);
+                bf16_split3(As[ks[v] + 1][rows[v]], hi);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tn + 16 * c];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[a][c] += av[a] * bv[c];
+                for (int z = 0; z < 3; ++z) af[i][z][v] = lo[z] | (hi[z] << 16);
+            }
         }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int c = wn + 8 * j + g;
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int kb = 2 * q + 8 * v;
+                unsigned lo[3], hi[3];
+                if (RB) {
+                    lo[0] = __float_as_uint(Bs[kb][c]) >> 16;       // already bfloat16
+                    hi[0] = __float_as_uint(Bs[kb + 1][c]) >> 16;
+                } else {
+                    bf16_split3(Bs[kb][c], lo);
+                    bf16_split3(Bs[kb + 1][c], hi);
+                }
+#pragma unroll
+                for (int z = 0; z < NB_TERMS; ++z) bfr[j][z][v] = lo[z] | (hi[z] << 16);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (RB) {
+                    // smallest terms first
+                    mma_bf16(acc[i][j], af[i][2], bfr[j][0][0], bfr[j][0][1]);
+                    mma_bf16(acc[i][j], af[i][1], bfr[j][0][0], bfr[j][0][1]);
+                    mma_bf16(acc[i][j], af[i][0], bfr[j][0][0], bfr[j][0][1]);
+                } else {
+                    mma_bf16(acc[i][j], af[i][2], bfr[j][0][0], bfr[j][0][1]);
+                    mma_bf16(acc[i][j], af[i][1], bfr[j][1][0], bfr[j][1][1]);
+                    mma_bf16(acc[i][j], af[i][0], bfr[j][2][0], bfr[j][2][1]);
+                    mma_bf16(acc[i][j], af[i][1], bfr[j][0][0], bfr[j][0][1]);
+                    mma_bf16(acc[i][j], af[i][0], bfr[j][1][0], bfr[j][1][1]);
+                    mma_bf16(acc[i][j], af[i][0], bfr[j][0][0], bfr[j][0][1]);
+                }
+            }
         __syncthreads();
     }
+    // C fragments: (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1) of each 16 x 8 tile
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int m = m0 + tm + 16 * a;
-        if (m >= M) continue;
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int n = n0 + tn + 16 * c;
-            if (n >= N) continue;
-            float v = acc[a][c];
-            if (EPI == 1) v += bias[n];
-            C[(long long)m * ldc + n] = v;
-        }
-    }
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int m = m0 + wm + 16 * i + g + (c >> 1) * 8, n = n0 + wn + 8 * j + 2 * q + (c & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][c];
+                if (EPI == 1) v += bias[n];
+                C[(long long)m * ldc + n] = v;
+            }
 }
 
 template <bool TA, bool TB, bool RB, int EPI>
