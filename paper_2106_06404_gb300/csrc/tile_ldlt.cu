@@ -1839,6 +1839,191 @@ void launch_band_ws(const TileBatch& tb, const CUtensorMap& tm, double* X, int l
     MSDD_LAUNCH_CHECK();
 }
 
+// ---- one right-hand side, wide bands: the off-diagonal tiles of a step split
+// over warps.  With one column a step is a chain of kb tile products and the
+// T_R product in one warp; here WS consumer warps each take the tiles d = w + 1,
+// w + 1 + WS, ... of the step and store their partial sums, and warp 0 forms
+// the right-hand side minus those sums and applies T_R (T_R^T backward), writes
+// the step's solution to the ring and to X, under two named barriers of the
+// consumer warps.  The producer warp streams the tiles as in
+// k_tile_solve_band_ws; warp 0 alone releases a stage, after the barrier that
+// ends every warp's reads of it.
+template <int KBP, int WS, int NST, int XD>
+struct BandSplit {
+    static_assert(XD <= KBP + 2, "X prefetch deeper than the solution ring allows");
+    static constexpr int S = KBP + 1;
+    static constexpr int NT = 32 * (WS + 1);
+    static constexpr size_t smem_bytes = 1024 + (size_t)NST * S * NB2 * sizeof(float) + (size_t)NST * NB * 4 +
+                                         16 * (size_t)NST + (size_t)(S + WS + 1) * NB * 4 + 16 + (size_t)XD * NB * 8;
+};
+
+template <int KBP, int WS, int NST, int XD>
+__global__ void __launch_bounds__(32 * (WS + 1)) k_tile_solve_band_split(
+    const __grid_constant__ CUtensorMap tmt, const float* __restrict__ dinv, const int* __restrict__ kb_,
+    const int* __restrict__ K_, const int* __restrict__ b_, const long long* __restrict__ toff_,
+    const long long* __restrict__ roff_, double* __restrict__ X, const int* __restrict__ gdone)
+{
+    using Cfg = BandSplit<KBP, WS, NST, XD>;
+    constexpr int S = Cfg::S;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    float* St = reinterpret_cast<float*>(base);                                        // [NST][S][32*32]
+    float* Sd = St + (size_t)NST * S * NB2;                                            // [NST][32]
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(Sd + (size_t)NST * NB);
+    unsigned long long* empty = full + NST;
+    float* Zr = reinterpret_cast<float*>(empty + NST);                                // [S][32] solutions
+    float* Pp = Zr + (size_t)S * NB;                                                   // [WS][32] partial sums
+    float* Acc = Pp + (size_t)WS * NB;                                                 // [32]
+    double* Xs = reinterpret_cast<double*>(                                            // [XD][32]
+        base + ((reinterpret_cast<unsigned char*>(Acc + NB) - base + 15) & ~(size_t)15));
+    __shared__ int s_abort, s_stop;
+
+    const int i = blockIdx.x;
+    if (gdone && *gdone) return;
+    const int kb = kb_[i], K = K_[i], bw = b_[i];
+    if (kb > KBP) return;                            // never launched so (host dispatch)
+    const long long toff = toff_[i], roff = roff_[i];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t == 0) {
+        s_abort = 0;
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto stile = [&](int st, int slot) { return St + (size_t)(st * S + slot) * NB2; };
+    auto give_up = [&]() {
+        if (atomicExch(&s_abort, 1) == 0) atomicAdd(&g_wait_timeouts, 1);
+    };
+    const int total = 2 * K;
+
+    if (warp == WS) {
+        // ---------------- producer (as in k_tile_solve_band_ws)
+        if (lane == 0) {
+            unsigned pending = 0, par = 0;
+            for (int it = 0; it < total; ++it) {
+                const int st = it % NST;
+                if (it >= NST) {
+                    if (!mbar_wait_bounded(&empty[st], ((it / NST) - 1) & 1u)) { give_up(); break; }
+                    pending &= ~(1u << st);
+                }
+                if (*(volatile int*)&s_abort) break;
+                const bool fwd = it < K;
+                const int R = fwd ? it : total - 1 - it;
+                int nt = 1;
+                for (int d = 1; d <= kb; ++d) {
+                    const int o = fwd ? R - d : R + d;
+                    if (o >= 0 && o < K) ++nt;
+                }
+                mbar_expect_tx(&full[st], nt * NB2 * 4 + (fwd ? 0 : NB * 4));
+                tma_load_tile(stile(st, 0), &tmt, (int)(tile_index(toff, kb, R, R) / NB), &full[st]);
+                for (int d = 1; d <= kb; ++d) {
+                    const int o = fwd ? R - d : R + d;
+                    if (o < 0 || o >= K) continue;
+                    const long long ti = fwd ? tile_index(toff, kb, R, o) : tile_index(toff, kb, o, R);
+                    tma_load_tile(stile(st, d), &tmt, (int)(ti / NB), &full[st]);
+                }
+                if (!fwd) bulk_load(Sd + st * NB, dinv + roff + (long long)R * NB, NB * 4, &full[st]);
+                pending |= 1u << st;
+                par = (par & ~(1u << st)) | (((unsigned)(it / NST) & 1u) << st);
+            }
+            if (*(volatile int*)&s_abort)
+                for (int s = 0; s < NST; ++s)
+                    if (pending & (1u << s)) mbar_wait_bounded(&full[s], (par >> s) & 1u);
+        }
+        return;
+    }
+
+    auto consumers_sync = [&]() { asm volatile("bar.sync 1, %0;\n" ::"r"(32 * WS) : "memory"); };
+    // X prefetch of warp 0 (lane = row): index u < K forward block u; u >= K
+    // backward block K - 1 - S - (u - K) (backward steps s >= S)
+    const int nload = K + max(0, K - S);
+    auto issue_load = [&](int u) {
+        if (u < nload) {
+            if (u >= K) __threadfence_block();       // rows written by this lane in the forward sweep
+            const int R = u < K ? u : K - 1 - S - (u - K);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(Xs + (u % XD) * NB + lane)),
+                         "l"(X + roff + (long long)R * NB + lane));
+        }
+        cp_async_commit();
+    };
+    if (warp == 0)
+        for (int u = 0; u < XD - 1; ++u) issue_load(u);
+    int u_next = XD - 1, u_use = 0;
+    for (int it = 0; it < total; ++it) {
+        const int st = it % NST;
+        const bool fwd = it < K;
+        const int R = fwd ? it : total - 1 - it;
+        float rhs[1] = {0.f};
+        if (warp == 0) {
+            if (fwd || (it - K) >= S) {
+                issue_load(u_next++);
+                cp_async_wait_n<XD - 1>();
+                rhs[0] = f64_to_f32(Xs[(u_use % XD) * NB + lane]);
+                ++u_use;
+            } else {
+                rhs[0] = Zr[(R % S) * NB + lane];
+            }
+        }
+        const bool ok = mbar_wait_bounded(&full[st], (it / NST) & 1u);
+        if (!ok) give_up();
+        float part[1] = {0.f};
+        if (ok) {
+            for (int d = warp + 1; d <= kb; d += WS) {
+                const int o = fwd ? R - d : R + d;
+                if (o < 0 || o >= K) continue;
+                const float* L = stile(st, d);
+                const float* Z = Zr + (size_t)(o % S) * NB;
+                if (fwd) {
+                    const int k0 = NB * d - bw;
+                    if (k0 >= 24) ws_row_product<1, 24, 32, 1>(L, Z, lane, part);
+                    else if (k0 >= 16) ws_row_product<1, 16, 32, 1>(L, Z, lane, part);
+                    else ws_row_product<1, 0, 32, 1>(L, Z, lane, part);
+                } else {
+                    const int kend = bw - NB * d + NB;
+                    if (kend <= 8) ws_col_product<1, 8, 1>(L, Z, lane, part);
+                    else if (kend <= 16) ws_col_product<1, 16, 1>(L, Z, lane, part);
+                    else ws_col_product<1, 32, 1>(L, Z, lane, part);
+                }
+            }
+        }
+        Pp[warp * NB + lane] = part[0];
+        consumers_sync();                            // every partial is in Pp
+        if (warp == 0) {
+            if (ok) {
+                float acc = fwd ? rhs[0] : rhs[0] * Sd[st * NB + lane];
+                for (int w = 0; w < WS; ++w) acc -= Pp[w * NB + lane];
+                Acc[lane] = acc;
+                __syncwarp();
+                float out[1] = {0.f};
+                const float* T = stile(st, 0);
+                if (fwd) ws_row_product<1, 0, 32, 1>(T, Acc, lane, out);
+                else ws_col_product<1, 32, 1>(T, Acc, lane, out);
+                Zr[(R % S) * NB + lane] = out[0];
+                X[roff + (long long)R * NB + lane] = f32_to_f64(out[0]);
+            }
+            if (lane == 0) *(volatile int*)&s_stop = *(volatile int*)&s_abort;
+        }
+        consumers_sync();                            // the solution is in the ring; the stage and Pp are free
+        if (warp == 0 && lane == 0) mbar_arrive(&empty[st]);
+        if (*(volatile int*)&s_stop) break;          // sampled once by warp 0: every warp leaves after this step
+    }
+    if (warp == 0) cp_async_wait_n<0>();
+}
+
+template <int KBP, int WS, int NST, int XD>
+void launch_band_split(const TileBatch& tb, const CUtensorMap& tm, double* X, cudaStream_t s, const int* gdone) {
+    using Cfg = BandSplit<KBP, WS, NST, XD>;
+    static_assert(Cfg::smem_bytes <= 227 * 1024, "shared memory per CTA");
+    auto kern = k_tile_solve_band_split<KBP, WS, NST, XD>;
+    raise_smem_limit(kern, Cfg::smem_bytes);
+    kern<<<tb.P, Cfg::NT, Cfg::smem_bytes, s>>>(tm, tb.dinv_f.p, tb.d_kb.p, tb.d_K.p, tb.d_b.p, tb.d_toff.p,
+                                                tb.d_roff.p, X, gdone);
+    MSDD_LAUNCH_CHECK();
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -2123,10 +2308,10 @@ void tile_solve(const TileBatch& tb, double* X, int ldx, int ncols, const int* s
         }
         if (tb.prec && maxkb > 2 && maxkb <= 12) {
             // wide bands, one right-hand side (PCG local solves of 3D boxes):
-            // one consumer warp, two stages of 13 tiles, 8-byte copies of X
+            // the step's off-diagonal tiles split over 6 warps, two stages of 13 tiles
             const CUtensorMap* tm = tile_tensor_map(tb);
             if (tm) {
-                launch_band_ws<12, 1, 1, 2, 4>(tb, *tm, X, 1, 1, nullptr, s, gdone);
+                launch_band_split<12, 6, 2, 4>(tb, *tm, X, s, gdone);
                 return;
             }
         }
