@@ -55,11 +55,6 @@ __global__ void k_copy(const double* __restrict__ z, double* __restrict__ p, lon
         p[u] = z[u];
 }
 
-__global__ void k_fin_alpha(PcgScalars* sc, const double* __restrict__ partial, int nblocks) {
-    if (sc->done) return;
-    double v = sum_partials(partial, nblocks);
-    if (threadIdx.x == 0) pcg_fin_apply(sc, PCG_FIN_ALPHA, v);
-}
 
 // fin = PCG_FIN_RR: the last block applies the r.r test itself
 __global__ void __launch_bounds__(1024) k_axpy(PcgScalars* sc, double* __restrict__ x, double* __restrict__ r,
@@ -85,17 +80,7 @@ __global__ void __launch_bounds__(1024) k_axpy(PcgScalars* sc, double* __restric
     if (fin) pcg_last_block(sc, fin, partial);
 }
 
-__global__ void k_fin_rr(PcgScalars* sc, const double* __restrict__ partial, int nblocks) {
-    if (sc->done) return;
-    double v = sum_partials(partial, nblocks);
-    if (threadIdx.x == 0) pcg_fin_apply(sc, PCG_FIN_RR, v);
-}
 
-__global__ void k_fin_beta(PcgScalars* sc, const double* __restrict__ partial, int nblocks) {
-    if (sc->done) return;
-    double v = sum_partials(partial, nblocks);
-    if (threadIdx.x == 0) pcg_fin_apply(sc, PCG_FIN_BETA, v);
-}
 
 __global__ void k_update_p(const PcgScalars* sc, const double* __restrict__ z, double* __restrict__ p, long long n) {
     if (sc->done) return;
@@ -254,21 +239,9 @@ void pcg_fin_rho0(PcgScalars* sc, const double* partial, int nblocks, const doub
     k_copy<<<vec_blocks(n), 256, 0, s>>>(z, p, n, sc);
     MSDD_LAUNCH_CHECK();
 }
-void pcg_fin_alpha(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s) {
-    k_fin_alpha<<<1, 32, 0, s>>>(sc, partial, nblocks);
-    MSDD_LAUNCH_CHECK();
-}
 void pcg_axpy(PcgScalars* sc, double* x, double* r, const double* p, const double* q, long long n, double* partial,
               int nblocks, cudaStream_t s, bool fuse_rr) {
     k_axpy<<<nblocks, 1024, 0, s>>>(sc, x, r, p, q, n, partial, fuse_rr ? PCG_FIN_RR : PCG_FIN_NONE);
-    MSDD_LAUNCH_CHECK();
-}
-void pcg_fin_rr(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s) {
-    k_fin_rr<<<1, 32, 0, s>>>(sc, partial, nblocks);
-    MSDD_LAUNCH_CHECK();
-}
-void pcg_fin_beta(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s) {
-    k_fin_beta<<<1, 32, 0, s>>>(sc, partial, nblocks);
     MSDD_LAUNCH_CHECK();
 }
 void pcg_update_p(PcgScalars* sc, const double* z, double* p, long long n, cudaStream_t s) {

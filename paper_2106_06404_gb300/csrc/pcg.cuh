@@ -44,8 +44,8 @@ __device__ __forceinline__ void pcg_fin_apply(PcgScalars* sc, int fin, double v)
 }
 // Called by every thread of every block once thread 0 has stored
 // partial[blockIdx.x]: the last block to arrive sums the gridDim.x partials
-// (one warp, lane-strided then a fixed shuffle tree, the order of the
-// separate finishing kernels) and applies `fin`.
+// (one warp, lane-strided then a fixed shuffle tree: a fixed order, so the
+// result does not depend on which block arrives last) and applies `fin`.
 __device__ __forceinline__ void pcg_last_block(PcgScalars* sc, int fin, const double* partial) {
     __shared__ int s_last;
     __threadfence();
@@ -71,16 +71,10 @@ void pcg_fin_bb(PcgScalars* sc, const double* partial, int nblocks, double tol, 
 // rho = sum(partial) (r.z after the first preconditioner application); p = z
 void pcg_fin_rho0(PcgScalars* sc, const double* partial, int nblocks, const double* z, double* p, long long n,
                   cudaStream_t s);
-// alpha = rho / sum(partial)
-void pcg_fin_alpha(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
 // x += alpha p, r -= alpha q, partial sums of r.r (fuse_rr: and the r.r
-// test of pcg_fin_rr, applied by the kernel's last block)
+// convergence / maxit test, PCG_FIN_RR, applied by the kernel's last block)
 void pcg_axpy(PcgScalars* sc, double* x, double* r, const double* p, const double* q, long long n, double* partial,
               int nblocks, cudaStream_t s, bool fuse_rr = false);
-// rr = sum(partial); iters += 1; convergence / maxit test
-void pcg_fin_rr(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
-// beta = sum(partial) / rho; rho = sum(partial)
-void pcg_fin_beta(PcgScalars* sc, const double* partial, int nblocks, cudaStream_t s);
 // p = z + beta p
 void pcg_update_p(PcgScalars* sc, const double* z, double* p, long long n, cudaStream_t s);
 
