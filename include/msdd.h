@@ -97,7 +97,9 @@ typedef struct msdd_spectral {
 
 typedef struct msdd_options {
     int precision;       /* 0: FP64 everywhere ("plain");
-                            1: FP32 fine-level factors and solves, FP64 elsewhere ("chosen") */
+                            1: FP32 fine-level factors and solves, the fine level's Gram products,
+                               operator applications and updates in double-float (FP32 pairs,
+                               ~47 significant bits), FP64 elsewhere ("chosen") */
     int block_p;         /* subspace block size; 0 selects min(nev_max + 4, 32) on the fine
                             level and min(nev_max + 8, 32) on coarse levels */
     int eig_maxit;       /* subspace iterations per level (default 200) */

@@ -143,3 +143,23 @@ def test_oracle_leg_error_summary(tmp_path):
     assert e["coarse_dims"]["gpu"] == e["coarse_dims"]["oracle"]
     assert e["iterations"]["gpu"] == e["iterations"]["oracle"]
     assert e["solution_gpu"]["rel_err_A"] < 1e-6 and e["solution_oracle"]["rel_err_A"] < 1e-6
+
+
+def test_measured_traffic_holds_only_for_its_workload_and_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from the committed capture only for the
+    workload and the kernel source it was taken from."""
+    import hashlib
+    src = tmp_path / "kernel.cu"
+    src.write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# comment = ignored\nfamily=fine_gevp_solve\nkernel=k\nworkload=w512\nsource=kernel.cu\n"
+        "source_sha256=%s\ndram_bytes_per_launch=1000\nalgorithmic_bytes_captured_launch=1200\n" % digest)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    got = bench.measured_traffic("fine_gevp_solve", "w512")
+    assert got["traffic"] == 1000.0 and got["traffic_launch_algorithmic_bytes"] == 1200.0
+    assert bench.measured_traffic("fine_gevp_solve", "other_workload") == {}
+    assert bench.measured_traffic("fine_gevp_apply", "w512") == {}
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    assert bench.measured_traffic("fine_gevp_solve", "w512")["traffic"] is None
