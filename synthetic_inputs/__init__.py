@@ -104,6 +104,17 @@ def composite_3d(N, seed=0, ply_aniso=1e-3, resin=1e-2, n_ply=9, n_resin=8, resi
     return comps.reshape(N * N * N, 6)
 
 
+def layered_3d(N, seed=0, contrast=1e4):
+    """Seeded 3D scalar field for small 3D cases: one-element layers along z
+    alternating kappa 1 and `contrast`, times exp(0.5 g) with g standard normal
+    per element (PCG64(seed)); element-major, x fastest."""
+    rng = np.random.default_rng(seed)
+    z = np.arange(N)
+    layer = np.where(z % 2 == 0, 1.0, contrast)
+    k = layer[:, None, None] * np.ones((N, N, N)) * np.exp(0.5 * rng.standard_normal((N, N, N)))
+    return k.ravel()
+
+
 @dataclass
 class Workload:
     """A named problem: mesh, coefficient recipe, decomposition, spectral options."""

@@ -47,6 +47,10 @@ CASES = {
     "ragged3": dict(n=(52, 44), parts=(6, 5), overlap=2, levels=3, group=(2, 2), nev=6, eta=0.3,
                     kappa=lambda: si.grf_channels_inclusions_2d(52, seed=3, n_channels=3, n_inclusions=4,
                                                                 inclusion_side=(3, 6))[: 52 * 44]),
+    # 3D: the tensor-core factorisation, the wide-band TMA solves and the split
+    # single-column PCG solves at half-bandwidths of 3-4 tiles
+    "layered3d": dict(n=(14, 14, 14), parts=(3, 3, 3), overlap=1, levels=2, group=(1, 1, 1), nev=6, eta=0.3,
+                      kappa=lambda: si.layered_3d(14, seed=4)),
 }
 
 
@@ -66,7 +70,7 @@ def _chosen(name, precision=1):
                          precision=precision)
 
 
-@pytest.mark.parametrize("name", ["channels64", "ragged3"])
+@pytest.mark.parametrize("name", ["channels64", "ragged3", "layered3d"])
 def test_chosen_form_eigenvalues_counts_and_dimensions(name):
     c = CASES[name]
     mesh, kap, H = oracle_case(name)
@@ -88,7 +92,7 @@ def test_chosen_form_eigenvalues_counts_and_dimensions(name):
     assert st["eig_unconverged"] == [0] * c["levels"]
 
 
-@pytest.mark.parametrize("name", ["channels64", "ragged3"])
+@pytest.mark.parametrize("name", ["channels64", "ragged3", "layered3d"])
 def test_chosen_form_preconditioner_and_solution(name):
     mesh, kap, H = oracle_case(name)
     G = _chosen(name)

@@ -48,6 +48,9 @@ CASES = {
     "ragged3": dict(n=(52, 44), parts=(6, 5), overlap=2, levels=3, group=(2, 2), nev=6, eta=0.3,
                     kappa=lambda: si.grf_channels_inclusions_2d(52, seed=3, n_channels=3, n_inclusions=4,
                                                                 inclusion_side=(3, 6))[: 52 * 44]),
+    # 3D boxes of 5-6 elements a side: half-bandwidths of 3-4 tiles
+    "layered3d": dict(n=(14, 14, 14), parts=(3, 3, 3), overlap=1, levels=2, group=(1, 1, 1), nev=6, eta=0.3,
+                      kappa=lambda: si.layered_3d(14, seed=4)),
 }
 
 
@@ -127,7 +130,7 @@ def test_operator_and_load_vector_match_oracle():
 
 
 # ---------------------------------------------------------------- hierarchy
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d"])
 def test_setup_matches_oracle(name):
     c = CASES[name]
     mesh, kap, H = oracle_case(name)
@@ -153,7 +156,7 @@ def test_setup_matches_oracle(name):
     assert st["eig_unconverged"] == [0] * c["levels"]
 
 
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d"])
 def test_preconditioner_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)
@@ -165,7 +168,7 @@ def test_preconditioner_matches_oracle(name):
         assert np.linalg.norm(z - zo) / np.linalg.norm(zo) < 1e-6
 
 
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d"])
 def test_pcg_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)

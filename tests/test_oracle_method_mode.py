@@ -83,21 +83,12 @@ def test_subspace_iteration_matches_dense_gevp():
         assert np.allclose(X.T @ B @ X, np.eye(X.shape[1]), atol=1e-9)
 
 
-def _layered_3d(N, seed):
-    """Seeded 3D scalar field: layers of kappa 1 and 1e4 along z times a log-normal factor."""
-    rng = np.random.default_rng(seed)
-    z = np.arange(N)
-    layer = np.where(z % 2 == 0, 1.0, 1e4)
-    k = layer[:, None, None] * np.ones((N, N, N)) * np.exp(0.5 * rng.standard_normal((N, N, N)))
-    return k.ravel()
-
-
 CASES = {
     "channels64": lambda: (si.channels64(), None),
     "three_level": lambda: (None, dict(n=(32, 32), parts=(4, 4), overlap=2, levels=3, group=(2, 2), nev=6,
                                        eta=0.3, kappa=si.channels_2d(32, 4, 1e5, seed=5))),
     "three_d": lambda: (None, dict(n=(8, 8, 8), parts=(2, 2, 2), overlap=1, levels=2, group=(1, 1, 1), nev=6,
-                                   eta=0.3, kappa=_layered_3d(8, seed=3))),
+                                   eta=0.3, kappa=si.layered_3d(8, seed=3))),
 }
 
 
