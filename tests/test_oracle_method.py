@@ -4,6 +4,8 @@ Expected values come from the paper's theorems (Lemma upper_bound, Theorem
 multilevelrate with Lemma spectral1's C_1 = 1/eta), from exact special cases
 (one subdomain covering the domain), from a direct sparse solve, and from the
 behaviour the paper reports (iterations flat in the contrast, Tab. 1 and 3).
+The CG Lanczos estimate of the spectrum of BA is pinned by exact
+termination on a diagonal system with a known spectrum.
 """
 import numpy as np
 import pytest
@@ -101,3 +103,25 @@ def test_iterations_flat_in_contrast_one_level_not():
         one.append(method.pcg(H.A, b, H.apply_one_level, 1e-8, maxit=3000)[1])
     assert max(two) - min(two) <= 5
     assert max(one) > 1.5 * max(two)
+
+
+def test_lanczos_condition_recovers_the_spectrum():
+    """CG's Lanczos tridiagonal (built from the recorded alphas and betas):
+    with A = diag(d) and B = diag(1/w), BA has the eigenvalues d/w; from a
+    right-hand side touching all 12 of them, CG ends after 12 steps and the
+    extreme eigenvalues of the tridiagonal are the extreme d/w (exact
+    termination); after fewer steps its eigenvalues lie inside them
+    (interlacing)."""
+    d = np.arange(1.0, 13.0) ** 2
+    w = np.linspace(0.5, 2.0, 12)
+    ev = np.sort(d / w)
+    A = np.diag(d)
+    b = np.ones(12)
+    _, it, _, al, be = method.pcg(A, b, lambda r: r / w, 1e-12, maxit=40)
+    assert it == 12
+    lo, hi = method.lanczos_condition(al, be)
+    assert abs(lo - ev[0]) <= 1e-8 * ev[0] and abs(hi - ev[-1]) <= 1e-8 * ev[-1]
+    _, it5, _, al5, be5 = method.pcg(A, b, lambda r: r / w, 1e-12, maxit=5)
+    assert it5 == 5
+    lo5, hi5 = method.lanczos_condition(al5, be5)
+    assert ev[0] - 1e-9 <= lo5 < hi5 <= ev[-1] + 1e-9 and hi5 < ev[-1]

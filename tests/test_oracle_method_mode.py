@@ -12,7 +12,9 @@ the fine level) against the dense oracle and against brute force.
     and coarse dimensions exact, eigenvalues to 1e-8 relative (1e-7 on the
     middle level), the preconditioner application and the PCG iterates to
     1e-8;
-  * worker processes give the same result as the in-process loop.
+  * worker processes give the same result as the in-process loop;
+  * the bounded fine-level sample (the host baseline of the 3D workloads)
+    against the dense oracle's eigenvalues and counts on sampled subdomains.
 """
 import numpy as np
 import pytest
@@ -136,3 +138,21 @@ def test_worker_processes_give_the_same_hierarchy():
     for a, b in zip(M1.levels[M1.L].subs, M2.levels[M2.L].subs):
         assert np.array_equal(a["lam"], b["lam"]) and np.array_equal(a["W"], b["W"])
     assert np.array_equal(M1.A0, M2.A0)
+
+
+def test_fine_level_sample_matches_dense_oracle():
+    """The bounded fine-level sample that stands in for a full step on
+    workloads too large for the host: its Ritz values and selected counts on
+    sampled subdomains equal the dense oracle's complete GEVP solution."""
+    c = CASES["three_d"]()[1]
+    mesh = fem.Mesh(c["n"], 0b1)
+    D = method.Hierarchy(mesh, c["kappa"], c["parts"], c["overlap"], c["levels"], c["group"], c["nev"], c["eta"])
+    sample = [0, 3, 7]
+    got = method_mode.fine_level_sample(c["n"], 0b1, c["kappa"], c["parts"], c["overlap"], c["levels"], c["group"],
+                                        c["nev"], c["eta"], sample, processes=1, tol=1e-10)
+    for i, g in zip(sample, got):
+        ref = D.levels[D.L].subs[i]
+        assert g["m"] == ref["m"] and g["eig_iterations"] > 0
+        k = g["m"]
+        err = np.abs(g["lam"][:k] - ref["lam"][:k]) / np.maximum(np.abs(ref["lam"][:k]), 1e-3 * c["eta"])
+        assert k == 0 or err.max() < 1e-8, (i, err)
