@@ -186,7 +186,16 @@ long long msdd_num_unknowns(const msdd_mesh* mesh);
 /* Build the hierarchy (Section 2.3 construction, recursive over levels):
  * local Dirichlet factorisations, local GEVPs by batched subspace iteration,
  * coarse Galerkin matrices, coarse GEVPs on generating systems and the
- * coarsest factorisation.  On success *out owns all device memory it needs. */
+ * coarsest factorisation.  On success *out owns all device memory it needs.
+ * A coarse level must not come out empty: if no fine eigenvalue on any
+ * subdomain lies below eta (level 1 would have dimension 0), if a level-1
+ * subdomain's patch holds no fine coarse function, or if no level-1
+ * eigenvalue lies below eta (the coarsest space would be empty), the call
+ * returns MSDD_ERR_UNSUPPORTED naming the case, after the local set-up work,
+ * and *out is left NULL.  (The method itself degenerates gracefully there:
+ * the empty coarse correction contributes nothing, e.g. one subdomain
+ * covering the domain with chi = 1 gives all eigenvalues 1; raise eta or use
+ * fewer levels instead.) */
 msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msdd_decomp* decomp,
                        const msdd_spectral* spectral, const msdd_options* options, msdd_hierarchy** out);
 
