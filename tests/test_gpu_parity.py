@@ -34,7 +34,7 @@ EIG_TOL = 1e-10
 @functools.lru_cache(maxsize=None)
 def oracle_case(name):
     c = CASES[name]
-    mesh = fem.Mesh(c["n"], 0b1)
+    mesh = fem.Mesh(c["n"], c.get("faces", 0b1))
     kap = c["kappa"]()
     H = method.Hierarchy(mesh, kap, c["parts"], c["overlap"], c["levels"], c["group"], c["nev"], c["eta"])
     return mesh, kap, H
@@ -51,6 +51,12 @@ CASES = {
     # 3D boxes of 5-6 elements a side: half-bandwidths of 3-4 tiles
     "layered3d": dict(n=(14, 14, 14), parts=(3, 3, 3), overlap=1, levels=2, group=(1, 1, 1), nev=6, eta=0.3,
                       kappa=lambda: si.layered_3d(14, seed=4)),
+    # Dirichlet faces other than x = 0: x = 1 and y = 0 (2D, ragged boxes);
+    # x = 0 and z = 1 (3D)
+    "faces2d": dict(n=(30, 26), parts=(4, 3), overlap=2, levels=2, group=(1, 1), nev=6, eta=0.3, faces=0b0110,
+                    kappa=lambda: si.channels_2d(30, 4, 1e4, seed=6)[: 30 * 26]),
+    "faces3d": dict(n=(10, 9, 8), parts=(2, 2, 2), overlap=1, levels=2, group=(1, 1, 1), nev=6, eta=0.3,
+                    faces=0b100001, kappa=lambda: si.layered_3d(10, seed=7).reshape(10, 10, 10)[:8, :9, :].ravel()),
 }
 
 
@@ -58,7 +64,7 @@ def _gpu(name, precision=0, eig_tol=EIG_TOL):
     c = CASES[name]
     kap = torch.tensor(c["kappa"](), device="cuda")
     return pkg.Hierarchy(c["n"], kap, c["parts"], c["overlap"], c["levels"], c["group"], c["nev"], c["eta"],
-                         precision=precision, eig_tol=eig_tol)
+                         dirichlet_faces=c.get("faces", 0b1), precision=precision, eig_tol=eig_tol)
 
 
 def _eig_close(theta, lam, eta, m):
@@ -130,7 +136,7 @@ def test_operator_and_load_vector_match_oracle():
 
 
 # ---------------------------------------------------------------- hierarchy
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d"])
 def test_setup_matches_oracle(name):
     c = CASES[name]
     mesh, kap, H = oracle_case(name)
@@ -156,7 +162,7 @@ def test_setup_matches_oracle(name):
     assert st["eig_unconverged"] == [0] * c["levels"]
 
 
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d"])
 def test_preconditioner_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)
@@ -168,7 +174,7 @@ def test_preconditioner_matches_oracle(name):
         assert np.linalg.norm(z - zo) / np.linalg.norm(zo) < 1e-6
 
 
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d"])
 def test_pcg_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)

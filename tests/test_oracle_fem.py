@@ -91,6 +91,25 @@ def test_manufactured_solution_is_nodally_exact(N, M):
     assert np.abs(u - (x - 0.5 * x * x)).max() < 1e-12
 
 
+@pytest.mark.parametrize("faces,axis", [(0b11, 0), (0b1100, 1)])
+def test_manufactured_solution_two_dirichlet_faces(faces, axis):
+    """-u'' = 1 along one axis with u = 0 on both of its faces has
+    u = t (1 - t) / 2; with kappa = 1 and Neumann on the other faces the Q1
+    system reduces to 1D linear elements as above, which are nodally exact.
+    Pins the unknown numbering and the load vector with Dirichlet faces at
+    x_d = 1 as well as x_d = 0."""
+    N, M = (10, 7) if axis == 0 else (7, 10)
+    mesh = fem.Mesh((N, M), faces)
+    A = fem.assemble_system(mesh, np.ones(mesh.num_elements))
+    b = fem.load_vector(mesh)
+    import scipy.sparse.linalg as spla
+    u = spla.spsolve(A.tocsc(), b)
+    sx, sy = mesh.unknown_shape
+    ix, iy = np.meshgrid(np.arange(sx) + mesh.unknown_lo[0], np.arange(sy) + mesh.unknown_lo[1], indexing="xy")
+    t = (ix / N if axis == 0 else iy / M).ravel()
+    assert np.abs(u - 0.5 * t * (1 - t)).max() < 1e-12
+
+
 def test_unknown_numbering_is_lexicographic():
     mesh = fem.Mesh((4, 3), 0b1 | 0b1000)         # x=0 and y=1 Dirichlet
     n2u = mesh.node_to_unknown()
