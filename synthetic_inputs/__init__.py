@@ -104,6 +104,17 @@ def composite_3d(N, seed=0, ply_aniso=1e-3, resin=1e-2, n_ply=9, n_resin=8, resi
     return comps.reshape(N * N * N, 6)
 
 
+def rotated_channels_2d(N, n_channels=4, contrast=1e4, aniso=1e-2, seed=0):
+    """Seeded 2D tensor field (kxx, kyy, kxy) per element: the scalar field
+    channels_2d(N, n_channels, contrast, seed) times R diag(1, aniso) R^T, R
+    the rotation by an angle drawn uniformly from [0, pi) per element
+    (PCG64(seed + 1)); element-major, x fastest."""
+    k = channels_2d(N, n_channels, contrast, seed)
+    th = np.random.default_rng(seed + 1).uniform(0.0, np.pi, N * N)
+    c, s = np.cos(th), np.sin(th)
+    return np.stack([k * (c * c + aniso * s * s), k * (s * s + aniso * c * c), k * (1.0 - aniso) * c * s], axis=1)
+
+
 def layered_3d(N, seed=0, contrast=1e4):
     """Seeded 3D scalar field for small 3D cases: one-element layers along z
     alternating kappa 1 and `contrast`, times exp(0.5 g) with g standard normal

@@ -51,6 +51,12 @@ CASES = {
     # single-column PCG solves at half-bandwidths of 3-4 tiles
     "layered3d": dict(n=(14, 14, 14), parts=(3, 3, 3), overlap=1, levels=2, group=(1, 1, 1), nev=6, eta=0.3,
                       kappa=lambda: si.layered_3d(14, seed=4)),
+    # tensor coefficients: rotated anisotropic channels (2D, kxx kyy kxy) and
+    # rotated plies with resin layers (3D, six components)
+    "tensor2d": dict(n=(28, 28), parts=(4, 4), overlap=2, levels=2, group=(1, 1), nev=6, eta=0.3,
+                     kappa=lambda: si.rotated_channels_2d(28, seed=3)),
+    "tensor3d": dict(n=(10, 10, 10), parts=(2, 2, 2), overlap=1, levels=2, group=(1, 1, 1), nev=8, eta=0.3,
+                     kappa=lambda: si.composite_3d(10, seed=1, n_ply=3, n_resin=2, resin_thickness=1)),
 }
 
 
@@ -70,7 +76,7 @@ def _chosen(name, precision=1):
                          precision=precision)
 
 
-@pytest.mark.parametrize("name", ["channels64", "ragged3", "layered3d"])
+@pytest.mark.parametrize("name", ["channels64", "ragged3", "layered3d", "tensor2d", "tensor3d"])
 def test_chosen_form_eigenvalues_counts_and_dimensions(name):
     c = CASES[name]
     mesh, kap, H = oracle_case(name)
@@ -92,7 +98,7 @@ def test_chosen_form_eigenvalues_counts_and_dimensions(name):
     assert st["eig_unconverged"] == [0] * c["levels"]
 
 
-@pytest.mark.parametrize("name", ["channels64", "ragged3", "layered3d"])
+@pytest.mark.parametrize("name", ["channels64", "ragged3", "layered3d", "tensor2d", "tensor3d"])
 def test_chosen_form_preconditioner_and_solution(name):
     mesh, kap, H = oracle_case(name)
     G = _chosen(name)

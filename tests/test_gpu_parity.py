@@ -57,6 +57,12 @@ CASES = {
                     kappa=lambda: si.channels_2d(30, 4, 1e4, seed=6)[: 30 * 26]),
     "faces3d": dict(n=(10, 9, 8), parts=(2, 2, 2), overlap=1, levels=2, group=(1, 1, 1), nev=6, eta=0.3,
                     faces=0b100001, kappa=lambda: si.layered_3d(10, seed=7).reshape(10, 10, 10)[:8, :9, :].ravel()),
+    # tensor coefficients: rotated anisotropic channels (2D, kxx kyy kxy) and
+    # rotated plies with resin layers (3D, six components)
+    "tensor2d": dict(n=(28, 28), parts=(4, 4), overlap=2, levels=2, group=(1, 1), nev=6, eta=0.3,
+                     kappa=lambda: si.rotated_channels_2d(28, seed=3)),
+    "tensor3d": dict(n=(10, 10, 10), parts=(2, 2, 2), overlap=1, levels=2, group=(1, 1, 1), nev=8, eta=0.3,
+                     kappa=lambda: si.composite_3d(10, seed=1, n_ply=3, n_resin=2, resin_thickness=1)),
 }
 
 
@@ -136,7 +142,8 @@ def test_operator_and_load_vector_match_oracle():
 
 
 # ---------------------------------------------------------------- hierarchy
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d",
+                                  "tensor2d", "tensor3d"])
 def test_setup_matches_oracle(name):
     c = CASES[name]
     mesh, kap, H = oracle_case(name)
@@ -162,7 +169,8 @@ def test_setup_matches_oracle(name):
     assert st["eig_unconverged"] == [0] * c["levels"]
 
 
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d",
+                                  "tensor2d", "tensor3d"])
 def test_preconditioner_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)
@@ -174,7 +182,8 @@ def test_preconditioner_matches_oracle(name):
         assert np.linalg.norm(z - zo) / np.linalg.norm(zo) < 1e-6
 
 
-@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d"])
+@pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d",
+                                  "tensor2d", "tensor3d"])
 def test_pcg_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)

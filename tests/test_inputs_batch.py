@@ -1,5 +1,6 @@
-"""The batched multi-problem input recipe: 256 seeded 2D problems of uneven
-size (sides 128..384, 4x4..12x12 subdomains, contrast 1e4..1e6)."""
+"""Input recipes: the batched multi-problem recipe (256 seeded 2D problems of
+uneven size: sides 128..384, 4x4..12x12 subdomains, contrast 1e4..1e6) and
+the 2D tensor field of the tensor-coefficient parity cases."""
 import numpy as np
 
 import synthetic_inputs as si
@@ -31,3 +32,16 @@ def test_batch_coefficients():
         # the channel rows carry the contrast on top of the log-normal background
         ratio = np.exp(np.median(np.log(rows), axis=1))
         assert np.sum(ratio > np.sqrt(w.contrast)) == N // 16
+
+
+def test_rotated_channel_tensors():
+    """The 2D tensor field: per element a symmetric tensor with eigenvalues
+    k and aniso * k, k the channel field's value; seeded."""
+    N, aniso = 20, 1e-2
+    T = si.rotated_channels_2d(N, n_channels=3, contrast=1e4, aniso=aniso, seed=5)
+    k = si.channels_2d(N, 3, 1e4, seed=5)
+    assert T.shape == (N * N, 3)
+    M = np.stack([np.stack([T[:, 0], T[:, 2]], 1), np.stack([T[:, 2], T[:, 1]], 1)], 1)
+    ev = np.linalg.eigvalsh(M)
+    assert np.allclose(ev[:, 0], aniso * k, rtol=1e-12) and np.allclose(ev[:, 1], k, rtol=1e-12)
+    assert np.array_equal(T, si.rotated_channels_2d(N, n_channels=3, contrast=1e4, aniso=aniso, seed=5))
