@@ -27,7 +27,19 @@ same pencil by an independent route and check what Section 3.3 fixes:
   * the regularised LDL^T route of Section 4.2 (Eq. evp_reg) that the
     oracle takes on coarse levels: on generators with exact dependencies it
     drops exactly those (null pivots = dim ker A cap ker B) and yields the
-    pencil's eigenvalues on the span, whatever the generators' scaling.
+    pencil's eigenvalues on the span, whatever the generators' scaling;
+  * in 3D the threshold (a pivot d_k <= 1e-6 K_kk is null) also drops
+    generators that are only nearly dependent; there the null pivots are
+    recomputed as explicit Schur complements of K = Abar + sigma B onto the
+    generators kept before them, and the finite eigenvalues as those of the
+    Schur complement of Abar onto the own generators (B vanishes outside
+    that block) against B's own block, by scipy's symmetric-definite
+    solver; a pencil restricted to fewer generators has eigenvalues no
+    lower, one by one, than the pencil with every generator kept (the
+    Courant-Fischer characterisation), which the hierarchy built with a
+    threshold that keeps them all must show.  The 2D spectrum-structure and
+    brute-force pins assume exact dependencies only and stay on the 2D
+    cases.
 """
 import numpy as np
 import pytest
@@ -51,6 +63,15 @@ def ragged_three_level():
     mesh = fem.Mesh((20, 18), 0b1)
     kap = si.channels_2d(20, 3, 1e5, seed=4)[: 20 * 18]
     H = method.Hierarchy(mesh, kap, (5, 4), 2, 3, (2, 2), 5, 0.3, keep_local=True)
+    return mesh, kap, H
+
+
+@pytest.fixture(scope="module")
+def three_level_3d():
+    # 8^3 elements, 4^3 fine subdomains, 2^3 middle subdomains of 2^3 children
+    mesh = fem.Mesh((8, 8, 8), 0b1)
+    kap = si.layered_3d(8, seed=2)
+    H = method.Hierarchy(mesh, kap, (4, 4, 4), 1, 3, (2, 2, 2), 4, 0.3, keep_local=True)
     return mesh, kap, H
 
 
@@ -107,7 +128,7 @@ def _cases(H):
     return range(H.dec.num_subdomains(1))
 
 
-@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level"])
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level", "three_level_3d"])
 def test_generating_system_matches_element_assembly(fixture, request):
     mesh, kap, H = request.getfixturevalue(fixture)
     lev = H.levels[1]
@@ -173,7 +194,7 @@ def test_coarse_eigenvalues_brute_force(fixture, request):
         assert err.max() < 1e-7, err
 
 
-@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level"])
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level", "three_level_3d"])
 def test_coarse_projection_stability(fixture, request):
     """|Pi_m v|_a <= |v|_a, |v - Pi_m v|_a <= |v|_a and, for m >= #zeros,
     |v - Pi_m v|_b^2 <= |v - Pi_m v|_a^2 / lambda_{m+1} (Lemma gevp_properties)."""
@@ -253,3 +274,58 @@ def test_null_pivots_are_the_common_kernel(fixture, request):
         A, B = s["Abar"], s["B"]
         rAB, _ = _rank(A + B)
         assert s["null_pivots"] == A.shape[0] - rAB
+
+
+def _schur_route(A, B, sigma, tau):
+    """(number of null pivots, finite eigenvalues ascending) of the pencil
+    (A, B) by explicit Schur complements: generator k is null when
+    K_kk - K_kS K_SS^{-1} K_Sk <= tau K_kk, S the generators kept before it;
+    the finite eigenvalues are those of A_oo - A_on A_nn^{-1} A_no against
+    B_oo on the kept own (o) and neighbour (n) generators."""
+    n = A.shape[0]
+    no = int(np.sum(np.diag(B) > 0))
+    assert np.all(B[no:, :] == 0.0) and np.all(B[:, no:] == 0.0)     # B lives on the own block
+    K = A + sigma * B
+    kept = []
+    for k in range(n):
+        d = K[k, k]
+        if kept:
+            d -= K[k, kept] @ np.linalg.solve(K[np.ix_(kept, kept)], K[kept, k])
+        if d > tau * K[k, k]:
+            kept.append(k)
+    ko = [k for k in kept if k < no]
+    kn = [k for k in kept if k >= no]
+    S = A[np.ix_(ko, ko)]
+    if kn:
+        Aon = A[np.ix_(ko, kn)]
+        S = S - Aon @ np.linalg.solve(A[np.ix_(kn, kn)], Aon.T)
+    lam = sla.eigh(0.5 * (S + S.T), B[np.ix_(ko, ko)], eigvals_only=True)
+    return n - len(kept), np.sort(lam)
+
+
+@pytest.mark.parametrize("fixture", ["three_level", "ragged_three_level", "three_level_3d"])
+def test_coarse_eigenvalues_schur_complement(fixture, request):
+    mesh, kap, H = request.getfixturevalue(fixture)
+    for i, s in enumerate(H.levels[1].subs):
+        nnull, lam_ref = _schur_route(s["Abar"], s["B"], H.sigma, H.reg_tol)
+        assert s["null_pivots"] == nnull, i
+        lam = s["lam"]
+        assert len(lam) == len(lam_ref), i
+        err = np.abs(lam - lam_ref) / np.maximum(np.abs(lam_ref), 1e-6)
+        assert err.max() < 1e-8, (i, err)
+
+
+def test_three_d_threshold_drops_near_dependencies(three_level_3d):
+    mesh, kap, H = three_level_3d
+    assert H.reg_tol == 1e-6
+    near = 0
+    for s in H.levels[1].subs:
+        rAB, _ = _rank(s["Abar"] + s["B"])
+        near += s["null_pivots"] - (s["Abar"].shape[0] - rAB)
+    assert near > 0                              # null pivots that are not exact dependencies
+    full = method.Hierarchy(mesh, kap, (4, 4, 4), 1, 3, (2, 2, 2), 4, 0.3, reg_tol=1e-10, keep_local=True)
+    for s, f in zip(H.levels[1].subs, full.levels[1].subs):
+        assert f["null_pivots"] == 0 and np.array_equal(s["Abar"], f["Abar"])
+        lo, hi = f["lam"], s["lam"]
+        assert len(hi) == len(lo)               # rank B: the own generators are all kept
+        assert np.all(hi >= lo - 1e-9 * np.maximum(1.0, np.abs(lo)))
