@@ -57,6 +57,10 @@ CASES = {
                     kappa=lambda: si.channels_2d(30, 4, 1e4, seed=6)[: 30 * 26]),
     "faces3d": dict(n=(10, 9, 8), parts=(2, 2, 2), overlap=1, levels=2, group=(1, 1, 1), nev=6, eta=0.3,
                     faces=0b100001, kappa=lambda: si.layered_3d(10, seed=7).reshape(10, 10, 10)[:8, :9, :].ravel()),
+    # 3D with three levels: generating systems whose null-pivot threshold
+    # (1e-6 in 3D) also drops near dependencies
+    "three_level_3d": dict(n=(8, 8, 8), parts=(4, 4, 4), overlap=1, levels=3, group=(2, 2, 2), nev=4, eta=0.3,
+                           kappa=lambda: si.layered_3d(8, seed=2)),
     # tensor coefficients: rotated anisotropic channels (2D, kxx kyy kxy) and
     # rotated plies with resin layers (3D, six components)
     "tensor2d": dict(n=(28, 28), parts=(4, 4), overlap=2, levels=2, group=(1, 1), nev=6, eta=0.3,
@@ -143,7 +147,7 @@ def test_operator_and_load_vector_match_oracle():
 
 # ---------------------------------------------------------------- hierarchy
 @pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d",
-                                  "tensor2d", "tensor3d"])
+                                  "tensor2d", "tensor3d", "three_level_3d"])
 def test_setup_matches_oracle(name):
     c = CASES[name]
     mesh, kap, H = oracle_case(name)
@@ -170,7 +174,7 @@ def test_setup_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d",
-                                  "tensor2d", "tensor3d"])
+                                  "tensor2d", "tensor3d", "three_level_3d"])
 def test_preconditioner_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)
@@ -183,7 +187,7 @@ def test_preconditioner_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", ["small2", "channels64", "ragged3", "layered3d", "faces2d", "faces3d",
-                                  "tensor2d", "tensor3d"])
+                                  "tensor2d", "tensor3d", "three_level_3d"])
 def test_pcg_matches_oracle(name):
     mesh, kap, H = oracle_case(name)
     G = _gpu(name)
