@@ -201,7 +201,8 @@ msdd_status msdd_setup(const msdd_mesh* mesh, const msdd_coeff* coeff, const msd
 
 /* Preconditioned CG, x^0 = 0, stopped when ||b - A x^m||_2 < tol ||b||_2
  * (recursive residual; Section 5).  b, x: device, n doubles.  Returns
- * MSDD_ERR_NO_CONVERGENCE if maxit iterations did not suffice. */
+ * MSDD_ERR_NO_CONVERGENCE if maxit iterations did not suffice.  b = 0 gives
+ * x = 0, *iterations = 0 and *rel_residual = 0. */
 msdd_status msdd_solve(msdd_hierarchy* h, const double* b, double tol, int maxit, double* x, int* iterations,
                        double* rel_residual);
 
@@ -247,7 +248,8 @@ msdd_status msdd_apply_hybrid_preconditioner(msdd_hierarchy* h, const double* r,
  * the true residual.  b, x: device.  *iterations = Arnoldi steps;
  * *rel_residual = ||b - A x||_2 / ||b||_2, the true residual, which cannot
  * fall below about eps || |A| |x| ||_2 / ||b||_2 in FP64.
- * MSDD_ERR_NO_CONVERGENCE at maxit (x holds the last iterate). */
+ * MSDD_ERR_NO_CONVERGENCE at maxit (x holds the last iterate).  b = 0 gives
+ * x = 0 after no step, *rel_residual = 0. */
 msdd_status msdd_solve_gmres(msdd_hierarchy* h, const double* b, double tol, int restart, int maxit, double* x,
                              int* iterations, double* rel_residual);
 
