@@ -4,7 +4,7 @@ Test infrastructure.  Calls only oracle/ (and the seeded input generators of
 synthetic_inputs); nothing here comes from the CUDA library.  Re-run after a
 change of the oracle's arithmetic that a passage of the paper justifies:
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [case ...]
 
 Each JSON file holds one workload's oracle results: per level the selected
 counts m_i = min(nev_max, #{lambda < eta}) (Eq. coarse_space_def) and the
@@ -35,6 +35,10 @@ CASES = {
                                                                 inclusion_side=(3, 6))[: 52 * 44],
                     recipe="grf_channels_inclusions_2d(52, seed=3, n_channels=3, n_inclusions=4, "
                            "inclusion_side=(3, 6)), first 52 x 44 elements"),
+    "three_level_3d": dict(n=(8, 8, 8), parts=(4, 4, 4), overlap=1, levels=3, group=(2, 2, 2), nev=4, eta=0.3,
+                           kappa=lambda: si.layered_3d(8, seed=2),
+                           recipe="layered_3d(8, seed=2): one-element z layers of kappa 1 and 1e4 times "
+                                  "exp(0.5 g); null-pivot threshold 1e-6 on the middle level"),
 }
 
 
@@ -59,12 +63,12 @@ def compute(name):
     return out
 
 
-def main():
-    for name in CASES:
+def main(names=None):
+    for name in names or CASES:
         with open(os.path.join(HERE, name + ".json"), "w") as f:
             json.dump(compute(name), f, indent=1)
             f.write("\n")
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:])
