@@ -30,7 +30,8 @@ Steps, in the paper's order and notation:
 Readings where the paper is silent (listed with the others in the design
 notes): on coarse levels the regularised LDL^T factors K = A + sigma B
 (sigma = 1e-2) in generator order, and a pivot d_k <= tau K_kk is a null
-pivot (tau = 1e-10 in 2D, 1e-6 in 3D; eps^{-1} -> 0); for the b^2 and b^3
+pivot (tau = 1e-10 in 2D; 1e-6 in 3D, where it also drops generators that
+are only nearly dependent; eps^{-1} -> 0); for the b^2 and b^3
 forms on the fine level the common kernel is dropped by a rank threshold
 1e-12 * max eigenvalue of (A + B); eigenvalues with mu <= 1e-13 are treated
 as +infinity; an eigenvector is normalised to b(w, w) = 1 and signed so that
